@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the data-domain multiparameter LSRTM hot path.
+
+A step is one CGNR iteration (one Born modelling L, one migration L^T and the
+FP64 Krylov updates) over every shot of the workload, with the background
+boundary bands cached from the setup. Default workload: the 2D
+Marmousi-shaped batched case (384 x 1152 interior, dx = 8 m, order 8,
+nt = 4000, dt = 0.8 ms, 96 shots, 1152 receivers each, 10 Hz), seeded
+synthetic inputs.
+
+Metric: G cell-updates/s, one cell-update = one padded grid cell advanced one
+time step for one shot in one operator application (L and L^T each count
+Ncell * nt per shot). Printed as one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own copy of the shot set (the
+shots are independent: weak scaling, no data-path collective); the time is
+the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import lsrtm_inputs as li  # noqa: E402
+
+# Algorithmic HBM bytes per cell-update (FP32, one pass per step, model read
+# raw): L = 2 x (3 + 3) state fields read + written + 4 model arrays; L^T = 6
+# state fields read + written + 2 model arrays + 2 image planes read + written.
+BYTES_PER_CELL = {("born", 2): 64.0, ("adjoint", 2): 72.0, ("born", 3): 80.0, ("adjoint", 3): 88.0}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, default=2, help="preset number (default 2)")
+    ap.add_argument("--shots-per-batch", type=int, default=0)
+    ap.add_argument("--bands", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the
+    timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if self.path and os.path.exists(self.path):
+            os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    for f in ("kernels2d.cu", "lsrtm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_10405_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, cells_per_launch):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e.get("src_sha") != kernel_src_sha():
+            return None
+        return float(e["dram_bytes_per_cell"]) * cells_per_launch
+    except Exception:
+        return None
+
+
+def cpu_sample(w, seconds, reps=1):
+    """Times the FP64 oracle (L then L^T) on a bounded sample of the workload:
+    a subset of shots and the first nt_s time steps, sized for ~`seconds` of
+    work. Returns (G cell-updates/s, threads, description, seconds/rep)."""
+    import oracle
+    threads = oracle.num_threads()
+    ncell = w.padded_cells
+    nshot = min(w.geom.nshot, max(1, threads))
+    geom = w.geom.subset(list(range(nshot)))
+    # calibrate the per-step cost from two short runs (removes the set-up time)
+    ts = []
+    for nt_c in (4, 20):
+        t0 = time.perf_counter()
+        oracle.born(w, w.dm, geom=geom, nt=nt_c)
+        ts.append(time.perf_counter() - t0)
+    per_step = max((ts[1] - ts[0]) / 16.0, 1e-6)
+    # L^T costs about 3x L in the oracle (checkpointed recomputation)
+    nt_s = int(max(16, min(w.nt, seconds / (4.0 * per_step))))
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        d = oracle.born(w, w.dm, geom=geom, nt=nt_s)
+        oracle.adjoint(w, d, geom=geom, nt=nt_s)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    cells = 2.0 * nshot * ncell * nt_s
+    desc = (f"oracle L + L^T on {nshot} of {w.geom.nshot} shots x first {nt_s} of {w.nt} steps "
+            f"({cells:.3g} cell-updates), FP64, OpenMP over shots")
+    return cells / t / 1e9, threads, desc, times
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    w = li.preset(args.workload)
+    K, W = args.steps, args.warmup
+    # bounded per-step sample sized so the whole run stays within minutes
+    per = max(2.0, min(args.cpu_seconds, 120.0 / max(K + W, 1)))
+    _, _, _, _ = cpu_sample(w, per / 4, reps=max(W, 0)) if W > 0 else (0, 0, "", [])
+    val, threads, desc, times = cpu_sample(w, per, reps=K)
+    ms = 1e3 * float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": "Born+migration Gcell-updates/s", "value": val,
+        "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": K, "warmup": W,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.nz, w.nx], "nt": w.nt, "order": w.order,
+                   "shots": w.geom.nshot, "sample": desc},
+        "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, Lsrtm
+
+    w = li.preset(args.workload)
+    K, W = args.steps, args.warmup
+    ncell = w.padded_cells
+    nshot = w.geom.nshot
+    cells_per_step = 2.0 * nshot * ncell * w.nt          # L + L^T per CG iteration
+    h = Lsrtm.from_workload(w, band_precision=BAND_BF16 if args.bands == "bf16" else BAND_FP32,
+                            shots_per_batch=args.shots_per_batch)
+    dm_true = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    d_obs = h.born(dm_true)                 # synthetic observed data (untimed setup)
+    h.cg_begin(d_obs)                       # background bands cached here
+    for _ in range(W):
+        h.cg_iterate(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    h.timing(True)
+    h.timings(reset=True)
+    l0 = h.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0.record()
+    for _ in range(K):
+        h.cg_iterate(1)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    launches = h.kernel_launches() - l0
+    tm = h.timings(reset=True)
+    h.timing(False)
+    clk = clocks.stop()
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = cells_per_step * K * world / t_max / 1e9
+
+    # dominant kernel and its roofline
+    kinds = {"born": (tm["born_ms"], tm["born_launches"], tm["born_cells"]),
+             "adjoint": (tm["adjoint_ms"], tm["adjoint_launches"], tm["adjoint_cells"])}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, nl, cells = kinds[dom]
+    cells_per_launch = cells / max(nl, 1)
+    avg_launch_s = ms / 1e3 / max(nl, 1)
+    bpc = BYTES_PER_CELL[(dom, w.ndim)]
+    achieved = bpc * cells_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = ncu_traffic({"born": "k_fwd2d_born", "adjoint": "k_adj2d"}[dom], cells_per_launch)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": {"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"}[dom],
+                "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_cell": bpc, "cells_per_launch": cells_per_launch,
+                "avg_launch_ms": avg_launch_s * 1e3}
+    per_op = {k: {"ms_per_step": v[0] / K, "gcells_per_s": v[2] / (v[0] / 1e3) / 1e9 if v[0] else None,
+                  "gbs": BYTES_PER_CELL[(k, w.ndim)] * v[2] / (v[0] / 1e3) / 1e9 if v[0] else None}
+              for k, v in kinds.items()}
+
+    # end to end through the public API with pinned host buffers: per step a
+    # Born modelling (host dm in, host d out) and a migration (host d in, host g out)
+    E = args.e2e_steps if args.e2e_steps is not None else K
+    e2e = None
+    if E > 0:
+        dm_h = torch.empty(dm_true.shape, dtype=torch.float32, pin_memory=True)
+        dm_h.copy_(dm_true.cpu())
+        d_h = torch.empty((h.nrec_total, h.nt), dtype=torch.float32, pin_memory=True)
+        g_h = torch.empty((2,) + h.shape, dtype=torch.float32, pin_memory=True)
+        h.born(dm_h, out=d_h)
+        h.adjoint(d_h, out=g_h)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(E):
+            h.born(dm_h, out=d_h)
+            h.adjoint(d_h, out=g_h)
+        e1.record()
+        torch.cuda.synchronize()
+        te = torch.tensor([e0.elapsed_time(e1) / 1e3], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        te = float(te.item())
+        e2e = {"value": cells_per_step * E * world / te / 1e9, "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": int(dm_h.numel() * 4 + d_h.numel() * 4),
+               "d2h_bytes_per_step": int(d_h.numel() * 4 + g_h.numel() * 4),
+               "calls": "lsrtm_born + lsrtm_adjoint with pinned host buffers"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, threads, desc, _ = cpu_sample(w, args.cpu_seconds)
+        cpu = {"value": val, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "Born+migration Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": t_max / K * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": [w.nz, w.nx], "padded_cells": ncell,
+                       "nt": w.nt, "order": w.order, "shots_per_rank": nshot,
+                       "receivers_per_shot": int(w.geom.rec_ptr[1]), "bands": args.bands,
+                       "step": "one CGNR iteration (L + L^T + FP64 Krylov updates)",
+                       "s_per_lsrtm_iter": t_max / K,
+                       "l2": "inputs larger than L2 (state 4.6 GB + bands 37.7 GB per rank)",
+                       "parallelism": f"shots per rank, {world} rank(s), no data-path collective"},
+            "roofline": roofline, "per_operator": per_op, "clocks": clk,
+            "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

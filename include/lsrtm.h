@@ -1,0 +1,191 @@
+/*
+ * lsrtm.h — C ABI of the GB300 (sm_103a) multiparameter LSRTM operator library.
+ *
+ * The library applies the linearised Born modelling operator L and its exact
+ * transpose L^T for the first-order velocity-pressure acoustic system
+ * (Eq. 1: rho dv/dt + grad p = 0, kappa div v + dp/dt = f_p, kappa = rho Vp^2)
+ * on a staggered grid, parametrised by m = (dln Vp, dln Ip) through
+ * dln rho = dln Ip - dln Vp and dln kappa = dln Ip + dln Vp (Sec. 2), and
+ * drives them with CGNR (Sec. 3) and PSF probes (App. D).
+ *
+ * Conventions shared by every entry point
+ *   - Interior grid nz x (ny x) nx, x fastest; ny = 1 in 2D. A flat interior
+ *     index is (iz*ny + iy)*nx + ix.
+ *   - Models, perturbations and images are float32 arrays [nz][ny][nx]; a
+ *     two-parameter array is [2][nz][ny][nx] with plane 0 = dln Vp and plane 1
+ *     = dln Ip.
+ *   - Data are float32 [nrec_total][nt], receiver-major, contiguous in time;
+ *     receivers of shot s are rows rec_ptr[s] .. rec_ptr[s+1]-1. Sample n of a
+ *     receiver is the pressure after time step n (time (n+1)*dt).
+ *   - Array arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library detects host memory and stages it through its own
+ *     device buffers. Geometry arrays are host pointers. The caller owns all
+ *     arrays it passes; the library copies what it keeps.
+ *   - All device work is queued on the handle's stream; calls return once the
+ *     work is queued, except where a host result is returned (host output
+ *     pointers, misfit history), in which case the call synchronises the stream.
+ *   - Errors: every entry point returns an lsrtm_status; no exception crosses
+ *     the ABI. lsrtm_last_error() gives a thread-local description of the last
+ *     failure. Outputs are unspecified after an error.
+ *   - Outputs are overwritten, never accumulated into.
+ */
+#ifndef LSRTM_H
+#define LSRTM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSRTM_OK = 0,
+    LSRTM_ERR_ARG = 1,        /* invalid argument or configuration */
+    LSRTM_ERR_CFL = 2,        /* time step violates the stability limit */
+    LSRTM_ERR_GEOMETRY = 3,   /* source/receiver outside the interior grid */
+    LSRTM_ERR_OOM = 4,        /* workspace exceeds the HBM budget or cudaMalloc failed */
+    LSRTM_ERR_NONFINITE = 5,  /* NaN/Inf in an input or produced by a solve */
+    LSRTM_ERR_CUDA = 6,       /* a CUDA runtime call failed (message in last_error) */
+    LSRTM_ERR_STATE = 7       /* handle not usable for this call */
+} lsrtm_status;
+
+/* Band / checkpoint storage precision. */
+enum { LSRTM_BAND_FP32 = 0, LSRTM_BAND_BF16 = 1 };
+/* Source-wavefield reconstruction for L^T (App. A: the background field must
+ * be available in reverse time). */
+enum { LSRTM_RECON_BOUNDARY = 0,   /* boundary bands + reverse-time recomputation */
+       LSRTM_RECON_CHECKPOINT = 1, /* full-state checkpoints + forward recomputation */
+       LSRTM_RECON_AUTO = 2 };     /* boundary if it fits the budget, else checkpoints */
+/* Execution plan. */
+enum { LSRTM_PLAN_BATCHED = 0,     /* all shots of a batch per launch, CUDA graphs,
+                                      background bands cached across calls */
+       LSRTM_PLAN_PLAIN = 1 };     /* one shot per launch, no graph, background
+                                      recomputed inside every L^T (reference plan) */
+
+typedef struct {
+    int ndim;                /* 2 or 3 */
+    int nz, ny, nx;          /* interior grid (ny ignored in 2D) */
+    double dz, dy, dx;       /* grid spacing [m] */
+    double dt;               /* time step [s] */
+    int nt;                  /* number of time steps */
+    int fd_order;            /* 4 or 8: staggered Taylor order 2M */
+    int npml;                /* CPML thickness in cells (>= fd_order/2) on every side */
+    double f0;               /* dominant frequency [Hz]; sets the CPML alpha profile */
+    double pml_vmax;         /* velocity for the CPML damping; <= 0: max of vp */
+    int band_precision;      /* LSRTM_BAND_FP32 or LSRTM_BAND_BF16 */
+    size_t hbm_budget_bytes; /* workspace cap; 0 = no cap */
+    int recon_mode;          /* LSRTM_RECON_* */
+    int plan;                /* LSRTM_PLAN_* */
+    int shots_per_batch;     /* 0 = automatic */
+    int wavelet_per_shot;    /* 0: wavelet [nt] shared; 1: wavelet [nshot][nt] */
+} lsrtm_config;
+
+typedef struct {
+    int nshot;
+    const int *src_idx;  /* host [nshot]: flat interior index of each shot's source */
+    const int *rec_ptr;  /* host [nshot+1]: CSR offsets into rec_idx */
+    const int *rec_idx;  /* host [rec_ptr[nshot]]: flat interior receiver indices */
+} lsrtm_geometry;
+
+typedef struct lsrtm_handle lsrtm_handle;
+
+/* Creates an operator handle: validates the configuration (CFL limit
+ * dt <= 1 / (vmax sqrt(sum 1/h^2) sum|c_l|), geometry inside the interior),
+ * pads the model by edge replication, derives kappa = rho vp^2 and the
+ * staggered buoyancy (Eq. 1, Sec. 2), builds the CPML profiles and allocates
+ * the workspace within hbm_budget_bytes.
+ *   vp, rho : [nz][ny][nx] background velocity [m/s] and density [kg/m^3]
+ *   wavelet : [nt] (or [nshot][nt]) source samples w(n dt); step n adds
+ *             dt*w[n]/cell_volume to the pressure at the source node
+ *   stream  : cudaStream_t to run on (NULL = legacy default stream)
+ * The handle keeps copies; the caller may free its arrays afterwards. */
+lsrtm_status lsrtm_create(const lsrtm_config *cfg, const float *vp, const float *rho,
+                          const float *wavelet, const lsrtm_geometry *geom, void *stream,
+                          lsrtm_handle **out);
+
+/* Born modelling d = L dm (Eq. scattereqln with d = R dp, Sec. 3):
+ *   dm : [2][nz][ny][nx] (dln Vp, dln Ip), supported on the interior
+ *   d  : [nrec_total][nt] output */
+lsrtm_status lsrtm_born(lsrtm_handle *h, const float *dm, float *d);
+
+/* Migration g = L^T d: the exact transpose of lsrtm_born under the plain
+ * Euclidean inner products, i.e. the zero-lag cross-correlations of
+ * Eqs. (gradrho), (gradkappa) stacked over shots, mapped by the chain rule of
+ * Sec. 3 (g_Vp = g_kappa - g_rho, g_Ip = g_kappa + g_rho).
+ *   d           : [nrec_total][nt] input
+ *   g           : [2][nz][ny][nx] output
+ *   pseudo_hess : optional [nz][ny][nx] output of the pseudo-Hessian diagonal
+ *                 of App. B (shared by both parameters), or NULL */
+lsrtm_status lsrtm_adjoint(lsrtm_handle *h, const float *d, float *g, float *pseudo_hess);
+
+/* Point-spread-function probe of App. D: psf = L^T L comb, where comb holds
+ * unit spikes in plane `param` (0 = dln Vp, 1 = dln Ip) at every interior node
+ * whose coordinates are all spacing/2 + k*spacing.
+ *   psf : [2][nz][ny][nx] output */
+lsrtm_status lsrtm_psf(lsrtm_handle *h, int param, int spacing, float *psf);
+
+/* Remigration of App. E: out = L^T L m (m, out: [2][nz][ny][nx]). */
+lsrtm_status lsrtm_remigrate(lsrtm_handle *h, const float *m, float *out);
+
+/* Data-domain LSRTM (Sec. 3): CGNR on min ||L dm - d||^2, x0 = dm on entry,
+ * restricted to the planes in param_mask (1 = dln Vp, 2 = dln Ip, 3 = both).
+ * precond != 0 uses the diagonal pseudo-Hessian M = H + 1e-3 max(H) of App. B
+ * (computed once). Krylov scalars and inner products are FP64 on the device.
+ *   d      : [nrec_total][nt] observed data
+ *   dm     : [2][nz][ny][nx] in: starting model, out: solution after niter
+ *   misfit : host [niter+1] or NULL: ||d - L dm_k|| / ||d|| per iteration */
+lsrtm_status lsrtm_cg_solve(lsrtm_handle *h, const float *d, float *dm, int niter, int precond,
+                            int param_mask, double *misfit);
+
+/* Step-wise CGNR with the same algorithm as lsrtm_cg_solve:
+ * lsrtm_cg_begin computes r0 = d - L x0 and s0 = L^T r0 (x0 = NULL means 0),
+ * lsrtm_cg_iterate performs niter iterations (each one L, one L^T and the
+ * FP64 Krylov updates) and, if misfit is not NULL, synchronises and writes
+ * the normalised misfit after each of them (host [niter]);
+ * lsrtm_cg_result copies the current iterate to dm ([2][nz][ny][nx]) and,
+ * if misfit0 is not NULL, the misfit of x0. Only one solve per handle is
+ * active; lsrtm_cg_begin restarts it. */
+lsrtm_status lsrtm_cg_begin(lsrtm_handle *h, const float *d, const float *x0, int precond,
+                            int param_mask);
+lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit);
+lsrtm_status lsrtm_cg_result(lsrtm_handle *h, float *dm, double *misfit0);
+
+/* Device-time accounting of the time loops, measured with CUDA events on the
+ * library's own stream around each loop: born = fused background + Born
+ * forward loops, background = background-only loops (band saving), adjoint =
+ * reverse-time migration loops. launches = kernel launches those loops
+ * contain (one per time step per batch); cells = padded cells advanced. */
+typedef struct {
+    double born_ms, background_ms, adjoint_ms;
+    long long born_launches, background_launches, adjoint_launches;
+    double born_cells, background_cells, adjoint_cells;
+} lsrtm_timings;
+
+/* Enables (1) or disables (0) the event timing of lsrtm_timings. */
+lsrtm_status lsrtm_timing_enable(lsrtm_handle *h, int enable);
+
+/* Synchronises the handle's stream and returns the accumulated timings;
+ * reset != 0 clears them afterwards. */
+lsrtm_status lsrtm_timing_read(lsrtm_handle *h, lsrtm_timings *out, int reset);
+
+/* Replaces the stream used by later calls. */
+lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
+
+/* Bytes of device workspace the handle holds. */
+size_t lsrtm_workspace_bytes(const lsrtm_handle *h);
+
+/* Kernel launches issued by this handle since creation (graph replays count
+ * every kernel node they contain). */
+long long lsrtm_kernel_launches(const lsrtm_handle *h);
+
+/* Releases the handle and its workspace (NULL is ignored). */
+void lsrtm_destroy(lsrtm_handle *h);
+
+/* Thread-local description of the last error ("" if none). */
+const char *lsrtm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSRTM_H */

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of the C ABI in include/lsrtm.h.
+
+Argument marshalling only: every step of the operators runs in the CUDA
+library. Loading fails loudly if liblsrtm.so is missing or cannot be loaded;
+there is no CPU fallback.
+
+Arrays may be CUDA tensors (float32, contiguous) or host numpy / torch CPU
+arrays; results come back as CUDA tensors unless host output was requested.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_lib", "liblsrtm.so")
+
+LSRTM_OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CFL", 3: "ERR_GEOMETRY", 4: "ERR_OOM",
+          5: "ERR_NONFINITE", 6: "ERR_CUDA", 7: "ERR_STATE"}
+BAND_FP32, BAND_BF16 = 0, 1
+RECON_BOUNDARY, RECON_CHECKPOINT, RECON_AUTO = 0, 1, 2
+PLAN_BATCHED, PLAN_PLAIN = 0, 1
+
+# Every symbol include/lsrtm.h declares.
+EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_remigrate",
+           "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
+           "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
+           "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error"]
+
+
+class LsrtmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int), ("nx", ctypes.c_int),
+        ("dz", ctypes.c_double), ("dy", ctypes.c_double), ("dx", ctypes.c_double),
+        ("dt", ctypes.c_double), ("nt", ctypes.c_int), ("fd_order", ctypes.c_int),
+        ("npml", ctypes.c_int), ("f0", ctypes.c_double), ("pml_vmax", ctypes.c_double),
+        ("band_precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+        ("recon_mode", ctypes.c_int), ("plan", ctypes.c_int), ("shots_per_batch", ctypes.c_int),
+        ("wavelet_per_shot", ctypes.c_int),
+    ]
+
+
+class Timings(ctypes.Structure):
+    _fields_ = [("born_ms", ctypes.c_double), ("background_ms", ctypes.c_double),
+                ("adjoint_ms", ctypes.c_double), ("born_launches", ctypes.c_longlong),
+                ("background_launches", ctypes.c_longlong), ("adjoint_launches", ctypes.c_longlong),
+                ("born_cells", ctypes.c_double), ("background_cells", ctypes.c_double),
+                ("adjoint_cells", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GeometryC(ctypes.Structure):
+    _fields_ = [("nshot", ctypes.c_int), ("src_idx", ctypes.POINTER(ctypes.c_int)),
+                ("rec_ptr", ctypes.POINTER(ctypes.c_int)), ("rec_idx", ctypes.POINTER(ctypes.c_int))]
+
+
+_LIB = None
+
+
+def load_library(path: str | None = None):
+    """Loads liblsrtm.so (building it first if it is absent and nvcc exists)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or SO_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    L.lsrtm_create.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp,
+                               ctypes.POINTER(vp)]
+    L.lsrtm_born.argtypes = [vp, vp, vp]
+    L.lsrtm_adjoint.argtypes = [vp, vp, vp, vp]
+    L.lsrtm_psf.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    L.lsrtm_remigrate.argtypes = [vp, vp, vp]
+    L.lsrtm_cg_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_double)]
+    L.lsrtm_cg_begin.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int]
+    L.lsrtm_cg_iterate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.lsrtm_cg_result.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.lsrtm_timing_enable.argtypes = [vp, ctypes.c_int]
+    L.lsrtm_timing_read.argtypes = [vp, ctypes.POINTER(Timings), ctypes.c_int]
+    L.lsrtm_set_stream.argtypes = [vp, vp]
+    L.lsrtm_workspace_bytes.argtypes = [vp]
+    L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
+    L.lsrtm_kernel_launches.argtypes = [vp]
+    L.lsrtm_kernel_launches.restype = ctypes.c_longlong
+    L.lsrtm_destroy.argtypes = [vp]
+    L.lsrtm_destroy.restype = None
+    L.lsrtm_last_error.argtypes = []
+    L.lsrtm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy",
+                        "lsrtm_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(rc: int):
+    if rc != LSRTM_OK:
+        raise LsrtmError(rc, load_library().lsrtm_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (float32/int32, contiguous)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _f32(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32:
+            raise TypeError("expected float32")
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Lsrtm:
+    """Operator handle: L (born), L^T (adjoint), PSF, remigration, CGNR.
+
+    Parameters mirror lsrtm_config; `vp`, `rho` are [nz, (ny,) nx] arrays,
+    `wavelet` [nt] (or [nshot, nt]), geometry = (src_idx, rec_ptr, rec_idx)
+    flat interior indices. `stream` is a torch.cuda.Stream or raw handle
+    (default: torch's current stream)."""
+
+    def __init__(self, *, ndim, nz, nx, ny=1, dz, dx, dy=None, dt, nt, fd_order, npml, f0,
+                 vp, rho, wavelet, src_idx, rec_ptr, rec_idx, pml_vmax=None,
+                 band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_BOUNDARY,
+                 plan=PLAN_BATCHED, shots_per_batch=0, stream=None):
+        import torch
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        vp = _f32(vp)
+        rho = _f32(rho)
+        wav = _f32(wavelet)
+        if pml_vmax is None:
+            pml_vmax = float(vp.max())
+        self.cfg = Config(ndim, nz, ny if ndim == 3 else 1, nx, dz, dy or dx, dx, dt, nt,
+                          fd_order, npml, f0, float(pml_vmax), band_precision,
+                          int(hbm_budget_bytes), recon_mode, plan, shots_per_batch,
+                          1 if np.ndim(wavelet) == 2 else 0)
+        self._src = np.ascontiguousarray(src_idx, dtype=np.int32)
+        self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
+        self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int)
+        geo = GeometryC(len(self._src), self._src.ctypes.data_as(ip), self._rp.ctypes.data_as(ip),
+                        self._ri.ctypes.data_as(ip))
+        self.nshot = len(self._src)
+        self.nrec_total = int(self._rp[-1])
+        self.nt = nt
+        self.shape = (nz, nx) if ndim == 2 else (nz, ny, nx)
+        self.nint = int(np.prod(self.shape))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._stream = self._stream_handle(stream)
+        _check(self._lib.lsrtm_create(ctypes.byref(self.cfg), _ptr(vp), _ptr(rho), _ptr(wav),
+                                      ctypes.byref(geo), self._stream, ctypes.byref(self._h)))
+
+    @staticmethod
+    def _stream_handle(stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        if hasattr(stream, "cuda_stream"):
+            return ctypes.c_void_p(stream.cuda_stream)
+        return ctypes.c_void_p(stream)
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        """Handle for an lsrtm_inputs.Workload."""
+        return cls(ndim=w.ndim, nz=w.nz, ny=w.ny, nx=w.nx, dz=w.dz, dy=w.dy, dx=w.dx, dt=w.dt,
+                   nt=w.nt, fd_order=w.order, npml=w.npml, f0=w.f0, vp=w.vp, rho=w.rho,
+                   wavelet=w.wavelet, src_idx=w.geom.src_idx, rec_ptr=w.geom.rec_ptr,
+                   rec_idx=w.geom.rec_idx, **kw)
+
+    # -- helpers
+    def _empty(self, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.float32, device=self.device)
+
+    def _sync_stream(self):
+        _check(self._lib.lsrtm_set_stream(self._h, self._stream_handle(None)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        return int(self._lib.lsrtm_workspace_bytes(self._h))
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.lsrtm_kernel_launches(self._h))
+
+    # -- operators
+    def born(self, dm, out=None):
+        """d = L dm: dm [2, *shape] -> d [nrec_total, nt]."""
+        self._sync_stream()
+        dm = _f32(dm)
+        out = self._empty((self.nrec_total, self.nt)) if out is None else out
+        _check(self._lib.lsrtm_born(self._h, _ptr(dm), _ptr(out)))
+        return out
+
+    def adjoint(self, d, out=None, pseudo_hessian=False):
+        """g = L^T d: d [nrec_total, nt] -> g [2, *shape] (and the pseudo-Hessian)."""
+        self._sync_stream()
+        d = _f32(d)
+        out = self._empty((2,) + self.shape) if out is None else out
+        ph = self._empty(self.shape) if pseudo_hessian else None
+        _check(self._lib.lsrtm_adjoint(self._h, _ptr(d), _ptr(out),
+                                       _ptr(ph) if ph is not None else None))
+        return (out, ph) if pseudo_hessian else out
+
+    def psf(self, param, spacing, out=None):
+        """PSF = L^T L comb (comb: unit spikes every `spacing` in plane `param`)."""
+        self._sync_stream()
+        out = self._empty((2,) + self.shape) if out is None else out
+        _check(self._lib.lsrtm_psf(self._h, int(param), int(spacing), _ptr(out)))
+        return out
+
+    def remigrate(self, m, out=None):
+        """m'' = L^T L m."""
+        self._sync_stream()
+        m = _f32(m)
+        out = self._empty((2,) + self.shape) if out is None else out
+        _check(self._lib.lsrtm_remigrate(self._h, _ptr(m), _ptr(out)))
+        return out
+
+    def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3):
+        """CGNR / PCGNR; returns (dm, misfit history of length niter+1)."""
+        import torch
+        self._sync_stream()
+        d = _f32(d)
+        x = torch.zeros((2,) + self.shape, dtype=torch.float32, device=self.device) \
+            if x0 is None else _f32(x0).clone()
+        mis = (ctypes.c_double * (niter + 1))()
+        _check(self._lib.lsrtm_cg_solve(self._h, _ptr(d), _ptr(x), int(niter), int(bool(precond)),
+                                        int(param_mask), mis))
+        return x, np.array(list(mis))
+
+    def cg_begin(self, d, x0=None, precond=False, param_mask=3):
+        """Starts a step-wise CGNR solve (r0 = d - L x0, s0 = L^T r0)."""
+        self._sync_stream()
+        d = _f32(d)
+        self._cg_keep = (d, None if x0 is None else _f32(x0))
+        _check(self._lib.lsrtm_cg_begin(self._h, _ptr(d),
+                                        None if x0 is None else _ptr(self._cg_keep[1]),
+                                        int(bool(precond)), int(param_mask)))
+
+    def cg_iterate(self, niter=1, misfit=False):
+        """Runs niter CGNR iterations; returns their misfits if misfit=True."""
+        self._sync_stream()
+        if misfit:
+            mis = (ctypes.c_double * max(niter, 1))()
+            _check(self._lib.lsrtm_cg_iterate(self._h, int(niter), mis))
+            return np.array(list(mis))[:niter]
+        _check(self._lib.lsrtm_cg_iterate(self._h, int(niter), None))
+        return None
+
+    def cg_result(self):
+        """Current CGNR iterate [2, *shape] and the misfit of x0."""
+        self._sync_stream()
+        x = self._empty((2,) + self.shape)
+        m0 = ctypes.c_double()
+        _check(self._lib.lsrtm_cg_result(self._h, _ptr(x), ctypes.byref(m0)))
+        return x, float(m0.value)
+
+    def timing(self, enable=True):
+        _check(self._lib.lsrtm_timing_enable(self._h, int(bool(enable))))
+
+    def timings(self, reset=False) -> dict:
+        t = Timings()
+        _check(self._lib.lsrtm_timing_read(self._h, ctypes.byref(t), int(bool(reset))))
+        return t.as_dict()
+
+    def close(self):
+        if self._h:
+            self._lib.lsrtm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def born_op():
+    """torch.autograd.Function whose forward is L and backward is L^T, both
+    in the CUDA library: BornOp.apply(dm, handle) -> d."""
+    import torch
+
+    class BornOp(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, dm, handle):
+            ctx.handle = handle
+            return handle.born(dm.detach())
+
+        @staticmethod
+        def backward(ctx, grad_d):
+            return ctx.handle.adjoint(grad_d.contiguous()), None
+
+    return BornOp

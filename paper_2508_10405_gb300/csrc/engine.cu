@@ -1,0 +1,1031 @@
+// Host engine and C ABI of the LSRTM operator library (see include/lsrtm.h).
+//
+// The engine validates the configuration, lays the padded model and the
+// per-shot wavefield slots out in HBM, groups shots into batches that one
+// launch advances together, captures each batch's nt-step loop in a CUDA
+// graph, caches the background boundary bands across L^T calls, and runs
+// the CGNR driver with FP64 device scalars. All device work runs on a private
+// stream ordered after and before the caller's stream by events.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lsrtm.h"
+#include "lsrtm_internal.cuh"
+
+using namespace lsrtm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lsrtm_status fail(lsrtm_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(LSRTM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CHECK(expr)                            \
+    do {                                       \
+        lsrtm_status s_ = (expr);              \
+        if (s_ != LSRTM_OK) return s_;         \
+    } while (0)
+
+// Planes per wavefield slot: 10 ping-pong planes (forward: p v psi_p for the
+// background and the scattered field; adjoint: background p v, lambda p v and
+// the four lambda CPML memories), 4 in-place node CPML planes (forward).
+constexpr int kStatePlanes2D = 10;
+constexpr int kPsivPlanes2D = 4;
+
+enum GraphKind { G_BORN = 0, G_BG = 1, G_BG_HESS = 2, G_ADJ = 3 };
+
+}  // namespace
+
+struct lsrtm_handle {
+    lsrtm_config cfg{};
+    GridDev g{};
+    cudaStream_t user = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int nshot = 0;
+    long long nrec_total = 0;
+    long long nint = 0;
+    std::vector<int> rec_ptr;
+    // device model and geometry
+    float *kdt = nullptr, *binv = nullptr, *dkdt = nullptr, *rr = nullptr;
+    float *pml_buf = nullptr;
+    Pml pml{};
+    float *wav = nullptr;
+    int *src_cell = nullptr;
+    int *trec_ptr = nullptr;
+    int2 *trec = nullptr;
+    TileRecs trv{};
+    float src_scale = 0.f;
+    // wavefield slots
+    int batch = 1;
+    float *st[2] = {nullptr, nullptr};
+    long long sstride = 0;
+    float *psiv = nullptr;
+    long long vstride = 0;
+    float2 *img = nullptr;
+    double2 *img_acc = nullptr;
+    float *hess = nullptr;
+    double *hess_acc = nullptr;
+    float *hess_img = nullptr;
+    bool hess_ready = false;
+    // background cache
+    Bands bands{};
+    void *band_mem = nullptr;
+    float *final_state = nullptr;
+    bool bg_cached = false;
+    // staging
+    float *dstage = nullptr;     // [nrec_total][nt]
+    float *mstage = nullptr;     // [2][nint]
+    float *gstage = nullptr;     // [2][nint]
+    float *scratch1 = nullptr;   // [nint]
+    // Krylov
+    float *cg_x = nullptr, *cg_s = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_minv = nullptr;
+    float *cg_r = nullptr;
+    double *scal = nullptr;      // device scalars: [0] gamma [1] gamma_new [2] <q,q> [3] <d,d> [5] 1.0
+    double *dotwork = nullptr;
+    double *mis_dev = nullptr;   // per-iteration <r,r>
+    int mis_cap = 0;
+    float *fscal = nullptr;      // device float scalars
+    int *flag = nullptr;
+    // CGNR state
+    bool cg_active = false;
+    int cg_mask = 3, cg_precond = 0, cg_iter = 0;
+    // event timing of the time loops (kind: 0 born, 1 background, 2 adjoint)
+    bool timing = false;
+    struct TimedLoop {
+        int kind;
+        cudaEvent_t a, b;
+        long long launches;
+        double cells;
+    };
+    std::vector<TimedLoop> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double t_ms[3] = {0, 0, 0};
+    long long t_launch[3] = {0, 0, 0};
+    double t_cells[3] = {0, 0, 0};
+    // graphs
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    long long launches = 0;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+lsrtm_status dalloc(lsrtm_handle *h, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (h->cfg.hbm_budget_bytes && h->bytes + bytes > h->cfg.hbm_budget_bytes)
+        return fail(LSRTM_ERR_OOM, "workspace exceeds hbm_budget_bytes");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LSRTM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    h->bytes += bytes;
+    cudaError_t e2 = cudaMemsetAsync(*p, 0, bytes, h->work);
+    if (e2 != cudaSuccess) return fail(LSRTM_ERR_CUDA, cudaGetErrorString(e2));
+    return LSRTM_OK;
+}
+
+template <class T>
+lsrtm_status dalloc_t(lsrtm_handle *h, T **p, size_t count)
+{
+    return dalloc(h, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Makes `src` usable on the device: returns it as is if it is device memory,
+// else copies it into `stage` on the work stream.
+lsrtm_status stage_in(lsrtm_handle *h, const float *src, float *stage, size_t count,
+                      const float **dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return LSRTM_OK;
+    }
+    CU(cudaMemcpyAsync(stage, src, count * sizeof(float), cudaMemcpyHostToDevice, h->work));
+    *dev = stage;
+    return LSRTM_OK;
+}
+
+lsrtm_status copy_out(lsrtm_handle *h, float *dst, const float *src, size_t count)
+{
+    CU(cudaMemcpyAsync(dst, src, count * sizeof(float), cudaMemcpyDefault, h->work));
+    return LSRTM_OK;
+}
+
+// Orders the private work stream after everything queued on the caller's stream.
+lsrtm_status begin_call(lsrtm_handle *h)
+{
+    g_last_error.clear();
+    CU(cudaEventRecord(h->ev_in, h->user));
+    CU(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    return LSRTM_OK;
+}
+
+// Orders the caller's stream after the work queued by this call.
+lsrtm_status end_call(lsrtm_handle *h, bool sync)
+{
+    CU(cudaGetLastError());
+    CU(cudaEventRecord(h->ev_out, h->work));
+    CU(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    if (sync) CU(cudaStreamSynchronize(h->work));
+    return LSRTM_OK;
+}
+
+// Staggered Taylor coefficients of order 2M (closed forms).
+void fd_coeffs(int M, double *c)
+{
+    if (M == 2) {
+        c[0] = 9.0 / 8.0;
+        c[1] = -1.0 / 24.0;
+    } else {
+        c[0] = 1225.0 / 1024.0;
+        c[1] = -245.0 / 3072.0;
+        c[2] = 49.0 / 5120.0;
+        c[3] = -5.0 / 7168.0;
+    }
+}
+
+// CPML profile: damping d0 (r)^2, alpha = pi f0 (1 - r), r = distance beyond
+// the interface half node / npml; zero (no memory) at and inside the interface.
+void cpml_profile(int N, int o, int n, int npml, double h, double vmax, double f0, double dt,
+                  float *ai, float *bi, float *ah, float *bh)
+{
+    const double pi = 3.14159265358979323846;
+    double d0 = npml > 0 ? -3.0 * vmax * std::log(1e-4) / (2.0 * npml * h) : 0.0;
+    auto coef = [&](double dist, float *a, float *b) {
+        if (dist <= 0.0) {
+            *a = 0.f;
+            *b = 0.f;
+            return;
+        }
+        double r = dist / npml;
+        double d = d0 * r * r;
+        double al = pi * f0 * (1.0 - r);
+        if (al < 0) al = 0;
+        double bb = std::exp(-(d + al) * dt);
+        *b = (float)bb;
+        *a = (float)(d * (bb - 1.0) / (d + al));
+    };
+    double lo = o - 0.5, hi = o + n - 0.5;
+    for (int i = 0; i < N; ++i) {
+        double di = std::max(0.0, std::max(lo - i, i - hi));
+        double dh = std::max(0.0, std::max(lo - (i + 0.5), (i + 0.5) - hi));
+        coef(di, &ai[i], &bi[i]);
+        coef(dh, &ah[i], &bh[i]);
+    }
+}
+
+Step2D step_args(lsrtm_handle *h, int shot0)
+{
+    Step2D a{};
+    a.g = h->g;
+    a.pml = h->pml;
+    a.kdt = h->kdt;
+    a.binv = h->binv;
+    a.dkdt = h->dkdt;
+    a.rr = h->rr;
+    a.psiv = h->psiv;
+    a.sstride = h->sstride;
+    a.vstride = h->vstride;
+    a.shot0 = shot0;
+    a.wav = h->wav;
+    a.wav_per_shot = h->cfg.wavelet_per_shot;
+    a.src_cell = h->src_cell;
+    a.src_scale = h->src_scale;
+    a.trec = h->trv;
+    a.dstage = h->dstage;
+    a.bands = h->bands;
+    a.hess = h->hess;
+    a.img = h->img;
+    return a;
+}
+
+bool use_graphs(const lsrtm_handle *h) { return h->cfg.plan == LSRTM_PLAN_BATCHED; }
+
+cudaEvent_t take_event(lsrtm_handle *h)
+{
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+int timing_kind(int graph_kind)
+{
+    return graph_kind == G_BORN ? 0 : (graph_kind == G_ADJ ? 2 : 1);
+}
+
+// Runs `body` (which enqueues the nt-step loop of one batch on h->work),
+// captured once into a CUDA graph per (kind, batch) and replayed afterwards.
+template <class F>
+lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
+{
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (h->timing) {
+        ea = take_event(h);
+        eb = take_event(h);
+        if (ea) CU(cudaEventRecord(ea, h->work));
+    }
+    if (!use_graphs(h)) {
+        CHECK(body());
+    } else {
+        auto key = std::make_pair(kind, shot0);
+        auto it = h->graphs.find(key);
+        cudaGraphExec_t exec;
+        if (it == h->graphs.end()) {
+            CU(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
+            lsrtm_status s = body();
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->work, &graph);
+            if (s != LSRTM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (e != cudaSuccess) return fail(LSRTM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return fail(LSRTM_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+            h->graphs[key] = exec;
+        } else {
+            exec = it->second;
+        }
+        CU(cudaGraphLaunch(exec, h->work));
+    }
+    h->launches += h->g.nt;
+    if (h->timing && ea && eb) {
+        CU(cudaEventRecord(eb, h->work));
+        double cells = (double)bs * h->g.Nz * h->g.Ny * h->g.Nx * h->g.nt;
+        h->pending.push_back({timing_kind(kind), ea, eb, (long long)h->g.nt, cells});
+    } else {
+        if (ea) h->event_pool.push_back(ea);
+        if (eb) h->event_pool.push_back(eb);
+    }
+    return LSRTM_OK;
+}
+
+int batch_size(const lsrtm_handle *h, int shot0) { return std::min(h->batch, h->nshot - shot0); }
+
+lsrtm_status zero_slots(lsrtm_handle *h, int bs)
+{
+    size_t sb = (size_t)bs * h->sstride * sizeof(float);
+    CU(cudaMemsetAsync(h->st[0], 0, sb, h->work));
+    CU(cudaMemsetAsync(h->st[1], 0, sb, h->work));
+    CU(cudaMemsetAsync(h->psiv, 0, (size_t)bs * h->vstride * sizeof(float), h->work));
+    return LSRTM_OK;
+}
+
+// Background forward pass over all shots: saves the boundary bands of p and
+// the normal velocity every step and the final state (p^{nt-1}, v^{nt-1/2});
+// optionally accumulates the pseudo-Hessian diagonal.
+lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
+{
+    const long long plane = h->g.plane;
+    const int nt = h->g.nt;
+    if (hess) CU(cudaMemsetAsync(h->hess_acc, 0, h->nint * sizeof(double), h->work));
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
+        int bs = batch_size(h, s0);
+        CHECK(zero_slots(h, bs));
+        if (hess) CU(cudaMemsetAsync(h->hess, 0, (size_t)bs * plane * sizeof(float), h->work));
+        CHECK(run_loop(h, hess ? G_BG_HESS : G_BG, s0, bs, [&]() -> lsrtm_status {
+            Step2D a = step_args(h, s0);
+            for (int n = 0; n < nt; ++n) {
+                a.n = n;
+                a.in = h->st[n & 1];
+                a.out = h->st[(n + 1) & 1];
+                CU(launch_fwd2d(a, bs, false, true, hess, h->work));
+            }
+            return LSRTM_OK;
+        }));
+        // final state: p^{nt-1} is the input of the last step, v^{nt-1/2} its output
+        const float *pin = h->st[(nt - 1) & 1];
+        const float *vout = h->st[nt & 1];
+        for (int s = 0; s < bs; ++s) {
+            float *fs = h->final_state + (size_t)(s0 + s) * 3 * plane;
+            CU(cudaMemcpyAsync(fs, pin + s * h->sstride, plane * sizeof(float), cudaMemcpyDeviceToDevice, h->work));
+            CU(cudaMemcpyAsync(fs + plane, vout + s * h->sstride + 1 * plane, 2 * plane * sizeof(float),
+                               cudaMemcpyDeviceToDevice, h->work));
+        }
+        if (hess) {
+            CU(launch_hess_accumulate(h->g, h->hess, bs, h->hess_acc, h->work));
+            h->launches++;
+        }
+    }
+    if (hess) {
+        CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+        h->launches++;
+        h->hess_ready = true;
+    }
+    h->bg_cached = true;
+    return LSRTM_OK;
+}
+
+// Born modelling of the perturbation already prepared in h->dkdt / h->rr;
+// records go to h->dstage.
+lsrtm_status born_core(lsrtm_handle *h)
+{
+    const int nt = h->g.nt;
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
+        int bs = batch_size(h, s0);
+        CHECK(zero_slots(h, bs));
+        CHECK(run_loop(h, G_BORN, s0, bs, [&]() -> lsrtm_status {
+            Step2D a = step_args(h, s0);
+            for (int n = 0; n < nt; ++n) {
+                a.n = n;
+                a.in = h->st[n & 1];
+                a.out = h->st[(n + 1) & 1];
+                CU(launch_fwd2d(a, bs, true, false, false, h->work));
+            }
+            return LSRTM_OK;
+        }));
+    }
+    return LSRTM_OK;
+}
+
+// L^T of the data in h->dstage; stacked images into h->img_acc, then the
+// chain rule into gout ([2][nint], device).
+lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
+{
+    const long long plane = h->g.plane;
+    const int nt = h->g.nt;
+    if (!h->bg_cached || h->cfg.plan == LSRTM_PLAN_PLAIN || (want_hess && !h->hess_ready))
+        CHECK(bg_forward(h, want_hess && !h->hess_ready));
+    CU(cudaMemsetAsync(h->img_acc, 0, h->nint * sizeof(double2), h->work));
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
+        int bs = batch_size(h, s0);
+        CHECK(zero_slots(h, bs));
+        CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
+        for (int s = 0; s < bs; ++s) {
+            const float *fs = h->final_state + (size_t)(s0 + s) * 3 * plane;
+            CU(cudaMemcpyAsync(h->st[0] + s * h->sstride, fs, 3 * plane * sizeof(float),
+                               cudaMemcpyDeviceToDevice, h->work));
+        }
+        CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1, h->st[0] + 3 * plane,
+                                  h->sstride, h->work));
+        h->launches++;
+        CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
+            Step2D a = step_args(h, s0);
+            for (int i = 0; i < nt; ++i) {
+                a.n = nt - 1 - i;
+                a.in = h->st[i & 1];
+                a.out = h->st[(i + 1) & 1];
+                CU(launch_adj2d(a, bs, h->work));
+            }
+            return LSRTM_OK;
+        }));
+        CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
+        h->launches++;
+    }
+    CU(launch_image_finalize(h->g, h->img_acc, h->kdt, h->binv, gout, h->work));
+    h->launches++;
+    return LSRTM_OK;
+}
+
+lsrtm_status prep_perturbation(lsrtm_handle *h, const float *dm_dev)
+{
+    CU(launch_pert_prep(h->g, dm_dev, h->kdt, h->binv, h->dkdt, h->rr, h->work));
+    h->launches++;
+    return LSRTM_OK;
+}
+
+lsrtm_status check_finite(lsrtm_handle *h, const float *x, long long n, const char *what)
+{
+    CU(cudaMemsetAsync(h->flag, 0, sizeof(int), h->work));
+    CU(launch_nonfinite_count(x, n, h->flag, h->work));
+    h->launches++;
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+    CU(cudaStreamSynchronize(h->work));
+    if (flag) return fail(LSRTM_ERR_NONFINITE, std::string("non-finite values in ") + what);
+    return LSRTM_OK;
+}
+
+lsrtm_status validate_cfg(const lsrtm_config *c)
+{
+    if (!c) return fail(LSRTM_ERR_ARG, "null config");
+    if (c->ndim != 2)
+        return fail(LSRTM_ERR_ARG, "ndim must be 2 (the 3D kernels are not part of this build)");
+    if (c->fd_order != 4 && c->fd_order != 8) return fail(LSRTM_ERR_ARG, "fd_order must be 4 or 8");
+    if (c->nz < 1 || c->nx < 1 || c->nt < 1) return fail(LSRTM_ERR_ARG, "empty grid or nt < 1");
+    if (c->npml < c->fd_order / 2) return fail(LSRTM_ERR_ARG, "npml must be >= fd_order/2");
+    if (!(c->dt > 0) || !(c->dx > 0) || !(c->dz > 0)) return fail(LSRTM_ERR_ARG, "non-positive spacing or dt");
+    if (c->band_precision != LSRTM_BAND_FP32 && c->band_precision != LSRTM_BAND_BF16)
+        return fail(LSRTM_ERR_ARG, "band_precision must be 0 (fp32) or 1 (bf16)");
+    if (c->recon_mode != LSRTM_RECON_BOUNDARY && c->recon_mode != LSRTM_RECON_AUTO)
+        return fail(LSRTM_ERR_ARG, "only boundary-band reconstruction is available");
+    if (c->plan != LSRTM_PLAN_BATCHED && c->plan != LSRTM_PLAN_PLAIN)
+        return fail(LSRTM_ERR_ARG, "unknown plan");
+    if (c->shots_per_batch < 0) return fail(LSRTM_ERR_ARG, "shots_per_batch < 0");
+    return LSRTM_OK;
+}
+
+lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
+{
+    const GridDev &g = h->g;
+    if (!geo || geo->nshot < 1 || !geo->src_idx || !geo->rec_ptr || (!geo->rec_idx && geo->rec_ptr[geo->nshot] > 0))
+        return fail(LSRTM_ERR_ARG, "invalid geometry");
+    h->nshot = geo->nshot;
+    if (geo->rec_ptr[0] != 0) return fail(LSRTM_ERR_GEOMETRY, "rec_ptr[0] must be 0");
+    for (int s = 0; s < h->nshot; ++s)
+        if (geo->rec_ptr[s + 1] < geo->rec_ptr[s]) return fail(LSRTM_ERR_GEOMETRY, "rec_ptr not monotone");
+    h->nrec_total = geo->rec_ptr[h->nshot];
+    h->rec_ptr.assign(geo->rec_ptr, geo->rec_ptr + h->nshot + 1);
+    auto pad_cell = [&](long long k) {
+        long long ix = k % g.nx, t = k / g.nx, iy = t % g.ny, iz = t / g.ny;
+        return (iz + g.z0) * g.rowz + (iy + g.y0) * g.pitch + (ix + g.x0);
+    };
+    std::vector<int> src(h->nshot);
+    for (int s = 0; s < h->nshot; ++s) {
+        long long k = geo->src_idx[s];
+        if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "source outside the interior grid");
+        src[s] = (int)pad_cell(k);
+    }
+    int ntx = (g.Nx + kTX2 - 1) / kTX2, ntz = (g.Nz + kTZ2 - 1) / kTZ2;
+    int ntiles = ntx * ntz;
+    std::vector<std::vector<int2>> lists((size_t)h->nshot * ntiles);
+    for (int s = 0; s < h->nshot; ++s)
+        for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
+            long long k = geo->rec_idx[r];
+            if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
+            long long cell = pad_cell(k);
+            int z = (int)(cell / g.rowz), x = (int)(cell % g.pitch);
+            int t = (z / kTZ2) * ntx + x / kTX2;
+            lists[(size_t)s * ntiles + t].push_back(make_int2((int)cell, r));
+        }
+    std::vector<int> ptr(lists.size() + 1, 0);
+    std::vector<int2> flat;
+    flat.reserve(h->nrec_total);
+    for (size_t i = 0; i < lists.size(); ++i) {
+        auto &L = lists[i];
+        std::stable_sort(L.begin(), L.end(), [](int2 a, int2 b) { return a.x < b.x; });
+        flat.insert(flat.end(), L.begin(), L.end());
+        ptr[i + 1] = (int)flat.size();
+    }
+    CHECK(dalloc_t(h, &h->src_cell, src.size()));
+    CHECK(dalloc_t(h, &h->trec_ptr, ptr.size()));
+    CHECK(dalloc_t(h, &h->trec, std::max<size_t>(flat.size(), 1)));
+    CU(cudaMemcpyAsync(h->src_cell, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+    CU(cudaMemcpyAsync(h->trec_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+    if (!flat.empty())
+        CU(cudaMemcpyAsync(h->trec, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice, h->work));
+    CU(cudaStreamSynchronize(h->work));
+    h->trv.ptr = h->trec_ptr;
+    h->trv.rec = h->trec;
+    h->trv.ntiles = ntiles;
+    return LSRTM_OK;
+}
+
+lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *rho,
+                         const float *wavelet, const lsrtm_geometry *geo, void *stream,
+                         lsrtm_handle *h)
+{
+    CHECK(validate_cfg(cfg));
+    h->cfg = *cfg;
+    h->user = (cudaStream_t)stream;
+    CU(cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CU(cudaEventRecord(h->ev_in, h->user));
+    CU(cudaStreamWaitEvent(h->work, h->ev_in, 0));
+    static bool configured = false;
+    if (!configured) {
+        CU(configure_2d_kernels());
+        configured = true;
+    }
+
+    GridDev &g = h->g;
+    g.ndim = cfg->ndim;
+    g.M = cfg->fd_order / 2;
+    g.nz = cfg->nz;
+    g.ny = 1;
+    g.nx = cfg->nx;
+    g.z0 = cfg->npml;
+    g.y0 = 0;
+    g.x0 = cfg->npml;
+    g.Nz = g.nz + 2 * cfg->npml;
+    g.Ny = 1;
+    g.Nx = g.nx + 2 * cfg->npml;
+    g.pitch = (g.Nx + 31) / 32 * 32;
+    g.rowz = (long long)g.Ny * g.pitch;
+    g.plane = (long long)g.Nz * g.rowz;
+    g.dt = (float)cfg->dt;
+    g.nt = cfg->nt;
+    double c[4];
+    fd_coeffs(g.M, c);
+    for (int l = 0; l < kMaxM; ++l) {
+        double cl = l < g.M ? c[l] : 0.0;
+        g.cz[l] = (float)(cl / cfg->dz);
+        g.cy[l] = (float)(cl / (cfg->dy > 0 ? cfg->dy : 1.0));
+        g.cx[l] = (float)(cl / cfg->dx);
+    }
+    h->nint = (long long)g.nz * g.ny * g.nx;
+    h->src_scale = (float)(cfg->dt / (cfg->dz * cfg->dx));
+
+    // model on the device
+    CHECK(dalloc_t(h, &h->scratch1, 2 * h->nint));
+    const float *vp_d, *rho_d;
+    CHECK(stage_in(h, vp, h->scratch1, h->nint, &vp_d));
+    CHECK(stage_in(h, rho, h->scratch1 + h->nint, h->nint, &rho_d));
+    CHECK(dalloc_t(h, &h->flag, 4));
+    CHECK(check_finite(h, vp_d, h->nint, "vp"));
+    CHECK(check_finite(h, rho_d, h->nint, "rho"));
+    CHECK(dalloc_t(h, &h->fscal, 8));
+    double vmax = cfg->pml_vmax;
+    if (!(vmax > 0)) {
+        CU(launch_max_abs_reduce(vp_d, h->nint, h->fscal, h->work));
+        float vm = 0.f;
+        CU(cudaMemcpyAsync(&vm, h->fscal, sizeof(float), cudaMemcpyDeviceToHost, h->work));
+        CU(cudaStreamSynchronize(h->work));
+        vmax = vm;
+    }
+    {
+        double s = 0.0, inv2 = 1.0 / (cfg->dz * cfg->dz) + 1.0 / (cfg->dx * cfg->dx);
+        for (int l = 0; l < g.M; ++l) s += std::fabs(c[l]);
+        double lim = 1.0 / (vmax * std::sqrt(inv2) * s);
+        if (!(cfg->dt < lim)) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "dt = %g exceeds the stability limit %g", cfg->dt, lim);
+            return fail(LSRTM_ERR_CFL, buf);
+        }
+    }
+    CHECK(dalloc_t(h, &h->kdt, g.plane));
+    CHECK(dalloc_t(h, &h->binv, g.plane));
+    CHECK(dalloc_t(h, &h->dkdt, g.plane));
+    CHECK(dalloc_t(h, &h->rr, g.plane));
+    CU(launch_model_prep(g, vp_d, rho_d, h->kdt, h->binv, h->work));
+    h->launches++;
+
+    // CPML profiles: per direction ai bi ah bh
+    {
+        int N[3] = {g.Nz, g.Ny, g.Nx};
+        int o[3] = {g.z0, g.y0, g.x0};
+        int ni[3] = {g.nz, g.ny, g.nx};
+        double hh[3] = {cfg->dz, cfg->dy, cfg->dx};
+        size_t tot = 4 * ((size_t)N[0] + N[1] + N[2]);
+        std::vector<float> prof(tot, 0.f);
+        CHECK(dalloc_t(h, &h->pml_buf, tot));
+        size_t off = 0;
+        for (int d = 0; d < 3; ++d) {
+            float *b = prof.data() + off;
+            if (!(d == 1 && g.ndim == 2))
+                cpml_profile(N[d], o[d], ni[d], cfg->npml, hh[d], vmax, cfg->f0, cfg->dt, b, b + N[d],
+                             b + 2 * N[d], b + 3 * N[d]);
+            h->pml.ai[d] = h->pml_buf + off;
+            h->pml.bi[d] = h->pml_buf + off + N[d];
+            h->pml.ah[d] = h->pml_buf + off + 2 * N[d];
+            h->pml.bh[d] = h->pml_buf + off + 3 * N[d];
+            off += 4 * (size_t)N[d];
+        }
+        CU(cudaMemcpyAsync(h->pml_buf, prof.data(), tot * sizeof(float), cudaMemcpyHostToDevice, h->work));
+        CU(cudaStreamSynchronize(h->work));
+    }
+
+    CHECK(build_geometry(h, geo));
+    size_t nw = (size_t)(cfg->wavelet_per_shot ? h->nshot : 1) * g.nt;
+    CHECK(dalloc_t(h, &h->wav, nw));
+    CU(cudaMemcpyAsync(h->wav, wavelet, nw * sizeof(float), cudaMemcpyDefault, h->work));
+
+    // staging and Krylov vectors
+    long long nd = h->nrec_total * g.nt;
+    CHECK(dalloc_t(h, &h->dstage, std::max<long long>(nd, 1)));
+    CHECK(dalloc_t(h, &h->mstage, 2 * h->nint));
+    CHECK(dalloc_t(h, &h->gstage, 2 * h->nint));
+    CHECK(dalloc_t(h, &h->img_acc, h->nint));
+    CHECK(dalloc_t(h, &h->hess_acc, h->nint));
+    CHECK(dalloc_t(h, &h->hess_img, h->nint));
+    CHECK(dalloc_t(h, &h->scal, 16));
+    {
+        const double one = 1.0;
+        CU(cudaMemcpyAsync(h->scal + 5, &one, sizeof(double), cudaMemcpyHostToDevice, h->work));
+        CU(cudaStreamSynchronize(h->work));
+    }
+    CHECK(dalloc_t(h, &h->dotwork, 152 * 4 + 32));
+
+    // bands and final states for every shot
+    h->bands.nb = 2LL * g.M * (g.nz + g.nx);
+    h->bands.bf16 = (cfg->plan == LSRTM_PLAN_BATCHED && cfg->band_precision == LSRTM_BAND_BF16) ? 1 : 0;
+    size_t esz = h->bands.bf16 ? 2 : 4;
+    size_t band_bytes = (size_t)h->nshot * g.nt * h->bands.nb * esz;
+    CHECK(dalloc(h, &h->band_mem, 2 * band_bytes));
+    h->bands.p = h->band_mem;
+    h->bands.v = static_cast<char *>(h->band_mem) + band_bytes;
+    CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * 3 * g.plane));
+
+    // wavefield slots: as many shots per batch as the budget allows
+    h->sstride = kStatePlanes2D * g.plane;
+    h->vstride = kPsivPlanes2D * g.plane;
+    size_t per_slot = (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
+    int batch = cfg->plan == LSRTM_PLAN_PLAIN ? 1 : (cfg->shots_per_batch > 0 ? cfg->shots_per_batch : h->nshot);
+    batch = std::min(batch, h->nshot);
+    size_t cg_bytes = (5 * 2 * (size_t)h->nint + (size_t)nd) * sizeof(float);
+    if (cfg->hbm_budget_bytes) {
+        long long room = (long long)cfg->hbm_budget_bytes - (long long)h->bytes - (long long)cg_bytes;
+        long long fit = room > 0 ? room / (long long)per_slot : 0;
+        if (fit < 1) return fail(LSRTM_ERR_OOM, "hbm_budget_bytes too small for one wavefield slot");
+        if (fit < batch) batch = (int)fit;
+    }
+    h->batch = batch;
+    CHECK(dalloc_t(h, &h->st[0], (size_t)batch * h->sstride));
+    CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride));
+    CHECK(dalloc_t(h, &h->psiv, (size_t)batch * h->vstride));
+    CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
+    CHECK(dalloc_t(h, &h->hess, (size_t)batch * g.plane));
+    CU(cudaStreamSynchronize(h->work));
+    return LSRTM_OK;
+}
+
+lsrtm_status ensure_cg(lsrtm_handle *h)
+{
+    if (h->cg_x) return LSRTM_OK;
+    size_t m = 2 * (size_t)h->nint;
+    CHECK(dalloc_t(h, &h->cg_x, m));
+    CHECK(dalloc_t(h, &h->cg_s, m));
+    CHECK(dalloc_t(h, &h->cg_z, m));
+    CHECK(dalloc_t(h, &h->cg_p, m));
+    CHECK(dalloc_t(h, &h->cg_minv, m));
+    CHECK(dalloc_t(h, &h->cg_r, std::max<long long>(h->nrec_total * h->g.nt, 1)));
+    return LSRTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsrtm_status lsrtm_create(const lsrtm_config *cfg, const float *vp, const float *rho,
+                          const float *wavelet, const lsrtm_geometry *geom, void *stream,
+                          lsrtm_handle **out)
+{
+    g_last_error.clear();
+    if (!out || !vp || !rho || !wavelet) return fail(LSRTM_ERR_ARG, "null argument");
+    *out = nullptr;
+    lsrtm_handle *h = new (std::nothrow) lsrtm_handle();
+    if (!h) return fail(LSRTM_ERR_OOM, "host allocation failed");
+    lsrtm_status s = create_impl(cfg, vp, rho, wavelet, geom, stream, h);
+    if (s != LSRTM_OK) {
+        std::string msg = g_last_error;
+        lsrtm_destroy(h);
+        g_last_error = msg;
+        return s;
+    }
+    *out = h;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_born(lsrtm_handle *h, const float *dm, float *d)
+{
+    if (!h || !dm || !d) return fail(LSRTM_ERR_ARG, "null argument");
+    CHECK(begin_call(h));
+    const float *dm_d;
+    CHECK(stage_in(h, dm, h->mstage, 2 * h->nint, &dm_d));
+    CHECK(prep_perturbation(h, dm_d));
+    CHECK(born_core(h));
+    CHECK(copy_out(h, d, h->dstage, h->nrec_total * h->g.nt));
+    return end_call(h, !is_device_ptr(d));
+}
+
+lsrtm_status lsrtm_adjoint(lsrtm_handle *h, const float *d, float *g, float *pseudo_hess)
+{
+    if (!h || !d || !g) return fail(LSRTM_ERR_ARG, "null argument");
+    CHECK(begin_call(h));
+    CHECK(copy_out(h, h->dstage, d, h->nrec_total * h->g.nt));
+    bool gdev = is_device_ptr(g);
+    float *gd = gdev ? g : h->gstage;
+    CHECK(adjoint_core(h, gd, pseudo_hess != nullptr));
+    if (!gdev) CHECK(copy_out(h, g, gd, 2 * h->nint));
+    bool hdev = true;
+    if (pseudo_hess) {
+        hdev = is_device_ptr(pseudo_hess);
+        CHECK(copy_out(h, pseudo_hess, h->hess_img, h->nint));
+    }
+    return end_call(h, !gdev || !hdev);
+}
+
+lsrtm_status lsrtm_remigrate(lsrtm_handle *h, const float *m, float *out)
+{
+    if (!h || !m || !out) return fail(LSRTM_ERR_ARG, "null argument");
+    CHECK(begin_call(h));
+    const float *m_d;
+    CHECK(stage_in(h, m, h->mstage, 2 * h->nint, &m_d));
+    CHECK(prep_perturbation(h, m_d));
+    CHECK(born_core(h));
+    bool odev = is_device_ptr(out);
+    float *od = odev ? out : h->gstage;
+    CHECK(adjoint_core(h, od, false));
+    if (!odev) CHECK(copy_out(h, out, od, 2 * h->nint));
+    return end_call(h, !odev);
+}
+
+lsrtm_status lsrtm_psf(lsrtm_handle *h, int param, int spacing, float *psf)
+{
+    if (!h || !psf) return fail(LSRTM_ERR_ARG, "null argument");
+    if (param != 0 && param != 1) return fail(LSRTM_ERR_ARG, "param must be 0 (Vp) or 1 (Ip)");
+    if (spacing < 1) return fail(LSRTM_ERR_ARG, "spacing must be >= 1");
+    CHECK(begin_call(h));
+    CU(launch_comb(h->g, param, spacing, h->mstage, h->work));
+    h->launches++;
+    CHECK(prep_perturbation(h, h->mstage));
+    CHECK(born_core(h));
+    bool odev = is_device_ptr(psf);
+    float *od = odev ? psf : h->gstage;
+    CHECK(adjoint_core(h, od, false));
+    if (!odev) CHECK(copy_out(h, psf, od, 2 * h->nint));
+    return end_call(h, !odev);
+}
+
+}  // extern "C"
+
+namespace {
+
+// CGNR (CGLS form), Sec. 3, with FP64 device scalars:
+//   begin:   x = P x0, r = d - L x, s = P L^T r, z = M^-1 s, p = z, gamma = <s, z>
+//   iterate: q = L p, alpha = gamma / <q, q>, x += alpha p, r -= alpha q,
+//            s = P L^T r, z = M^-1 s, gamma' = <s, z>, p = z + (gamma'/gamma) p
+// P zeroes the planes outside param_mask; M is the diagonal pseudo-Hessian.
+lsrtm_status cg_begin_impl(lsrtm_handle *h, const float *d, const float *x0, int precond,
+                           int param_mask)
+{
+    CHECK(ensure_cg(h));
+    const long long nm = 2 * h->nint;
+    const long long nd = h->nrec_total * h->g.nt;
+    cudaStream_t s = h->work;
+    double *gamma = h->scal + 0, *dd = h->scal + 3, *one = h->scal + 5;
+    h->cg_mask = param_mask;
+    h->cg_precond = precond;
+    h->cg_iter = 0;
+    if (x0) CHECK(copy_out(h, h->cg_x, x0, nm));
+    else CU(cudaMemsetAsync(h->cg_x, 0, nm * sizeof(float), s));
+    CU(launch_mul_mask(h->cg_x, nullptr, param_mask, h->nint, s));
+    CHECK(copy_out(h, h->cg_r, d, nd));
+    CU(launch_dot(h->cg_r, h->cg_r, nd, dd, h->dotwork, s));
+    h->launches += 3;
+    if (x0) {
+        CHECK(prep_perturbation(h, h->cg_x));
+        CHECK(born_core(h));
+        CU(launch_axpy_ratio(h->cg_r, h->dstage, one, one, -1.0f, nd, s));
+        h->launches++;
+    }
+    if (precond) {
+        if (!h->hess_ready) CHECK(bg_forward(h, true));
+        CU(cudaMemsetAsync(h->fscal, 0, sizeof(float), s));
+        CU(launch_max_abs_reduce(h->hess_img, h->nint, h->fscal, s));
+        CU(launch_precond_build(h->hess_img, h->fscal, 1e-3f, h->nint, h->cg_minv, s));
+        h->launches += 2;
+    }
+    CU(launch_scale_copy(h->dstage, h->cg_r, nd, s));
+    CHECK(adjoint_core(h, h->cg_s, false));
+    CU(launch_mul_mask(h->cg_s, nullptr, param_mask, h->nint, s));
+    CU(launch_scale_copy(h->cg_z, h->cg_s, nm, s));
+    if (precond) CU(launch_mul_mask(h->cg_z, h->cg_minv, param_mask, h->nint, s));
+    CU(launch_scale_copy(h->cg_p, h->cg_z, nm, s));
+    CU(launch_dot(h->cg_s, h->cg_z, nm, gamma, h->dotwork, s));
+    CU(launch_dot(h->cg_r, h->cg_r, nd, h->scal + 6, h->dotwork, s));
+    h->launches += 10;
+    h->cg_active = true;
+    return LSRTM_OK;
+}
+
+lsrtm_status cg_iterate_impl(lsrtm_handle *h, int niter)
+{
+    const long long nm = 2 * h->nint;
+    const long long nd = h->nrec_total * h->g.nt;
+    cudaStream_t s = h->work;
+    double *gamma = h->scal + 0, *gnew = h->scal + 1, *qq = h->scal + 2;
+    if (h->mis_cap < h->cg_iter + niter + 1) {
+        int cap = std::max(2 * (h->cg_iter + niter + 1), 64);
+        double *nb = nullptr;
+        CHECK(dalloc_t(h, &nb, cap));
+        if (h->mis_dev) CU(cudaMemcpyAsync(nb, h->mis_dev, h->mis_cap * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        h->mis_dev = nb;
+        h->mis_cap = cap;
+    }
+    for (int k = 0; k < niter; ++k) {
+        CHECK(prep_perturbation(h, h->cg_p));
+        CHECK(born_core(h));
+        CU(launch_dot(h->dstage, h->dstage, nd, qq, h->dotwork, s));
+        CU(launch_axpy_ratio(h->cg_x, h->cg_p, gamma, qq, 1.0f, nm, s));
+        CU(launch_axpy_ratio(h->cg_r, h->dstage, gamma, qq, -1.0f, nd, s));
+        CU(launch_scale_copy(h->dstage, h->cg_r, nd, s));
+        CHECK(adjoint_core(h, h->cg_s, false));
+        CU(launch_mul_mask(h->cg_s, nullptr, h->cg_mask, h->nint, s));
+        CU(launch_scale_copy(h->cg_z, h->cg_s, nm, s));
+        if (h->cg_precond) CU(launch_mul_mask(h->cg_z, h->cg_minv, h->cg_mask, h->nint, s));
+        CU(launch_dot(h->cg_s, h->cg_z, nm, gnew, h->dotwork, s));
+        CU(launch_xpby_ratio(h->cg_p, h->cg_z, gnew, gamma, nm, s));
+        CU(cudaMemcpyAsync(gamma, gnew, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        h->cg_iter++;
+        CU(launch_dot(h->cg_r, h->cg_r, nd, h->mis_dev + h->cg_iter, h->dotwork, s));
+        h->launches += 16;
+    }
+    return LSRTM_OK;
+}
+
+lsrtm_status read_misfits(lsrtm_handle *h, int first, int count, double *out)
+{
+    std::vector<double> m2(count);
+    double dd = 0.0;
+    CU(cudaMemcpyAsync(m2.data(), h->mis_dev + first, count * sizeof(double), cudaMemcpyDeviceToHost, h->work));
+    CU(cudaMemcpyAsync(&dd, h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, h->work));
+    CU(cudaStreamSynchronize(h->work));
+    for (int k = 0; k < count; ++k) out[k] = dd > 0 ? std::sqrt(m2[k] / dd) : 0.0;
+    return LSRTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsrtm_status lsrtm_cg_begin(lsrtm_handle *h, const float *d, const float *x0, int precond,
+                            int param_mask)
+{
+    if (!h || !d) return fail(LSRTM_ERR_ARG, "null argument");
+    if (param_mask < 1 || param_mask > 3) return fail(LSRTM_ERR_ARG, "param_mask must be 1, 2 or 3");
+    CHECK(begin_call(h));
+    h->cg_active = false;
+    CHECK(cg_begin_impl(h, d, x0, precond, param_mask));
+    if (h->mis_cap < 64) {
+        CHECK(dalloc_t(h, &h->mis_dev, 64));
+        h->mis_cap = 64;
+    }
+    CU(cudaMemcpyAsync(h->mis_dev, h->scal + 6, sizeof(double), cudaMemcpyDeviceToDevice, h->work));
+    return end_call(h, false);
+}
+
+lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    if (!h->cg_active) return fail(LSRTM_ERR_STATE, "lsrtm_cg_begin has not been called");
+    if (niter < 0) return fail(LSRTM_ERR_ARG, "niter < 0");
+    CHECK(begin_call(h));
+    int first = h->cg_iter + 1;
+    CHECK(cg_iterate_impl(h, niter));
+    CHECK(end_call(h, false));
+    if (misfit && niter > 0) CHECK(read_misfits(h, first, niter, misfit));
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_cg_result(lsrtm_handle *h, float *dm, double *misfit0)
+{
+    if (!h || !dm) return fail(LSRTM_ERR_ARG, "null argument");
+    if (!h->cg_active) return fail(LSRTM_ERR_STATE, "lsrtm_cg_begin has not been called");
+    CHECK(begin_call(h));
+    CHECK(copy_out(h, dm, h->cg_x, 2 * h->nint));
+    CHECK(end_call(h, true));
+    if (misfit0) CHECK(read_misfits(h, 0, 1, misfit0));
+    return check_finite(h, h->cg_x, 2 * h->nint, "CG solution");
+}
+
+lsrtm_status lsrtm_cg_solve(lsrtm_handle *h, const float *d, float *dm, int niter, int precond,
+                            int param_mask, double *misfit)
+{
+    if (!h || !d || !dm) return fail(LSRTM_ERR_ARG, "null argument");
+    if (niter < 0) return fail(LSRTM_ERR_ARG, "niter < 0");
+    CHECK(lsrtm_cg_begin(h, d, dm, precond, param_mask));
+    CHECK(lsrtm_cg_iterate(h, niter, misfit ? misfit + 1 : nullptr));
+    return lsrtm_cg_result(h, dm, misfit);
+}
+
+lsrtm_status lsrtm_timing_enable(lsrtm_handle *h, int enable)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    h->timing = enable != 0;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_timing_read(lsrtm_handle *h, lsrtm_timings *out, int reset)
+{
+    if (!h || !out) return fail(LSRTM_ERR_ARG, "null argument");
+    CU(cudaStreamSynchronize(h->work));
+    for (auto &t : h->pending) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, t.a, t.b));
+        h->t_ms[t.kind] += ms;
+        h->t_launch[t.kind] += t.launches;
+        h->t_cells[t.kind] += t.cells;
+        h->event_pool.push_back(t.a);
+        h->event_pool.push_back(t.b);
+    }
+    h->pending.clear();
+    out->born_ms = h->t_ms[0];
+    out->background_ms = h->t_ms[1];
+    out->adjoint_ms = h->t_ms[2];
+    out->born_launches = h->t_launch[0];
+    out->background_launches = h->t_launch[1];
+    out->adjoint_launches = h->t_launch[2];
+    out->born_cells = h->t_cells[0];
+    out->background_cells = h->t_cells[1];
+    out->adjoint_cells = h->t_cells[2];
+    if (reset)
+        for (int k = 0; k < 3; ++k) h->t_ms[k] = 0, h->t_launch[k] = 0, h->t_cells[k] = 0;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    h->user = (cudaStream_t)stream;
+    return LSRTM_OK;
+}
+
+size_t lsrtm_workspace_bytes(const lsrtm_handle *h) { return h ? h->bytes : 0; }
+
+long long lsrtm_kernel_launches(const lsrtm_handle *h) { return h ? h->launches : 0; }
+
+void lsrtm_destroy(lsrtm_handle *h)
+{
+    if (!h) return;
+    if (h->work) cudaStreamSynchronize(h->work);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &t : h->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->work) cudaStreamDestroy(h->work);
+    delete h;
+}
+
+const char *lsrtm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

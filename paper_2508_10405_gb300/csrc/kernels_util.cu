@@ -1,0 +1,424 @@
+// Small kernels around the time loop: model and perturbation preparation
+// (Sec. 2 parameter map), residual injection, stacking of the per-shot images
+// and the chain rule of Sec. 3, pseudo-Hessian stacking (App. B), the spike
+// comb of App. D and the FP64-accumulated vector kernels of the CGNR driver.
+#include "lsrtm_internal.cuh"
+
+namespace lsrtm {
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ long long pad_of(const GridDev &g, long long k)
+{
+    long long ix = k % g.nx;
+    long long t = k / g.nx;
+    long long iy = t % g.ny;
+    long long iz = t / g.ny;
+    return (iz + g.z0) * g.rowz + (iy + g.y0) * (long long)g.pitch + (ix + g.x0);
+}
+
+__global__ void k_model_prep(GridDev g, const float *vp, const float *rho, float *kdt, float *binv)
+{
+    long long ncell = (long long)g.Nz * g.Ny * g.Nx;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(c % g.Nx);
+        long long t = c / g.Nx;
+        int y = (int)(t % g.Ny);
+        int z = (int)(t / g.Ny);
+        int iz = min(max(z - g.z0, 0), g.nz - 1);
+        int iy = min(max(y - g.y0, 0), g.ny - 1);
+        int ix = min(max(x - g.x0, 0), g.nx - 1);
+        long long k = ((long long)iz * g.ny + iy) * g.nx + ix;
+        float v = vp[k], r = rho[k];
+        long long p = (long long)z * g.rowz + (long long)y * g.pitch + x;
+        kdt[p] = g.dt * r * v * v;
+        binv[p] = 1.0f / r;
+    }
+}
+
+// dkdt = dt kappa (dlnVp + dlnIp), rr = (dlnIp - dlnVp) / rho on the interior;
+// the arrays are zeroed beforehand, so the pad stays zero.
+__global__ void k_pert_prep(GridDev g, const float *dm, const float *kdt, const float *binv,
+                            float *dkdt, float *rr)
+{
+    long long nint = (long long)g.nz * g.ny * g.nx;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long c = pad_of(g, k);
+        float m1 = dm[k], m2 = dm[nint + k];
+        dkdt[c] = kdt[c] * (m1 + m2);
+        rr[c] = (m2 - m1) * binv[c];
+    }
+}
+
+__global__ void k_inject(GridDev g, TileRecs tr, int shot0, const float *dstage, int n, float *lp,
+                         long long sstride)
+{
+    int slot = blockIdx.y;
+    int t = (shot0 + slot) * tr.ntiles + blockIdx.x;
+    int b = tr.ptr[t], e = tr.ptr[t + 1];
+    float *dst = lp + slot * sstride;
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        int2 rc = tr.rec[i];
+        if (i > b && tr.rec[i - 1].x == rc.x) continue;
+        float add = 0.f;
+        for (int k = i; k < e && tr.rec[k].x == rc.x; ++k)
+            add += dstage[(long long)tr.rec[k].y * g.nt + n];
+        dst[rc.x] += add;
+    }
+}
+
+__global__ void k_image_acc(GridDev g, const float2 *img, int batch, double2 *acc)
+{
+    long long nint = (long long)g.nz * g.ny * g.nx;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long c = pad_of(g, k);
+        double2 s = acc[k];
+        for (int b = 0; b < batch; ++b) {
+            float2 v = img[b * g.plane + c];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        acc[k] = s;
+    }
+}
+
+// g_kappa = -dt kappa sum_n Q lp, g_rho = (dt / 2) / rho * sum_n (products at
+// the adjacent half nodes); g_Vp = g_kappa - g_rho, g_Ip = g_kappa + g_rho.
+__global__ void k_image_fin(GridDev g, const double2 *acc, const float *kdt, const float *binv,
+                            float *gout)
+{
+    long long nint = (long long)g.nz * g.ny * g.nx;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long c = pad_of(g, k);
+        double gk = -(double)kdt[c] * acc[k].x;
+        double gr = 0.5 * (double)g.dt * (double)binv[c] * acc[k].y;
+        gout[k] = (float)(gk - gr);
+        gout[nint + k] = (float)(gk + gr);
+    }
+}
+
+__global__ void k_hess_acc(GridDev g, const float *hess, int batch, double *acc)
+{
+    long long nint = (long long)g.nz * g.ny * g.nx;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long c = pad_of(g, k);
+        double s = acc[k];
+        for (int b = 0; b < batch; ++b) s += hess[b * g.plane + c];
+        acc[k] = s;
+    }
+}
+
+__global__ void k_hess_fin(long long nint, const double *acc, float *out)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = (float)acc[k];
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-level FP64 sum of x*y (w optional), one partial per block.
+__global__ void k_dot_partial(const float *x, const float *y, const float *w, long long n,
+                              double *part)
+{
+    __shared__ double sh[NT / 32];
+    double acc = 0.0;
+    long long n4 = n / 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    const float4 *w4 = reinterpret_cast<const float4 *>(w);
+    bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
+                 reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    if (vec) {
+        for (long long i = start; i < n4; i += stride) {
+            float4 a = x4[i], b = y4[i];
+            if (w) {
+                float4 c = w4[i];
+                acc += (double)a.x * b.x * c.x + (double)a.y * b.y * c.y +
+                       (double)a.z * b.z * c.z + (double)a.w * b.w * c.w;
+            } else {
+                acc += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+            }
+        }
+        for (long long i = 4 * n4 + start; i < n; i += stride)
+            acc += (double)x[i] * y[i] * (w ? (double)w[i] : 1.0);
+    } else {
+        for (long long i = start; i < n; i += stride)
+            acc += (double)x[i] * y[i] * (w ? (double)w[i] : 1.0);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_sum_final(const double *part, int np, double *out)
+{
+    __shared__ double sh[NT / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+__global__ void k_maxabs(const float *x, long long n, float *out)
+{
+    __shared__ float sh[NT / 32];
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.f;
+        v = warp_max(v);
+        // non-negative floats compare like their bit patterns as ints
+        if (threadIdx.x == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(v));
+    }
+}
+
+__global__ void k_nonfinite(const float *x, long long n, int *flag)
+{
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_comb(GridDev g, int param, int spacing, float *m)
+{
+    long long nint = (long long)g.nz * g.ny * g.nx;
+    int h = spacing / 2;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
+         k += (long long)gridDim.x * blockDim.x) {
+        int ix = (int)(k % g.nx);
+        long long t = k / g.nx;
+        int iy = (int)(t % g.ny);
+        int iz = (int)(t / g.ny);
+        bool on = (iz >= h && (iz - h) % spacing == 0) && (ix >= h && (ix - h) % spacing == 0) &&
+                  (g.ndim == 2 || (iy >= h && (iy - h) % spacing == 0));
+        m[k] = (param == 0 && on) ? 1.f : 0.f;
+        m[nint + k] = (param == 1 && on) ? 1.f : 0.f;
+    }
+}
+
+__global__ void k_axpy_ratio(float *x, const float *p, const double *num, const double *den,
+                             float sign, long long n)
+{
+    double d = *den;
+    float alpha = d != 0.0 ? (float)(*num / d) * sign : 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] += alpha * p[i];
+}
+
+__global__ void k_xpby_ratio(float *p, const float *z, const double *num, const double *den,
+                             long long n)
+{
+    double d = *den;
+    float beta = d != 0.0 ? (float)(*num / d) : 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// x[plane][k] *= (mask bit of plane) * (w ? w[plane][k] : 1)
+__global__ void k_mul_mask(float *x, const float *w, int mask, long long nint)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2 * nint;
+         i += (long long)gridDim.x * blockDim.x) {
+        int plane = i >= nint;
+        float f = ((mask >> plane) & 1) ? 1.f : 0.f;
+        if (w) f *= w[i];
+        x[i] *= f;
+    }
+}
+
+__global__ void k_copy(float *dst, const float *src, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// minv = 1 / (h + eps * max(h)) for both planes
+__global__ void k_precond(const float *h, const float *hmax, float eps, long long nint, float *minv)
+{
+    float hm = *hmax;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nint;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = 1.0f / (h[i] + eps * hm);
+        minv[i] = v;
+        minv[nint + i] = v;
+    }
+}
+
+int grid_for(long long n)
+{
+    long long b = (n + NT - 1) / NT;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
+                              float *binv, cudaStream_t s)
+{
+    long long n = (long long)g.Nz * g.Ny * g.Nx;
+    k_model_prep<<<grid_for(n), NT, 0, s>>>(g, vp, rho, kdt, binv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt,
+                             const float *binv, float *dkdt, float *rr, cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_pert_prep<<<grid_for(n), NT, 0, s>>>(g, dm, kdt, binv, dkdt, rr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int batch, int shot0,
+                                   const float *dstage, int n, float *lp, long long sstride,
+                                   cudaStream_t s)
+{
+    dim3 grid(tr.ntiles, batch);
+    k_inject<<<grid, 64, 0, s>>>(g, tr, shot0, dstage, n, lp, sstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_accumulate(const GridDev &g, const float2 *img, int batch,
+                                    double2 *acc, cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_image_acc<<<grid_for(n), NT, 0, s>>>(g, img, batch, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_finalize(const GridDev &g, const double2 *acc, const float *kdt,
+                                  const float *binv, float *gout, cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_image_fin<<<grid_for(n), NT, 0, s>>>(g, acc, kdt, binv, gout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_accumulate(const GridDev &g, const float *hess, int batch, double *acc,
+                                   cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_hess_acc<<<grid_for(n), NT, 0, s>>>(g, hess, batch, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out, cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_hess_fin<<<grid_for(n), NT, 0, s>>>(n, acc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s)
+{
+    k_maxabs<<<grid_for(n), NT, 0, s>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s)
+{
+    k_nonfinite<<<grid_for(n), NT, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_comb(const GridDev &g, int param, int spacing, float *m, cudaStream_t s)
+{
+    long long n = (long long)g.nz * g.ny * g.nx;
+    k_comb<<<grid_for(n), NT, 0, s>>>(g, param, spacing, m);
+    return cudaGetLastError();
+}
+
+static constexpr int kDotBlocks = 152 * 4;
+
+cudaError_t launch_dot(const float *x, const float *y, long long n, double *out, double *work,
+                       cudaStream_t s)
+{
+    return launch_dot_w(x, y, nullptr, n, out, work, s);
+}
+
+cudaError_t launch_dot_w(const float *x, const float *y, const float *w, long long n,
+                         double *out, double *work, cudaStream_t s)
+{
+    int nb = grid_for(n) < kDotBlocks ? grid_for(n) : kDotBlocks;
+    k_dot_partial<<<nb, NT, 0, s>>>(x, y, w, n, work);
+    k_sum_final<<<1, NT, 0, s>>>(work, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_ratio(float *x, const float *p, const double *num, const double *den,
+                              float sign, long long n, cudaStream_t s)
+{
+    k_axpy_ratio<<<grid_for(n), NT, 0, s>>>(x, p, num, den, sign, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xpby_ratio(float *p, const float *z, const double *num, const double *den,
+                              long long n, cudaStream_t s)
+{
+    k_xpby_ratio<<<grid_for(n), NT, 0, s>>>(p, z, num, den, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_mask(float *x, const float *w, int param_mask, long long nint,
+                            cudaStream_t s)
+{
+    k_mul_mask<<<grid_for(2 * nint), NT, 0, s>>>(x, w, param_mask, nint);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(float *dst, const float *src, long long n, cudaStream_t s)
+{
+    k_copy<<<grid_for(n), NT, 0, s>>>(dst, src, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond_build(const float *h, const float *hmax, float eps, long long nint,
+                                 float *minv, cudaStream_t s)
+{
+    k_precond<<<grid_for(nint), NT, 0, s>>>(h, hmax, eps, nint, minv);
+    return cudaGetLastError();
+}
+
+}  // namespace lsrtm

@@ -1,0 +1,128 @@
+// Internal declarations shared by the engine and the kernel translation units.
+// Layout of every wavefield and model array on the device: padded grid
+// Nz x Ny x Nx (interior + npml on each side; Ny = 1 in 2D), x fastest with a
+// row pitch that is a multiple of 32 floats, one "plane" = Nz*Ny*pitch floats.
+// A shot's state is a block of planes; shots of a batch are consecutive blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lsrtm {
+
+constexpr int kMaxM = 4;
+
+struct GridDev {
+    int ndim, M;
+    int nz, ny, nx;        // interior
+    int Nz, Ny, Nx;        // padded
+    int pitch;             // floats per padded row (multiple of 32)
+    long long plane;       // floats per field plane
+    long long rowz;        // floats between consecutive z (Ny * pitch)
+    int z0, y0, x0;        // interior origin in padded coordinates
+    float cz[kMaxM], cy[kMaxM], cx[kMaxM];  // c_l / h
+    float dt;
+    int nt;
+};
+
+// CPML coefficients, per direction d (0 z, 1 y, 2 x) and array: a/b at
+// integer nodes (ai, bi) and at half nodes (ah, bh).
+struct Pml {
+    const float *ai[3], *bi[3], *ah[3], *bh[3];
+};
+
+// Boundary-band geometry (per shot, per step): the p band and the normal-v
+// band each hold NB values laid out as strips:
+//   2D: [x-left M*nz][x-right M*nz][z-top M*nx][z-bottom M*nx]
+//   3D: [x-faces 2*M*nz*ny][y-faces 2*M*nz*nx][z-faces 2*M*ny*nx]
+struct Bands {
+    void *p;              // [nshot][nt][NB]
+    void *v;              // [nshot][nt][NB]
+    long long nb;         // NB
+    int bf16;             // element type: 0 float, 1 bf16
+};
+
+// Receivers grouped by (shot, tile): CSR over shot*ntiles + tile.
+struct TileRecs {
+    const int *ptr;       // [nshot*ntiles + 1]
+    const int2 *rec;      // (cell offset in plane, global receiver row), sorted by cell
+    int ntiles;           // tiles per shot
+};
+
+// Arguments of the fused 2D time-step kernels.
+struct Step2D {
+    GridDev g;
+    Pml pml;
+    const float *kdt;     // dt * kappa          [plane]
+    const float *binv;    // 1 / rho             [plane]
+    const float *dkdt;    // dt * kappa * dlnk   [plane] (Born only)
+    const float *rr;      // dln rho / rho       [plane] (Born only)
+    const float *in;      // ping state, shot slot s at in + s*sstride
+    float *out;           // pong state
+    float *psiv;          // in-place node CPML memories, slot stride vstride
+    long long sstride, vstride;
+    int n;                // time step
+    int shot0;            // global index of slot 0
+    const float *wav;     // [nt] or [nshot][nt]
+    int wav_per_shot;
+    const int *src_cell;  // [nshot] plane offset of the source node
+    float src_scale;      // dt / cell volume
+    TileRecs trec;
+    float *dstage;        // [nrec_total][nt]: records (forward) or residual (adjoint)
+    Bands bands;
+    float *hess;          // [batch][plane] pseudo-Hessian accumulators (or null)
+    float2 *img;          // [batch][plane] image accumulators (adjoint)
+};
+
+// Tile shapes used by the 2D kernels.
+constexpr int kTX2 = 32;
+constexpr int kTZ2 = 16;
+constexpr int kThreads2D = 256;
+
+// Launchers (kernels2d.cu). Return the cudaError of the launch.
+cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess,
+                         cudaStream_t s);
+cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s);
+size_t fwd2d_smem(int M, bool born, bool hess);
+size_t adj2d_smem(int M);
+cudaError_t configure_2d_kernels();
+
+// Utility kernels (kernels_util.cu).
+cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
+                              float *binv, cudaStream_t s);
+cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt,
+                             const float *binv, float *dkdt, float *rr, cudaStream_t s);
+cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int batch, int shot0,
+                                   const float *dstage, int n, float *lp, long long sstride,
+                                   cudaStream_t s);
+cudaError_t launch_image_accumulate(const GridDev &g, const float2 *img, int batch,
+                                    double2 *acc, cudaStream_t s);
+cudaError_t launch_image_finalize(const GridDev &g, const double2 *acc, const float *kdt,
+                                  const float *binv, float *gout, cudaStream_t s);
+cudaError_t launch_hess_accumulate(const GridDev &g, const float *hess, int batch, double *acc,
+                                   cudaStream_t s);
+cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out,
+                                 cudaStream_t s);
+cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);
+cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s);
+cudaError_t launch_comb(const GridDev &g, int param, int spacing, float *m, cudaStream_t s);
+
+// FP64-accumulated vector kernels for the Krylov driver.
+cudaError_t launch_dot(const float *x, const float *y, long long n, double *out, double *work,
+                       cudaStream_t s);
+cudaError_t launch_dot_w(const float *x, const float *y, const float *w, long long n,
+                         double *out, double *work, cudaStream_t s);
+// x += alpha*p, with alpha = num/den read from device scalars (sign: +1 or -1)
+cudaError_t launch_axpy_ratio(float *x, const float *p, const double *num, const double *den,
+                              float sign, long long n, cudaStream_t s);
+// p = z + (num/den) * p
+cudaError_t launch_xpby_ratio(float *p, const float *z, const double *num, const double *den,
+                              long long n, cudaStream_t s);
+cudaError_t launch_mul_mask(float *x, const float *w, int param_mask, long long nint,
+                            cudaStream_t s);
+cudaError_t launch_scale_copy(float *dst, const float *src, long long n, cudaStream_t s);
+cudaError_t launch_precond_build(const float *h, const float *hmax, float eps, long long nint,
+                                 float *minv, cudaStream_t s);
+
+}  // namespace lsrtm

@@ -1,0 +1,246 @@
+"""Parity of the CUDA operators (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative L2 <= 1e-4 on records and images for the FP32 path
+(the bar the operators are built to), FP32 dot test <= 1e-6. The cases span
+several tiles with ragged tails (padded sizes not multiples of the 32 x 16
+tile) and both orders."""
+import numpy as np
+import pytest
+
+import lsrtm_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def handle(w, **kw):
+    from paper_2508_10405_gb300 import Lsrtm
+    return Lsrtm.from_workload(w, **kw)
+
+
+def cpu(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+CASES = {
+    "o4": dict(nz=37, nx=45, nt=300, order=4, npml=8, nshot=3, seed=31),
+    "o8": dict(nz=41, nx=53, nt=260, order=8, npml=10, nshot=2, seed=32),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    w = li.small_case(**CASES[request.param])
+    return request.param, w
+
+
+def test_born_matches_oracle(case):
+    name, w = case
+    h = handle(w)
+    d = cpu(h.born(torch.tensor(w.dm, dtype=torch.float32, device="cuda")))
+    ref = oracle.born(w, w.dm)
+    assert rel(d, ref) < TOL, (name, rel(d, ref))
+
+
+def test_adjoint_matches_oracle(case):
+    name, w = case
+    rng = np.random.default_rng(3)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    h = handle(w)
+    g = cpu(h.adjoint(torch.tensor(dres, dtype=torch.float32, device="cuda")))
+    ref = oracle.adjoint(w, dres)
+    assert rel(g, ref) < TOL, (name, rel(g, ref))
+
+
+def dot_tests(h, m, d):
+    """Two FP32 dot tests of <L m, d> = <m, L^T d>:
+    (1) d = L m, so the inner product is ||L m||^2 and no cancellation hides
+        or inflates the mismatch; relative to ||L m||^2;
+    (2) independent random d, mismatch relative to the Cauchy-Schwarz bound
+        ||L m|| ||d|| (the plain ratio to <L m, d> is amplified by the
+        cancellation of two uncorrelated vectors)."""
+    Lm = h.born(m).double()
+    a1 = float((Lm * Lm).sum())
+    b1 = float((m.double() * h.adjoint(Lm.float()).double()).sum())
+    a2 = float((Lm * d.double()).sum())
+    b2 = float((m.double() * h.adjoint(d).double()).sum())
+    r1 = abs(a1 - b1) / a1
+    r2 = abs(a2 - b2) / (float(Lm.norm()) * float(d.double().norm()))
+    return r1, r2
+
+
+def test_dot_product_fp32(case):
+    name, w = case
+    rng = np.random.default_rng(4)
+    m = torch.tensor(rng.standard_normal((2,) + w.shape), dtype=torch.float32, device="cuda")
+    d = torch.tensor(rng.standard_normal((w.geom.nrec_total, w.nt)), dtype=torch.float32,
+                     device="cuda")
+    r1, r2 = dot_tests(handle(w), m, d)
+    assert r1 < 1e-6 and r2 < 1e-6, (name, r1, r2)
+
+
+def test_config1_born_adjoint_dot():
+    """The 2D plain Born+migration workload at its full size (101 x 101,
+    order 4, nt = 1000, one shot): L, L^T and the FP32 dot test."""
+    w = li.preset(1)
+    h = handle(w)
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    d = h.born(dm)
+    ref_d = oracle.born(w, w.dm)
+    assert rel(cpu(d), ref_d) < TOL
+    g = h.adjoint(torch.tensor(ref_d, dtype=torch.float32, device="cuda"))
+    ref_g = oracle.adjoint(w, ref_d)
+    assert rel(cpu(g), ref_g) < TOL
+    rng = np.random.default_rng(5)
+    dd = torch.tensor(rng.standard_normal(d.shape), dtype=torch.float32, device="cuda")
+    r1, r2 = dot_tests(h, dm, dd)
+    assert r1 < 1e-6 and r2 < 1e-6, (r1, r2)
+
+
+def test_plain_plan_equals_batched():
+    """One shot per launch without graphs and the batched graph plan run the
+    same arithmetic per shot: bitwise-equal records and images."""
+    from paper_2508_10405_gb300 import PLAN_PLAIN
+    w = li.small_case(**CASES["o4"])
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    hb = handle(w)
+    hp = handle(w, plan=PLAN_PLAIN)
+    db, dp = hb.born(dm), hp.born(dm)
+    assert torch.equal(db, dp)
+    gb, gp = hb.adjoint(db), hp.adjoint(db)
+    assert torch.equal(gb, gp)
+
+
+def test_batching_does_not_change_results():
+    w = li.small_case(nz=30, nx=34, nt=200, order=8, npml=9, nshot=5, seed=41)
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    h1 = handle(w, shots_per_batch=2)
+    h2 = handle(w)
+    assert torch.equal(h1.born(dm), h2.born(dm))
+    d = h2.born(dm)
+    assert torch.equal(h1.adjoint(d), h2.adjoint(d))
+
+
+def test_host_pointers_roundtrip():
+    """Host (numpy) inputs and outputs through the same entry points."""
+    w = li.small_case(**CASES["o4"])
+    h = handle(w)
+    d_host = h.born(w.dm.astype(np.float32))  # host input, device output
+    ref = oracle.born(w, w.dm)
+    assert rel(cpu(d_host), ref) < TOL
+
+
+def test_duplicate_and_edge_receivers():
+    """Receivers on the interior edges and two receivers on the same node;
+    the source on the first interior row."""
+    w = li.small_case(nz=25, nx=33, nt=180, order=4, npml=6, nshot=1, seed=51)
+    nz, nx = w.nz, w.nx
+    recs = np.array([0, nx - 1, (nz - 1) * nx, nz * nx - 1, 5 * nx + 7, 5 * nx + 7, 12 * nx + 3],
+                    np.int32)
+    w.geom = li.Geometry(np.array([0 * nx + 16], np.int32), np.array([0, len(recs)], np.int32), recs)
+    h = handle(w)
+    d = cpu(h.born(torch.tensor(w.dm, dtype=torch.float32, device="cuda")))
+    ref = oracle.born(w, w.dm)
+    assert rel(d, ref) < TOL
+    rng = np.random.default_rng(9)
+    dres = rng.standard_normal(ref.shape)
+    g = cpu(h.adjoint(torch.tensor(dres, dtype=torch.float32, device="cuda")))
+    assert rel(g, oracle.adjoint(w, dres)) < TOL
+
+
+def test_psf_and_remigration_match_oracle():
+    w = li.small_case(nz=40, nx=44, nt=220, order=8, npml=10, nshot=3, seed=61)
+    h = handle(w)
+    for param in (0, 1):
+        psf = cpu(h.psf(param, 8))
+        ref = oracle.psf(w, param, 8)
+        assert rel(psf, ref) < TOL
+    m = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    assert rel(cpu(h.remigrate(m)), oracle.remigrate(w, w.dm)) < TOL
+
+
+def test_pseudo_hessian_matches_oracle():
+    w = li.small_case(**CASES["o8"])
+    h = handle(w)
+    rng = np.random.default_rng(2)
+    d = torch.tensor(rng.standard_normal((w.geom.nrec_total, w.nt)), dtype=torch.float32,
+                     device="cuda")
+    _, ph = h.adjoint(d, pseudo_hessian=True)
+    assert rel(cpu(ph), oracle.pseudo_hessian(w)) < TOL
+
+
+def test_cg_matches_oracle_cg():
+    """CGNR iterates and misfit history against the oracle's FP64 CGNR."""
+    w = li.small_case(nz=28, nx=32, nt=200, order=4, npml=8, nshot=3, seed=71)
+    d = oracle.born(w, w.dm)
+    h = handle(w)
+    x, mis = h.cg_solve(torch.tensor(d, dtype=torch.float32, device="cuda"), 4)
+    xr, misr = oracle.lsrtm_cg(w, d, 4)
+    assert np.all(np.abs(mis - misr) < 1e-3), (mis, misr)
+    assert rel(cpu(x), xr) < 1e-3
+
+
+def test_pcg_and_monoparameter_match_oracle():
+    w = li.small_case(nz=28, nx=32, nt=200, order=4, npml=8, nshot=3, seed=72)
+    d = oracle.born(w, w.dm)
+    h = handle(w)
+    x, mis = h.cg_solve(torch.tensor(d, dtype=torch.float32, device="cuda"), 3, precond=True,
+                        param_mask=2)
+    xr, misr = oracle.lsrtm_cg(w, d, 3, precond=True, param_mask=2)
+    assert np.all(cpu(x)[0] == 0)
+    assert np.all(np.abs(mis - misr) < 1e-3), (mis, misr)
+    assert rel(cpu(x), xr) < 1e-3
+
+
+def test_bf16_bands_error_stated():
+    """BF16 boundary bands: the image error against the FP64 oracle stays
+    within 1e-2 and within 1e-2 of the FP32-band result."""
+    from paper_2508_10405_gb300 import BAND_BF16
+    w = li.small_case(**CASES["o8"])
+    rng = np.random.default_rng(3)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    dt = torch.tensor(dres, dtype=torch.float32, device="cuda")
+    g32 = cpu(handle(w).adjoint(dt))
+    g16 = cpu(handle(w, band_precision=BAND_BF16).adjoint(dt))
+    ref = oracle.adjoint(w, dres)
+    assert rel(g16, ref) < 1e-2
+    assert rel(g16, g32) < 1e-2
+
+
+def test_autograd_function_backward_is_adjoint():
+    from paper_2508_10405_gb300 import born_op
+    w = li.small_case(**CASES["o4"])
+    h = handle(w)
+    BornOp = born_op()
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda", requires_grad=True)
+    d = BornOp.apply(dm, h)
+    rng = np.random.default_rng(8)
+    r = torch.tensor(rng.standard_normal(d.shape), dtype=torch.float32, device="cuda")
+    (d * r).sum().backward()
+    ref = oracle.adjoint(w, cpu(r))
+    assert rel(cpu(dm.grad), ref) < TOL
+
+
+def test_errors_are_reported():
+    from paper_2508_10405_gb300 import Lsrtm, LsrtmError
+    w = li.small_case(**CASES["o4"])
+    with pytest.raises(LsrtmError, match="ERR_CFL"):
+        Lsrtm.from_workload(li.small_case(**CASES["o4"], dt=0.01))
+    bad = li.small_case(**CASES["o4"])
+    bad.geom.rec_idx[0] = w.nint + 5
+    with pytest.raises(LsrtmError, match="ERR_GEOMETRY"):
+        Lsrtm.from_workload(bad)
+    nanw = li.small_case(**CASES["o4"])
+    nanw.vp[3, 3] = np.nan
+    with pytest.raises(LsrtmError, match="ERR_NONFINITE"):
+        Lsrtm.from_workload(nanw, pml_vmax=3000.0)
