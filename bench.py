@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--shots", type=int, default=None,
+                    help="override the shot count (smaller cases for profiling)")
+    ap.add_argument("--nt", type=int, default=None, help="override the number of time steps")
     return ap.parse_args()
 
 
@@ -187,10 +190,19 @@ def cpu_sample(w, seconds, reps=1):
     return cells / t / 1e9, threads, desc, times
 
 
+def workload(args):
+    kw = {}
+    if args.shots is not None:
+        kw["nshot"] = args.shots
+    if args.nt is not None:
+        kw["nt"] = args.nt
+    return li.preset(args.workload, **kw)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    w = li.preset(args.workload)
+    w = workload(args)
     K, W = args.steps, args.warmup
     # bounded per-step sample sized so the whole run stays within minutes
     per = max(2.0, min(args.cpu_seconds, 120.0 / max(K + W, 1)))
@@ -226,7 +238,7 @@ def main():
 
     from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, Lsrtm
 
-    w = li.preset(args.workload)
+    w = workload(args)
     K, W = args.steps, args.warmup
     ncell = w.padded_cells
     nshot = w.geom.nshot

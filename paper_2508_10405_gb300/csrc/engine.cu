@@ -45,9 +45,11 @@ lsrtm_status fail(lsrtm_status st, const std::string &msg)
         if (s_ != LSRTM_OK) return s_;         \
     } while (0)
 
-// Planes per wavefield slot: 10 ping-pong planes (forward: p v psi_p for the
-// background and the scattered field; adjoint: background p v, lambda p v and
-// the four lambda CPML memories), 4 in-place node CPML planes (forward).
+// Planes per wavefield slot: 10 ping-pong planes (Born: (p, dp) (vx, dvx)
+// (vz, dvz) (psi_px, dpsi_px) (psi_pz, dpsi_pz) as float2 pairs; background
+// only: p vx vz psi_px psi_pz; adjoint: (p, lambda_p) (vx, lambda_vx)
+// (vz, lambda_vz) pairs and four lambda CPML memories), 4 in-place node CPML
+// planes (forward).
 constexpr int kStatePlanes2D = 10;
 constexpr int kPsivPlanes2D = 4;
 
@@ -66,7 +68,8 @@ struct lsrtm_handle {
     long long nint = 0;
     std::vector<int> rec_ptr;
     // device model and geometry
-    float *kdt = nullptr, *binv = nullptr, *dkdt = nullptr, *rr = nullptr;
+    float *kdt = nullptr, *binv = nullptr;
+    float2 *kd2 = nullptr, *br2 = nullptr;   // (dt kappa, perturbation) and (1/rho, perturbation)
     float *pml_buf = nullptr;
     Pml pml{};
     float *wav = nullptr;
@@ -75,6 +78,7 @@ struct lsrtm_handle {
     int2 *trec = nullptr;
     TileRecs trv{};
     float src_scale = 0.f;
+    int txo = 0, tzc = 0;        // CTA output columns and z-chunk rows
     // wavefield slots
     int batch = 1;
     float *st[2] = {nullptr, nullptr};
@@ -254,8 +258,8 @@ Step2D step_args(lsrtm_handle *h, int shot0)
     a.pml = h->pml;
     a.kdt = h->kdt;
     a.binv = h->binv;
-    a.dkdt = h->dkdt;
-    a.rr = h->rr;
+    a.kd2 = h->kd2;
+    a.br2 = h->br2;
     a.psiv = h->psiv;
     a.sstride = h->sstride;
     a.vstride = h->vstride;
@@ -269,6 +273,7 @@ Step2D step_args(lsrtm_handle *h, int shot0)
     a.bands = h->bands;
     a.hess = h->hess;
     a.img = h->img;
+    a.tzc = h->tzc;
     return a;
 }
 
@@ -399,7 +404,7 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
     return LSRTM_OK;
 }
 
-// Born modelling of the perturbation already prepared in h->dkdt / h->rr;
+// Born modelling of the perturbation already prepared in h->kd2 / h->br2;
 // records go to h->dstage.
 lsrtm_status born_core(lsrtm_handle *h)
 {
@@ -434,14 +439,10 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
         int bs = batch_size(h, s0);
         CHECK(zero_slots(h, bs));
         CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
-        for (int s = 0; s < bs; ++s) {
-            const float *fs = h->final_state + (size_t)(s0 + s) * 3 * plane;
-            CU(cudaMemcpyAsync(h->st[0] + s * h->sstride, fs, 3 * plane * sizeof(float),
-                               cudaMemcpyDeviceToDevice, h->work));
-        }
-        CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1, h->st[0] + 3 * plane,
-                                  h->sstride, h->work));
-        h->launches++;
+        CU(launch_pack_adjoint(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
+        CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1,
+                                  reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
+        h->launches += 2;
         CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
             Step2D a = step_args(h, s0);
             for (int i = 0; i < nt; ++i) {
@@ -462,7 +463,7 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
 
 lsrtm_status prep_perturbation(lsrtm_handle *h, const float *dm_dev)
 {
-    CU(launch_pert_prep(h->g, dm_dev, h->kdt, h->binv, h->dkdt, h->rr, h->work));
+    CU(launch_pert_prep(h->g, dm_dev, h->kdt, h->binv, h->kd2, h->br2, h->work));
     h->launches++;
     return LSRTM_OK;
 }
@@ -519,7 +520,7 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "source outside the interior grid");
         src[s] = (int)pad_cell(k);
     }
-    int ntx = (g.Nx + kTX2 - 1) / kTX2, ntz = (g.Nz + kTZ2 - 1) / kTZ2;
+    int ntx = (g.Nx + h->txo - 1) / h->txo, ntz = (g.Nz + h->tzc - 1) / h->tzc;
     int ntiles = ntx * ntz;
     std::vector<std::vector<int2>> lists((size_t)h->nshot * ntiles);
     for (int s = 0; s < h->nshot; ++s)
@@ -528,7 +529,7 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
             if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
             long long cell = pad_cell(k);
             int z = (int)(cell / g.rowz), x = (int)(cell % g.pitch);
-            int t = (z / kTZ2) * ntx + x / kTX2;
+            int t = (z / h->tzc) * ntx + x / h->txo;
             lists[(size_t)s * ntiles + t].push_back(make_int2((int)cell, r));
         }
     std::vector<int> ptr(lists.size() + 1, 0);
@@ -598,6 +599,12 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         g.cx[l] = (float)(cl / cfg->dx);
     }
     h->nint = (long long)g.nz * g.ny * g.nx;
+    // CTA blocking: output columns fixed by the kernel, z-chunks of about 112 rows
+    h->txo = march2d_txo(g.M);
+    {
+        int nchunk = std::max(1, (g.Nz + 56) / 112);
+        h->tzc = (g.Nz + nchunk - 1) / nchunk;
+    }
     h->src_scale = (float)(cfg->dt / (cfg->dz * cfg->dx));
 
     // model on the device
@@ -629,8 +636,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     }
     CHECK(dalloc_t(h, &h->kdt, g.plane));
     CHECK(dalloc_t(h, &h->binv, g.plane));
-    CHECK(dalloc_t(h, &h->dkdt, g.plane));
-    CHECK(dalloc_t(h, &h->rr, g.plane));
+    CHECK(dalloc_t(h, &h->kd2, g.plane));
+    CHECK(dalloc_t(h, &h->br2, g.plane));
     CU(launch_model_prep(g, vp_d, rho_d, h->kdt, h->binv, h->work));
     h->launches++;
 

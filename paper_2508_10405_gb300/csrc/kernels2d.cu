@@ -1,43 +1,64 @@
 // Fused 2D time-step kernels for the staggered-grid Born operator and its
 // exact transpose (Eq. 1, Eq. scattereqln, App. A).
 //
-// One launch advances every shot of a batch by one time step. A CTA owns a
-// TZ x TX tile of integer nodes. It stages the pressure fields on the tile
-// plus a (2M-1)-deep halo in shared memory, recomputes the velocity stage on
-// the tile plus an M-deep halo (redundantly with its neighbours, so no grid
-// barrier is needed between the v and p stages), then finishes the pressure
-// stage on its own tile. Each state field is therefore read once and written
-// once per step; the halo reads are served by L2. Inputs and outputs are
-// separate (ping-pong) buffers, so neighbouring CTAs never race.
+// One launch advances every shot of a batch by one time step. A CTA of 256
+// threads owns one x-column per thread (240 output columns plus 2M halo
+// columns on each side for M = 4) and marches down a z-chunk of the padded
+// grid:
+//   * along z the stencil operands live in per-thread register rings of
+//     length 2M (the march loop is unrolled by 2M, so the rings never move);
+//   * along x each row passes through one shared-memory row per field;
+//   * the global loads of row z + PD - 1 are issued as asynchronous copies
+//     (cp.async, zero-filled out of range) into a PD-deep shared-memory stage
+//     ring while row z is computed;
+//   * a background field and its partner (the scattered field in Born
+//     modelling, the adjoint field in migration) are interleaved as float2 in
+//     HBM, so one 8-byte access and one packed FP32x2 FMA (FFMA2) serve both.
+// For every row the velocity stage (half nodes) is computed on the output
+// columns and the x halo, then the pressure stage (integer nodes), so a time
+// step needs no grid-wide barrier. Inputs and outputs are separate (ping-pong)
+// buffers; each state field is read once and written once per step from HBM.
+#include <algorithm>
+#include <type_traits>
+
 #include "lsrtm_internal.cuh"
 
 namespace lsrtm {
 namespace {
 
-constexpr int TX = kTX2;
-constexpr int TZ = kTZ2;
 constexpr int NTH = kThreads2D;
+constexpr int PD = 4;   // depth of the asynchronous row pipeline
 
-// Field planes of a shot slot.
-// Forward (background + Born): p vx vz psi_px psi_pz | dp dvx dvz dpsi_px dpsi_pz;
-// node CPML memories in place: psi_vx psi_vz dpsi_vx dpsi_vz.
-enum { F_P = 0, F_VX = 1, F_VZ = 2, F_PPX = 3, F_PPZ = 4, F_D = 5 };
-// Adjoint: background p vx vz | lambda p vx vz | lambda psi_px psi_pz psi_vx psi_vz.
-enum { A_P = 0, A_VX = 1, A_VZ = 2, A_LP = 3, A_LVX = 4, A_LVZ = 5, A_LPPX = 6, A_LPPZ = 7,
-       A_LPVX = 8, A_LPVZ = 9 };
+// State layouts, as offsets in float planes within a shot slot.
+// Born: float2 pairs (background, scattered).
+enum { B_P = 0, B_VX = 2, B_VZ = 4, B_PPX = 6, B_PPZ = 8 };
+enum { B_PVX = 0, B_PVZ = 2 };                 // in-place node CPML memories
+// Background only (band saving, pseudo-Hessian): float.
+enum { G_P = 0, G_VX = 1, G_VZ = 2, G_PPX = 3, G_PPZ = 4 };
+enum { G_PVX = 0, G_PVZ = 1 };
+// Adjoint: float2 pairs (background, lambda) and float lambda CPML memories.
+enum { A_PL = 0, A_VX = 2, A_VZ = 4, A_LPPX = 6, A_LPPZ = 7, A_LPVX = 8, A_LPVZ = 9 };
 
-template <int M>
-struct Geo {
-    static constexpr int H = 2 * M - 1;            // pressure halo depth
-    static constexpr int HX = (H + 3) & ~3;         // x halo rounded for float4 loads
-    static constexpr int SX = TX + 2 * HX;
-    static constexpr int SZ = TZ + 2 * H;
-    static constexpr int VXW = TX + 2 * M;          // x half nodes [tx0-M, tx0+TX+M-1)
-    static constexpr int VZH = TZ + 2 * M;          // z half rows  [tz0-M, tz0+TZ+M-1)
-    static constexpr int NVX = TZ * (VXW - 1);
-    static constexpr int NVZ = (VZH - 1) * TX;
-};
+// ---- packed arithmetic for T = float or float2
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 fma_(float a, float2 b, float2 c) { return __ffma2_rn(f2(a), b, c); }
+__device__ __forceinline__ float add_(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 mul_(float a, float2 b) { return __fmul2_rn(f2(a), b); }
+template <class T> __device__ __forceinline__ T zero_();
+template <> __device__ __forceinline__ float zero_<float>() { return 0.f; }
+template <> __device__ __forceinline__ float2 zero_<float2>() { return make_float2(0.f, 0.f); }
+// acc + c (a - b), as two fused multiply-adds
+template <class T>
+__device__ __forceinline__ T tap(float c, T a, T b, T acc) { return fma_(c, a, fma_(-c, b, acc)); }
+__device__ __forceinline__ float xof(float v) { return v; }
+__device__ __forceinline__ float xof(float2 v) { return v.x; }
+__device__ __forceinline__ float yof(float) { return 0.f; }
+__device__ __forceinline__ float yof(float2 v) { return v.y; }
 
+// ---- boundary bands
 __device__ __forceinline__ long long band_xstrip(int iz, int ix, int M, int nz, int nx)
 {
     return ix < 0 ? (long long)iz * M + (ix + M) : (long long)M * nz + (long long)iz * M + (ix - nx);
@@ -50,15 +71,16 @@ __device__ __forceinline__ long long band_zstrip(int iz, int ix, int M, int nz, 
                   : base + (long long)M * nx + (long long)(iz - nz) * nx + ix;
 }
 
+__device__ __forceinline__ bool in_xstrip(int ix, int M, int nx)
+{
+    return (ix >= -M && ix < 0) || (ix >= nx && ix < nx + M);
+}
+
 // Band slot of a node for the p band, -1 if the node is not in it.
 __device__ __forceinline__ long long pband_index(int iz, int ix, int M, int nz, int nx)
 {
-    if (iz >= 0 && iz < nz) {
-        if ((ix >= -M && ix < 0) || (ix >= nx && ix < nx + M)) return band_xstrip(iz, ix, M, nz, nx);
-        return -1;
-    }
-    if (ix >= 0 && ix < nx && ((iz >= -M && iz < 0) || (iz >= nz && iz < nz + M)))
-        return band_zstrip(iz, ix, M, nz, nx);
+    if (iz >= 0 && iz < nz) return in_xstrip(ix, M, nx) ? band_xstrip(iz, ix, M, nz, nx) : -1;
+    if (ix >= 0 && ix < nx && in_xstrip(iz, M, nz)) return band_zstrip(iz, ix, M, nz, nx);
     return -1;
 }
 
@@ -74,575 +96,750 @@ __device__ __forceinline__ float band_get(const Bands &b, const void *base, long
     return reinterpret_cast<const float *>(base)[off];
 }
 
-// Loads a (SZ x SX) box of one field starting at (tz0-H, tx0-HX) with 128-bit
-// loads; cells outside the padded array read as zero.
-template <int M>
-__device__ __forceinline__ void load_box(float *dst, const float *src, const GridDev &g, int tz0,
-                                         int tx0)
+// ---- asynchronous copies (pred = false zero-fills the destination)
+template <class T>
+__device__ __forceinline__ void cpa(T *dst, const T *src, bool pred)
 {
-    using G = Geo<M>;
-    constexpr int SX4 = G::SX / 4;
-    for (int i = threadIdx.x; i < G::SZ * SX4; i += NTH) {
-        int rz = i / SX4, q = i - rz * SX4;
-        int z = tz0 - G::H + rz, x = tx0 - G::HX + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (z >= 0 && z < g.Nz && x >= 0 && x < g.pitch)
-            v = __ldg(reinterpret_cast<const float4 *>(src + (long long)z * g.pitch + x));
-        *reinterpret_cast<float4 *>(dst + rz * G::SX + 4 * q) = v;
-    }
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte copies");
+    unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    int n = pred ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Waits until at most PD-1 of this thread's copy groups are pending.
+__device__ __forceinline__ void cp_wait_row() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PD - 1) : "memory"); }
+
+template <int M>
+struct Cols {
+    static constexpr int W = 2 * M;            // ring length along z
+    static constexpr int HXP = 2 * M;          // halo columns per side
+    static constexpr int TXO = NTH - 2 * HXP;  // output columns per CTA
+};
+
+// Stage ring of the forward kernel: 8 fields of 8-byte slots per thread.
+constexpr int kFwdSlots = 8;
+constexpr size_t kFwdStageSlotBytes = (size_t)kFwdSlots * NTH * 8;
+constexpr size_t kFwdStageBytes = PD * kFwdStageSlotBytes;
+// Stage ring of the adjoint kernel: 5 float2 fields then 9 float fields.
+constexpr int kAdjF2 = 5, kAdjF1 = 9;
+constexpr size_t kAdjStageFloats = (size_t)(2 * kAdjF2 + kAdjF1) * NTH;
+constexpr size_t kAdjStageBytes = PD * kAdjStageFloats * sizeof(float);
+
 // ---------------------------------------------------------------------------
-// Forward step: background (and, if BORN, the scattered field) from step n to
-// n+1. BANDS saves the boundary bands of p^n and v^{n+1/2}; HESS accumulates
-// the pseudo-Hessian diagonal of App. B.
+// Forward step from n to n+1. BORN: the background and the scattered field as
+// float2 pairs (Eq. scattereqln driven by the background). Otherwise the
+// background alone as float, with BANDS saving the boundary bands of p^n and
+// v^{n+1/2} and HESS accumulating the pseudo-Hessian diagonal of App. B.
 // ---------------------------------------------------------------------------
-template <int M, bool BORN, bool BANDS, bool HESS>
-__global__ void __launch_bounds__(NTH) k_fwd2d(const Step2D a)
+template <bool BORN>
+struct FwdT {
+    using T = typename std::conditional<BORN, float2, float>::type;   // state (pair)
+    using R = typename std::conditional<BORN, float2, float>::type;   // (1/rho, rr) or 1/rho
+    using K = typename std::conditional<BORN, float2, float>::type;   // (dt kappa, dt kappa dlnk) or dt kappa
+};
+
+template <bool BORN>
+struct FwdRow {
+    using T = typename FwdT<BORN>::T;
+    using R = typename FwdT<BORN>::R;
+    using K = typename FwdT<BORN>::K;
+    T p;      // node row z + 2M - 1 (look-ahead of the z rings)
+    T vz;     // half row k = z + M - 1
+    T psz;    // psi_pz at half row k (CPML rows)
+    T vx;     // row z
+    T psx;    // psi_px at row z (CPML columns)
+    R br1;    // 1/rho (, rr) at row k + 1
+    R brz;    // 1/rho (, rr) at row z
+    K kd;     // dt kappa (, dt kappa dlnk) at row z
+};
+
+template <int M, bool BORN>
+__device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float *in, int xc, int z,
+                                          int zc0, int zc1, bool colok, bool vxok, bool outcol,
+                                          bool pmlxh)
 {
-    using G = Geo<M>;
-    constexpr int NF = BORN ? 2 : 1;
-    constexpr int H = G::H, HX = G::HX, SX = G::SX, SZ = G::SZ, VXW = G::VXW;
-    extern __shared__ __align__(16) float smem[];
-    float *sP = smem;                       // [NF][SZ][SX]
-    float *sVx = sP + NF * SZ * SX;         // [NF][TZ][VXW]
-    float *sVz = sVx + NF * TZ * VXW;       // [NF][VZH][TX]
-    float *sHx = sVz + NF * G::VZH * TX;    // [TZ][TX+1]
-    float *sHz = sHx + TZ * (TX + 1);       // [TZ+1][TX]
+    using T = typename FwdT<BORN>::T;
+    using R = typename FwdT<BORN>::R;
+    using K = typename FwdT<BORN>::K;
+    const GridDev &g = a.g;
+    const int pitch = g.pitch;
+    const int W = 2 * M;
+    char *sl = st + threadIdx.x * 8;
+    const T *fin = reinterpret_cast<const T *>(in);
+    const R *br = BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv);
+    const K *kk = BORN ? reinterpret_cast<const K *>(a.kd2) : reinterpret_cast<const K *>(a.kdt);
+    const long long pT = g.plane;   // cells per plane: the stride of one (pair) field in units of T
+    const int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
+    const int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
+    const int zr = z + W - 1, k = z + M - 1;
+    const bool okr = colok && zr >= 0 && zr < g.Nz;
+    const long long cr = okr ? (long long)zr * pitch + xc : 0;
+    const bool okk1 = colok && k + 1 >= 0;
+    const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
+    const bool okk = colok && k >= 0 && k < g.Nz;
+    const long long ck = okk ? (long long)k * pitch + xc : 0;
+    const bool pz = okk && ((k <= g.z0 - 2) || (k >= g.z0 + g.nz));
+    const bool main = z >= zc0 && z < zc1;
+    const bool okz = colok && main;
+    const long long cz = okz ? (long long)z * pitch + xc : 0;
+    const bool okv = vxok && main;
+    const bool oko = outcol && main;
+    constexpr size_t F = (size_t)NTH * 8;   // bytes between field rows of a stage
+    cpa(reinterpret_cast<T *>(sl + 0 * F), fin + oP * pT + cr, okr);
+    cpa(reinterpret_cast<T *>(sl + 1 * F), fin + oVZ * pT + ck, okk);
+    cpa(reinterpret_cast<T *>(sl + 2 * F), fin + oPPZ * pT + ck, pz);
+    cpa(reinterpret_cast<T *>(sl + 3 * F), fin + oVX * pT + cz, okv);
+    cpa(reinterpret_cast<T *>(sl + 4 * F), fin + oPPX * pT + cz, okv && pmlxh);
+    cpa(reinterpret_cast<R *>(sl + 5 * F), br + ck1, okk1);
+    cpa(reinterpret_cast<R *>(sl + 6 * F), br + cz, okz);
+    cpa(reinterpret_cast<K *>(sl + 7 * F), kk + cz, oko);
+}
+
+template <bool BORN>
+__device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
+{
+    using T = typename FwdT<BORN>::T;
+    using R = typename FwdT<BORN>::R;
+    using K = typename FwdT<BORN>::K;
+    const char *sl = st + threadIdx.x * 8;
+    constexpr size_t F = (size_t)NTH * 8;
+    FwdRow<BORN> r;
+    r.p = *reinterpret_cast<const T *>(sl + 0 * F);
+    r.vz = *reinterpret_cast<const T *>(sl + 1 * F);
+    r.psz = *reinterpret_cast<const T *>(sl + 2 * F);
+    r.vx = *reinterpret_cast<const T *>(sl + 3 * F);
+    r.psx = *reinterpret_cast<const T *>(sl + 4 * F);
+    r.br1 = *reinterpret_cast<const R *>(sl + 5 * F);
+    r.brz = *reinterpret_cast<const R *>(sl + 6 * F);
+    r.kd = *reinterpret_cast<const K *>(sl + 7 * F);
+    return r;
+}
+
+template <int M, bool BORN, bool BANDS, bool HESS>
+__global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
+{
+    using C = Cols<M>;
+    using T = typename FwdT<BORN>::T;
+    using R = typename FwdT<BORN>::R;
+    constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
+    __shared__ T sP[NTH];
+    __shared__ R sB[NTH];
+    __shared__ T sV[NTH];
+    __shared__ float sH[HESS ? NTH : 1];
+    extern __shared__ __align__(16) char stages[];   // [PD][kFwdSlots][NTH] x 8 bytes
 
     const GridDev &g = a.g;
-    const int tid = threadIdx.x;
-    const int tx0 = blockIdx.x * TX, tz0 = blockIdx.y * TZ;
+    const int t = threadIdx.x;
+    const int x = (int)blockIdx.x * TXO - HXP + t;
+    const bool colok = x >= 0 && x < g.Nx;
+    const bool outcol = colok && t >= HXP && t < HXP + TXO;
+    const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
+    const int zc0 = (int)blockIdx.y * a.tzc;
+    const int zc1 = min(zc0 + a.tzc, g.Nz);
+    const int zstart = zc0 - W;
     const int slot = blockIdx.z, shot = a.shot0 + slot;
-    const int pitch = g.pitch;
     const long long plane = g.plane;
+    const long long pT = plane;   // cells per plane: the stride of one (pair) field in units of T
+    const int pitch = g.pitch;
+    const int xc = colok ? x : 0;
     const float *in = a.in + slot * a.sstride;
-    float *out = a.out + slot * a.sstride;
-    float *psiv = a.psiv + slot * a.vstride;
+    T *out = reinterpret_cast<T *>(a.out + slot * a.sstride) + xc;
+    T *psiv = reinterpret_cast<T *>(a.psiv + slot * a.vstride) + xc;
     const float dt = g.dt;
     const int x0 = g.x0, x1 = g.x0 + g.nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const int ix = x - x0;
+    const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
+    const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
+    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
     const long long bandoff = ((long long)shot * g.nt + a.n) * a.bands.nb;
-
-    load_box<M>(sP, in + F_P * plane, g, tz0, tx0);
-    if (BORN) load_box<M>(sP + SZ * SX, in + (F_D + F_P) * plane, g, tz0, tx0);
-    __syncthreads();
-
-    // ---- velocity stage along x on the tile + M halo
-    for (int i = tid; i < G::NVX; i += NTH) {
-        int r = i / (VXW - 1), ci = i - r * (VXW - 1);
-        int z = tz0 + r, j = tx0 - M + ci;
-        float vn = 0.f, dvn = 0.f, hq = 0.f;
-        if (z < g.Nz && j >= 0 && j < g.Nx) {
-            const float *pr = sP + (r + H) * SX + (ci - M + HX);
-            float dp = 0.f;
-#pragma unroll
-            for (int l = 1; l <= M; ++l) dp += g.cx[l - 1] * (pr[l] - pr[1 - l]);
-            long long cell = (long long)z * pitch + j;
-            bool own = ci >= M && ci < M + TX;
-            bool pml = (j <= x0 - 2) || (j >= x1);
-            float Gx = dp;
-            if (pml) {
-                float ps = a.pml.bh[2][j] * __ldg(in + F_PPX * plane + cell) + a.pml.ah[2][j] * dp;
-                Gx += ps;
-                if (own) out[F_PPX * plane + cell] = ps;
-            }
-            float bu = 0.5f * (__ldg(a.binv + cell) + __ldg(a.binv + (j + 1 < g.Nx ? cell + 1 : cell)));
-            float dtbu = dt * bu;
-            vn = __ldg(in + F_VX * plane + cell) - dtbu * Gx;
-            if (BORN) {
-                const float *dr = pr + SZ * SX;
-                float ddp = 0.f;
-#pragma unroll
-                for (int l = 1; l <= M; ++l) ddp += g.cx[l - 1] * (dr[l] - dr[1 - l]);
-                float Gd = ddp;
-                if (pml) {
-                    float ps = a.pml.bh[2][j] * __ldg(in + (F_D + F_PPX) * plane + cell) +
-                               a.pml.ah[2][j] * ddp;
-                    Gd += ps;
-                    if (own) out[(F_D + F_PPX) * plane + cell] = ps;
-                }
-                float r0 = __ldg(a.rr + cell), r1 = (j + 1 < g.Nx) ? __ldg(a.rr + cell + 1) : 0.f;
-                float dtdbu = -0.5f * dt * (r0 + r1);
-                dvn = __ldg(in + (F_D + F_VX) * plane + cell) - dtbu * Gd - dtdbu * Gx;
-            }
-            if (own) {
-                out[F_VX * plane + cell] = vn;
-                if (BORN) out[(F_D + F_VX) * plane + cell] = dvn;
-                if (BANDS) {
-                    int iz = z - z0, ix = j - x0;
-                    if (iz >= 0 && iz < g.nz && ((ix >= -M && ix < 0) || (ix >= g.nx && ix < g.nx + M)))
-                        band_put(a.bands, a.bands.v, bandoff + band_xstrip(iz, ix, M, g.nz, g.nx), vn);
-                }
-            }
-            if (HESS) { float t = bu * Gx; hq = t * t; }
-        }
-        sVx[r * VXW + ci] = vn;
-        if (BORN) sVx[TZ * VXW + r * VXW + ci] = dvn;
-        if (HESS && ci >= M - 1 && ci < M + TX) sHx[r * (TX + 1) + (ci - M + 1)] = hq;
-    }
-    // ---- velocity stage along z on the tile + M halo
-    for (int i = tid; i < G::NVZ; i += NTH) {
-        int r = i / TX, c = i - r * TX;
-        int k = tz0 - M + r, x = tx0 + c;
-        float vn = 0.f, dvn = 0.f, hq = 0.f;
-        if (k >= 0 && k < g.Nz && x < g.Nx) {
-            const float *pc = sP + (r - M + H) * SX + (c + HX);
-            float dp = 0.f;
-#pragma unroll
-            for (int l = 1; l <= M; ++l) dp += g.cz[l - 1] * (pc[l * SX] - pc[(1 - l) * SX]);
-            long long cell = (long long)k * pitch + x;
-            bool own = r >= M && r < M + TZ;
-            bool pml = (k <= z0 - 2) || (k >= z1);
-            float Gz = dp;
-            if (pml) {
-                float ps = a.pml.bh[0][k] * __ldg(in + F_PPZ * plane + cell) + a.pml.ah[0][k] * dp;
-                Gz += ps;
-                if (own) out[F_PPZ * plane + cell] = ps;
-            }
-            float bu = 0.5f * (__ldg(a.binv + cell) + __ldg(a.binv + (k + 1 < g.Nz ? cell + pitch : cell)));
-            float dtbu = dt * bu;
-            vn = __ldg(in + F_VZ * plane + cell) - dtbu * Gz;
-            if (BORN) {
-                const float *dc = pc + SZ * SX;
-                float ddp = 0.f;
-#pragma unroll
-                for (int l = 1; l <= M; ++l) ddp += g.cz[l - 1] * (dc[l * SX] - dc[(1 - l) * SX]);
-                float Gd = ddp;
-                if (pml) {
-                    float ps = a.pml.bh[0][k] * __ldg(in + (F_D + F_PPZ) * plane + cell) +
-                               a.pml.ah[0][k] * ddp;
-                    Gd += ps;
-                    if (own) out[(F_D + F_PPZ) * plane + cell] = ps;
-                }
-                float r0 = __ldg(a.rr + cell), r1 = (k + 1 < g.Nz) ? __ldg(a.rr + cell + pitch) : 0.f;
-                float dtdbu = -0.5f * dt * (r0 + r1);
-                dvn = __ldg(in + (F_D + F_VZ) * plane + cell) - dtbu * Gd - dtdbu * Gz;
-            }
-            if (own) {
-                out[F_VZ * plane + cell] = vn;
-                if (BORN) out[(F_D + F_VZ) * plane + cell] = dvn;
-                if (BANDS) {
-                    int iz = k - z0, ix = x - x0;
-                    if (ix >= 0 && ix < g.nx && ((iz >= -M && iz < 0) || (iz >= g.nz && iz < g.nz + M)))
-                        band_put(a.bands, a.bands.v, bandoff + band_zstrip(iz, ix, M, g.nz, g.nx), vn);
-                }
-            }
-            if (HESS) { float t = bu * Gz; hq = t * t; }
-        }
-        sVz[r * TX + c] = vn;
-        if (BORN) sVz[G::VZH * TX + r * TX + c] = dvn;
-        if (HESS && r >= M - 1 && r < M + TZ) sHz[(r - M + 1) * TX + c] = hq;
-    }
-    __syncthreads();
-
-    // ---- pressure stage on the own tile
     const int src = a.src_cell[shot];
     const float wsrc = a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + a.n];
-    for (int i = tid; i < TZ * TX; i += NTH) {
-        int r = i / TX, c = i - r * TX;
-        int z = tz0 + r, x = tx0 + c;
-        if (z >= g.Nz || x >= g.Nx) continue;
-        long long cell = (long long)z * pitch + x;
-        const float *vxr = sVx + r * VXW + c + M;
-        const float *vzc = sVz + (r + M) * TX + c;
-        float qx = 0.f, qz = 0.f;
+    constexpr int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
+    constexpr int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
+    constexpr int oPVX = BORN ? B_PVX / 2 : G_PVX, oPVZ = BORN ? B_PVZ / 2 : G_PVZ;
+
+    T P[W], VZ[W];
+    float HZ[HESS ? W : 1];
 #pragma unroll
-        for (int l = 1; l <= M; ++l) {
-            qx += g.cx[l - 1] * (vxr[l - 1] - vxr[-l]);
-            qz += g.cz[l - 1] * (vzc[(l - 1) * TX] - vzc[-l * TX]);
-        }
-        bool pmlx = (x <= x0 - 1) || (x >= x1);
-        bool pmlz = (z <= z0 - 1) || (z >= z1);
-        float dqx = 0.f, dqz = 0.f;
-        if (BORN) {
-            const float *dvxr = vxr + TZ * VXW;
-            const float *dvzc = vzc + G::VZH * TX;
+    for (int j = 0; j < W; ++j) {
+        P[j] = zero_<T>();
+        VZ[j] = zero_<T>();
+        if (HESS) HZ[j] = 0.f;
+    }
+    {
+        const T *pin = reinterpret_cast<const T *>(in) + oP * pT + xc;
 #pragma unroll
-            for (int l = 1; l <= M; ++l) {
-                dqx += g.cx[l - 1] * (dvxr[l - 1] - dvxr[-l]);
-                dqz += g.cz[l - 1] * (dvzc[(l - 1) * TX] - dvzc[-l * TX]);
+        for (int j = 0; j < W - 1; ++j) {
+            int zr = zstart + j;
+            P[j] = (colok && zr >= 0 && zr < g.Nz) ? pin[(long long)zr * pitch] : zero_<T>();
+        }
+    }
+    R br_old = zero_<R>();
+    {
+        const R *br = BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv);
+        int k = zstart + M - 1;
+        if (colok && k >= 0 && k < g.Nz) br_old = br[(long long)k * pitch + xc];
+    }
+
+#pragma unroll
+    for (int j = 0; j < PD - 1; ++j) {
+        if (zstart + j < zc1)
+            fwd_issue<M, BORN>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
+                               outcol, pmlxh);
+        cp_commit();
+    }
+
+    for (int zb = zstart; zb < zc1; zb += W) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int z = zb + u;
+            if (z >= zc1) break;
+            const int zi = z + PD - 1;
+            if (zi < zc1)
+                fwd_issue<M, BORN>(stages + ((zi - zstart) % PD) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
+                                   colok, vxok, outcol, pmlxh);
+            cp_commit();
+            cp_wait_row();
+            const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PD) * kFwdStageSlotBytes);
+            const int k = z + M - 1;   // half row of vz computed in this iteration
+            const int sl = (u + W - 1) % W;
+            P[sl] = cur.p;
+            // ---- vz at half row k (column-local)
+            const float buz = 0.5f * (xof(br_old) + xof(cur.br1));
+            const float rsum = yof(br_old) + yof(cur.br1);
+            br_old = cur.br1;
+            T vzn = zero_<T>();
+            float hzq = 0.f;
+            if (colok && k >= 0 && k < g.Nz) {
+                const long long ck = (long long)k * pitch;
+                const bool own = outcol && k >= zc0 && k < zc1;
+                T G = zero_<T>();
+#pragma unroll
+                for (int l = 1; l <= M; ++l) G = tap(g.cz[l - 1], P[(u + M - 1 + l) % W], P[(u + M - l) % W], G);
+                if ((k <= z0 - 2) || (k >= z1)) {
+                    T ps = fma_(a.pml.bh[0][k], cur.psz, mul_(a.pml.ah[0][k], G));
+                    if (own) out[oPPZ * pT + ck] = ps;
+                    G = add_(G, ps);
+                }
+                const float dtbu = dt * buz;
+                vzn = fma_(-dtbu, G, cur.vz);
+                if constexpr (BORN) vzn.y = fmaf(0.5f * dt * rsum, G.x, vzn.y);
+                if (own) {
+                    out[oVZ * pT + ck] = vzn;
+                    if (BANDS) {
+                        int iz = k - z0;
+                        if (ix >= 0 && ix < g.nx && in_xstrip(iz, M, g.nz))
+                            band_put(a.bands, a.bands.v, bandoff + band_zstrip(iz, ix, M, g.nz, g.nx), xof(vzn));
+                    }
+                }
+                if (HESS) {
+                    float q = buz * xof(G);
+                    hzq = q * q;
+                }
             }
-        }
-        if (pmlx) {
-            float ps = a.pml.bi[2][x] * psiv[0 * plane + cell] + a.pml.ai[2][x] * qx;
-            psiv[0 * plane + cell] = ps;
-            qx += ps;
-            if (BORN) {
-                float ds = a.pml.bi[2][x] * psiv[2 * plane + cell] + a.pml.ai[2][x] * dqx;
-                psiv[2 * plane + cell] = ds;
-                dqx += ds;
+            VZ[sl] = vzn;
+            if (HESS) HZ[sl] = hzq;
+            if (z < zc0) continue;   // warm-up rows of the z rings
+
+            // ---- row z: vx on the output columns and the halo
+            const long long cz = (long long)z * pitch;
+            const T p0 = P[u];
+            sP[t] = p0;
+            sB[t] = cur.brz;
+            __syncthreads();
+            T vxn = zero_<T>();
+            float hxq = 0.f;
+            if (vxok) {
+                T G = zero_<T>();
+#pragma unroll
+                for (int l = 1; l <= M; ++l) G = tap(g.cx[l - 1], sP[t + l], sP[t + 1 - l], G);
+                const bool last = x + 1 >= g.Nx;
+                const R bn = last ? cur.brz : sB[t + 1];
+                const float bux = 0.5f * (xof(cur.brz) + xof(bn));
+                if (pmlxh) {
+                    T ps = fma_(bhx, cur.psx, mul_(ahx, G));
+                    if (outcol) out[oPPX * pT + cz] = ps;
+                    G = add_(G, ps);
+                }
+                const float dtbu = dt * bux;
+                vxn = fma_(-dtbu, G, cur.vx);
+                if constexpr (BORN) {
+                    float rs = yof(cur.brz) + (last ? 0.f : yof(bn));
+                    vxn.y = fmaf(0.5f * dt * rs, G.x, vxn.y);
+                }
+                if (outcol) {
+                    out[oVX * pT + cz] = vxn;
+                    if (BANDS) {
+                        int iz = z - z0;
+                        if (iz >= 0 && iz < g.nz && in_xstrip(ix, M, g.nx))
+                            band_put(a.bands, a.bands.v, bandoff + band_xstrip(iz, ix, M, g.nz, g.nx), xof(vxn));
+                    }
+                }
+                if (HESS) {
+                    float q = bux * xof(G);
+                    hxq = q * q;
+                }
             }
-        }
-        if (pmlz) {
-            float ps = a.pml.bi[0][z] * psiv[1 * plane + cell] + a.pml.ai[0][z] * qz;
-            psiv[1 * plane + cell] = ps;
-            qz += ps;
-            if (BORN) {
-                float ds = a.pml.bi[0][z] * psiv[3 * plane + cell] + a.pml.ai[0][z] * dqz;
-                psiv[3 * plane + cell] = ds;
-                dqz += ds;
-            }
-        }
-        float Q = qx + qz;
-        float kd = __ldg(a.kdt + cell);
-        float p0 = sP[(r + H) * SX + c + HX];
-        float pn = p0 - kd * Q;
-        if (cell == src) pn += wsrc;
-        out[F_P * plane + cell] = pn;
-        if (BORN) {
-            float dp0 = sP[SZ * SX + (r + H) * SX + c + HX];
-            out[(F_D + F_P) * plane + cell] = dp0 - kd * (dqx + dqz) - __ldg(a.dkdt + cell) * Q;
-        }
-        if (BANDS) {
-            long long b = pband_index(z - z0, x - x0, M, g.nz, g.nx);
-            if (b >= 0) band_put(a.bands, a.bands.p, bandoff + b, p0);
-        }
-        if (HESS) {
-            int iz = z - z0, ix = x - x0;
-            if (iz >= 0 && iz < g.nz && ix >= 0 && ix < g.nx) {
-                float bi = __ldg(a.binv + cell);
-                float hr = 0.5f * (sHx[r * (TX + 1) + c + 1] + sHx[r * (TX + 1) + c] +
-                                   sHz[(r + 1) * TX + c] + sHz[r * TX + c]) / (bi * bi);
-                float kq = kd * Q / dt;
-                a.hess[slot * plane + cell] += dt * (hr + kq * kq);
+            sV[t] = vxn;
+            if (HESS) sH[t] = hxq;
+            __syncthreads();
+
+            // ---- row z: pressure on the output columns
+            if (outcol) {
+                T qx = zero_<T>(), qz = zero_<T>();
+#pragma unroll
+                for (int l = 1; l <= M; ++l) {
+                    qx = tap(g.cx[l - 1], sV[t + l - 1], sV[t - l], qx);
+                    qz = tap(g.cz[l - 1], VZ[(u + M + l - 1) % W], VZ[(u + M - l) % W], qz);
+                }
+                if (pmlxn) {
+                    T ps = fma_(bix, psiv[oPVX * pT + cz], mul_(aix, qx));
+                    psiv[oPVX * pT + cz] = ps;
+                    qx = add_(qx, ps);
+                }
+                if ((z <= z0 - 1) || (z >= z1)) {
+                    T ps = fma_(a.pml.bi[0][z], psiv[oPVZ * pT + cz], mul_(a.pml.ai[0][z], qz));
+                    psiv[oPVZ * pT + cz] = ps;
+                    qz = add_(qz, ps);
+                }
+                const T Q = add_(qx, qz);
+                const float kd = xof(cur.kd);
+                T pn = fma_(-kd, Q, p0);
+                if constexpr (BORN) {
+                    pn.y = fmaf(-cur.kd.y, Q.x, pn.y);
+                    if (cz + x == src) pn.x += wsrc;
+                } else {
+                    if (cz + x == src) pn += wsrc;
+                }
+                out[oP * pT + cz] = pn;
+                if (BANDS) {
+                    long long b = pband_index(z - z0, ix, M, g.nz, g.nx);
+                    if (b >= 0) band_put(a.bands, a.bands.p, bandoff + b, xof(p0));
+                }
+                if (HESS) {
+                    int iz = z - z0;
+                    if (iz >= 0 && iz < g.nz && ix >= 0 && ix < g.nx) {
+                        float bx0 = xof(cur.brz);
+                        float hr = 0.5f * ((sH[t] + sH[t - 1]) + (HZ[(u + M) % W] + HZ[(u + M - 1) % W])) /
+                                   (bx0 * bx0);
+                        float kq = kd * xof(Q) / dt;
+                        a.hess[slot * plane + cz + xc] += dt * (hr + kq * kq);
+                    }
+                }
             }
         }
     }
 
     if (BORN) {
-        // record dp^{n+1} at the receivers of this tile
+        // record dp^{n+1} at the receivers of this CTA
         __syncthreads();
-        int t = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
-        int b = a.trec.ptr[t], e = a.trec.ptr[t + 1];
-        for (int i = b + tid; i < e; i += NTH) {
+        int tile = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+        int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
+        const float2 *po = reinterpret_cast<const float2 *>(a.out + slot * a.sstride + B_P * plane);
+        for (int i = b + t; i < e; i += NTH) {
             int2 rc = a.trec.rec[i];
-            a.dstage[(long long)rc.y * g.nt + a.n] = out[(F_D + F_P) * plane + rc.x];
+            a.dstage[(long long)rc.y * g.nt + a.n] = po[rc.x].y;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Reverse step n (n = nt-1 .. 0) of L^T. Input state: background p^n,
-// v^{n+1/2}; adjoint lambda_p (with the residual of step n already added),
-// lambda_v, CPML memories. The step applies the transposed Born sub-steps
-// S4^T, S3^T, S2^T, S1^T, accumulates the two zero-lag images (Eqs. gradkappa,
-// gradrho in their discrete transposed form), reconstructs p^{n-1}, v^{n-1/2}
+// Reverse step n (n = nt-1 .. 0) of L^T. Input state: (background p^n,
+// lambda_p) with the residual of step n already added, (v^{n+1/2}, lambda_v)
+// and the lambda CPML memories. The step applies the transposed Born
+// sub-steps (S4^T, S3^T on the half nodes from lambda_p; S2^T, S1^T on the
+// nodes from lambda_v), accumulates the two zero-lag images (discrete
+// transposed forms of Eqs. gradkappa, gradrho), rebuilds p^{n-1}, v^{n-1/2}
 // in the interior from the saved boundary bands, and pre-adds the residual of
-// step n-1 to the new lambda_p.
+// step n-1. The D+ stencils of (p^n, u) and the D- stencils of (v^{n+1/2}, w)
+// run as packed pairs.
 // ---------------------------------------------------------------------------
+struct AdjRow {
+    float2 pl;      // node row r = z + 2M - 1: (p^n, lambda_p)
+    float2 v2z;     // half row k: (vz^{n+1/2}, lambda_vz)
+    float2 plz;     // row z: (p^n, lambda_p)
+    float2 v2x;     // row z: (vx^{n+1/2}, lambda_vx)
+    float2 img;     // row z: image accumulators
+    float kdr, lpvzr, bz, lppz, kdz, lpsvx, lpsvz, bx, lppx;
+};
+
 template <int M>
-__global__ void __launch_bounds__(NTH) k_adj2d(const Step2D a)
+__device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const float2 *img, const float *in,
+                                          int xc, int z, int zc0, int zc1, bool colok, bool vxok,
+                                          bool outcol, bool pmlxh, bool pmlxn, bool inner_col)
 {
-    using G = Geo<M>;
-    constexpr int H = G::H, HX = G::HX, SX = G::SX, SZ = G::SZ, VXW = G::VXW, VZH = G::VZH;
-    constexpr int SX4 = SX / 4;
-    extern __shared__ __align__(16) float smem[];
-    float *sP = smem;                 // [SZ][SX] background p^n
-    float *sUx = sP + SZ * SX;        // [SZ][SX] kdt*lp - ai_x*(lpsi_vx - kdt*lp)
-    float *sUz = sUx + SZ * SX;       // [SZ][SX] same along z
-    float *sVxo = sUz + SZ * SX;      // [TZ][VXW] background vx^{n+1/2}
-    float *sVxn = sVxo + TZ * VXW;    // [TZ][VXW] background vx^{n-1/2}
-    float *sWx = sVxn + TZ * VXW;     // [TZ][VXW] dt*bu*lvx - ah*lpsi_px
-    float *sVzo = sWx + TZ * VXW;     // [VZH][TX]
-    float *sVzn = sVzo + VZH * TX;
-    float *sWz = sVzn + VZH * TX;
-    float *sPix = sWz + VZH * TX;     // [TZ][TX+1]  Gx*lvx at half nodes tx0-1 .. tx0+TX-1
-    float *sPiz = sPix + TZ * (TX + 1);  // [TZ+1][TX]
+    const GridDev &g = a.g;
+    const long long plane = g.plane;
+    const long long p2 = plane;   // cells per plane: the stride of one pair field in float2 units
+    const int pitch = g.pitch;
+    const int W = 2 * M;
+    const int z0 = g.z0, z1 = g.z0 + g.nz;
+    const int t = threadIdx.x;
+    float2 *s2 = reinterpret_cast<float2 *>(st) + t;
+    float *s1 = st + 2 * kAdjF2 * NTH + t;
+    const float2 *in2 = reinterpret_cast<const float2 *>(in);
+    const int zr = z + W - 1, k = z + M - 1;
+    const bool okr = colok && zr >= 0 && zr < g.Nz;
+    const long long cr = okr ? (long long)zr * pitch + xc : 0;
+    const bool okk = colok && k >= 0 && k < g.Nz;
+    const long long ck = okk ? (long long)k * pitch + xc : 0;
+    const bool okk1 = colok && k + 1 >= 0;
+    const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
+    const bool main = z >= zc0 && z < zc1;
+    const bool okz = colok && main;
+    const long long cz = okz ? (long long)z * pitch + xc : 0;
+    const bool okv = vxok && main;
+    const int iz = z - z0;
+    cpa(s2 + 0 * NTH, in2 + (A_PL / 2) * p2 + cr, okr);
+    cpa(s2 + 1 * NTH, in2 + (A_VZ / 2) * p2 + ck, okk);
+    cpa(s2 + 2 * NTH, in2 + (A_PL / 2) * p2 + cz, okz);
+    cpa(s2 + 3 * NTH, in2 + (A_VX / 2) * p2 + cz, okv);
+    cpa(s2 + 4 * NTH, img + cz, outcol && main && inner_col && iz >= 0 && iz < g.nz);
+    cpa(s1 + 0 * NTH, a.kdt + cr, okr);
+    cpa(s1 + 1 * NTH, in + A_LPVZ * plane + cr, okr && ((zr <= z0 - 1) || (zr >= z1)));
+    cpa(s1 + 2 * NTH, a.binv + ck1, okk1);
+    cpa(s1 + 3 * NTH, in + A_LPPZ * plane + ck, okk && ((k <= z0 - 2) || (k >= z1)));
+    cpa(s1 + 4 * NTH, a.kdt + cz, okz);
+    cpa(s1 + 5 * NTH, in + A_LPVX * plane + cz, okz && pmlxn);
+    cpa(s1 + 6 * NTH, in + A_LPVZ * plane + cz, outcol && main && ((z <= z0 - 1) || (z >= z1)));
+    cpa(s1 + 7 * NTH, a.binv + cz, okz);
+    cpa(s1 + 8 * NTH, in + A_LPPX * plane + cz, okv && pmlxh);
+}
+
+__device__ __forceinline__ AdjRow adj_read(const float *st)
+{
+    const int t = threadIdx.x;
+    const float2 *s2 = reinterpret_cast<const float2 *>(st) + t;
+    const float *s1 = st + 2 * kAdjF2 * NTH + t;
+    AdjRow r;
+    r.pl = s2[0 * NTH];
+    r.v2z = s2[1 * NTH];
+    r.plz = s2[2 * NTH];
+    r.v2x = s2[3 * NTH];
+    r.img = s2[4 * NTH];
+    r.kdr = s1[0 * NTH];
+    r.lpvzr = s1[1 * NTH];
+    r.bz = s1[2 * NTH];
+    r.lppz = s1[3 * NTH];
+    r.kdz = s1[4 * NTH];
+    r.lpsvx = s1[5 * NTH];
+    r.lpsvz = s1[6 * NTH];
+    r.bx = s1[7 * NTH];
+    r.lppx = s1[8 * NTH];
+    return r;
+}
+
+template <int M>
+__global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
+{
+    using C = Cols<M>;
+    constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
+    __shared__ float2 sPU[NTH];   // (p^n, kdt*lp - ai_x (lpsi_vx - kdt*lp)), row z
+    __shared__ float sB[NTH];     // 1/rho, row z
+    __shared__ float2 sVW[NTH];   // (vx^{n+1/2}, dt*bu_x*lvx - ah_x*lpsi_px), row z
+    __shared__ float sVN[NTH];    // vx^{n-1/2}, row z
+    __shared__ float sPi[NTH];    // Gx * lvx, row z
+    extern __shared__ __align__(16) float stagef[];   // [PD][kAdjStageFloats]
 
     const GridDev &g = a.g;
-    const int tid = threadIdx.x;
-    const int tx0 = blockIdx.x * TX, tz0 = blockIdx.y * TZ;
+    const int t = threadIdx.x;
+    const int x = (int)blockIdx.x * TXO - HXP + t;
+    const bool colok = x >= 0 && x < g.Nx;
+    const bool outcol = colok && t >= HXP && t < HXP + TXO;
+    const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
+    const int zc0 = (int)blockIdx.y * a.tzc;
+    const int zc1 = min(zc0 + a.tzc, g.Nz);
+    const int zstart = zc0 - W;
     const int slot = blockIdx.z, shot = a.shot0 + slot;
-    const int pitch = g.pitch;
     const long long plane = g.plane;
+    const long long p2 = plane;   // stride of one pair field in float2 units
+    const int pitch = g.pitch;
+    const int xc = colok ? x : 0;
     const float *in = a.in + slot * a.sstride;
-    float *out = a.out + slot * a.sstride;
+    float *outf = a.out + slot * a.sstride + xc;
+    float2 *out2 = reinterpret_cast<float2 *>(a.out + slot * a.sstride) + xc;
     const float dt = g.dt;
     const int n = a.n;
-    const int x0 = g.x0, x1 = g.x0 + g.nx, z0 = g.z0, z1 = g.z0 + g.nz;
     const bool recon = n > 0;
+    const int x0 = g.x0, x1 = g.x0 + g.nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const int ix = x - x0;
+    const bool xint = ix >= 0 && ix < g.nx;
+    const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
+    const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
+    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
     const long long bandprev = ((long long)shot * g.nt + (n - 1)) * a.bands.nb;
+    const int src = a.src_cell[shot];
+    const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1] : 0.f;
+    const float2 *imgs = a.img + slot * plane;   // image accumulators of this slot
+    float2 *img = a.img + slot * plane + xc;
 
-    load_box<M>(sP, in + A_P * plane, g, tz0, tx0);
-    for (int i = tid; i < SZ * SX4; i += NTH) {
-        int rz = i / SX4, q = i - rz * SX4;
-        int z = tz0 - H + rz, xq = tx0 - HX + 4 * q;
-        float lp[4] = {0.f, 0.f, 0.f, 0.f}, kd[4] = {0.f, 0.f, 0.f, 0.f};
-        bool ok = z >= 0 && z < g.Nz && xq >= 0 && xq < g.pitch;
-        if (ok) {
-            long long cell = (long long)z * pitch + xq;
-            float4 l4 = __ldg(reinterpret_cast<const float4 *>(in + A_LP * plane + cell));
-            float4 k4 = __ldg(reinterpret_cast<const float4 *>(a.kdt + cell));
-            lp[0] = l4.x; lp[1] = l4.y; lp[2] = l4.z; lp[3] = l4.w;
-            kd[0] = k4.x; kd[1] = k4.y; kd[2] = k4.z; kd[3] = k4.w;
-        }
-        bool pmlz = ok && ((z <= z0 - 1) || (z >= z1));
-        float ux[4], uz[4];
+    // z rings: node rows (slot (r - zstart) % W), half rows (slot (k - zstart + M) % W)
+    float2 PU[W], VW[W];
+    float VN[W], PIZ[W];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float l1 = kd[e] * lp[e];
-            ux[e] = l1;
-            uz[e] = l1;
-            int x = xq + e;
-            if (ok && x < g.Nx) {
-                long long cell = (long long)z * pitch + x;
-                if ((x <= x0 - 1) || (x >= x1))
-                    ux[e] = l1 - a.pml.ai[2][x] * (__ldg(in + A_LPVX * plane + cell) - l1);
-                if (pmlz)
-                    uz[e] = l1 - a.pml.ai[0][z] * (__ldg(in + A_LPVZ * plane + cell) - l1);
-            }
+    for (int j = 0; j < W; ++j) {
+        PU[j] = make_float2(0.f, 0.f);
+        VW[j] = make_float2(0.f, 0.f);
+        VN[j] = 0.f;
+        PIZ[j] = 0.f;
+    }
+    // (p^n, kdt*lp - ai_z (lpsi_vz - kdt*lp)) at node row r of this column
+    auto pu_node = [&](int r, float2 pl, float kd, float lpvz) -> float2 {
+        float kl = kd * pl.y;
+        if (colok && r >= 0 && r < g.Nz && ((r <= z0 - 1) || (r >= z1))) kl -= a.pml.ai[0][r] * (lpvz - kl);
+        return make_float2(pl.x, kl);
+    };
+    {
+        const float2 *in2 = reinterpret_cast<const float2 *>(in);
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            const int r = zstart + j;
+            const bool ok = colok && r >= 0 && r < g.Nz;
+            const long long cr = ok ? (long long)r * pitch + xc : 0;
+            const float2 pl = ok ? in2[(A_PL / 2) * p2 + cr] : make_float2(0.f, 0.f);
+            const float kd = ok ? a.kdt[cr] : 0.f;
+            const float lpvz = (ok && ((r <= z0 - 1) || (r >= z1))) ? in[A_LPVZ * plane + cr] : 0.f;
+            PU[j] = pu_node(r, pl, kd, lpvz);
         }
-        *reinterpret_cast<float4 *>(sUx + rz * SX + 4 * q) = make_float4(ux[0], ux[1], ux[2], ux[3]);
-        *reinterpret_cast<float4 *>(sUz + rz * SX + 4 * q) = make_float4(uz[0], uz[1], uz[2], uz[3]);
     }
-    for (int i = tid; i < G::NVX; i += NTH) {
-        int r = i / (VXW - 1), ci = i - r * (VXW - 1);
-        int z = tz0 + r, j = tx0 - M + ci;
-        sVxo[r * VXW + ci] = (z < g.Nz && j >= 0 && j < g.Nx)
-                                 ? __ldg(in + A_VX * plane + (long long)z * pitch + j) : 0.f;
+    float bz_old = 0.f;
+    {
+        int k = zstart + M - 1;
+        if (colok && k >= 0 && k < g.Nz) bz_old = a.binv[(long long)k * pitch + xc];
     }
-    for (int i = tid; i < G::NVZ; i += NTH) {
-        int r = i / TX, c = i - r * TX;
-        int k = tz0 - M + r, x = tx0 + c;
-        sVzo[r * TX + c] = (k >= 0 && k < g.Nz && x < g.Nx)
-                               ? __ldg(in + A_VZ * plane + (long long)k * pitch + x) : 0.f;
-    }
-    __syncthreads();
 
-    // ---- half-node stage along x: lambda_vx (S4^T, S3^T), lambda_psi_px,
-    //      background vx^{n-1/2}, rho-image products
-    for (int i = tid; i < G::NVX; i += NTH) {
-        int r = i / (VXW - 1), ci = i - r * (VXW - 1);
-        int z = tz0 + r, j = tx0 - M + ci;
-        float w = 0.f, vn = 0.f, pi = 0.f;
-        if (z < g.Nz && j >= 0 && j < g.Nx) {
-            long long cell = (long long)z * pitch + j;
-            bool own = ci >= M && ci < M + TX;
-            const float *ur = sUx + (r + H) * SX + (ci - M + HX);
-            const float *pr = sP + (r + H) * SX + (ci - M + HX);
-            float du = 0.f, Gx = 0.f;
 #pragma unroll
-            for (int l = 1; l <= M; ++l) {
-                du += g.cx[l - 1] * (ur[l] - ur[1 - l]);
-                Gx += g.cx[l - 1] * (pr[l] - pr[1 - l]);
-            }
-            float lv = __ldg(in + A_LVX * plane + cell) + du;
-            float bu = 0.5f * (__ldg(a.binv + cell) + __ldg(a.binv + (j + 1 < g.Nx ? cell + 1 : cell)));
-            float dtbu = dt * bu;
-            w = dtbu * lv;
-            if ((j <= x0 - 2) || (j >= x1)) {
-                float l1 = __ldg(in + A_LPPX * plane + cell) - dtbu * lv;
-                w -= a.pml.ah[2][j] * l1;
-                if (own) out[A_LPPX * plane + cell] = a.pml.bh[2][j] * l1;
-            }
-            if (own) out[A_LVX * plane + cell] = lv;
-            pi = Gx * lv;
-            if (recon) {
-                int iz = z - z0, ix = j - x0;
-                if (iz >= 0 && iz < g.nz) {
-                    if (ix >= 0 && ix < g.nx) vn = sVxo[r * VXW + ci] + dtbu * Gx;
-                    else if ((ix >= -M && ix < 0) || (ix >= g.nx && ix < g.nx + M))
-                        vn = band_get(a.bands, a.bands.v, bandprev + band_xstrip(iz, ix, M, g.nz, g.nx));
+    for (int j = 0; j < PD - 1; ++j) {
+        if (zstart + j < zc1)
+            adj_issue<M>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
+                         outcol, pmlxh, pmlxn, xint);
+        cp_commit();
+    }
+
+    for (int zb = zstart; zb < zc1; zb += W) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int z = zb + u;
+            if (z >= zc1) break;
+            const int zi = z + PD - 1;
+            if (zi < zc1)
+                adj_issue<M>(stagef + ((zi - zstart) % PD) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
+                             colok, vxok, outcol, pmlxh, pmlxn, xint);
+            cp_commit();
+            cp_wait_row();
+            const AdjRow cur = adj_read(stagef + ((z - zstart) % PD) * kAdjStageFloats);
+            const int k = z + M - 1;
+            const int sl = (u + W - 1) % W;
+            PU[sl] = pu_node(z + W - 1, cur.pl, cur.kdr, cur.lpvzr);
+            const float buz = 0.5f * (bz_old + cur.bz);
+            bz_old = cur.bz;
+            // ---- half row k along z: lambda_vz, lambda_psi_pz, background vz^{n-1/2}
+            float wz = 0.f, vn = 0.f, piz = 0.f;
+            if (colok && k >= 0 && k < g.Nz) {
+                const long long ck = (long long)k * pitch;
+                const bool own = outcol && k >= zc0 && k < zc1;
+                float2 D = make_float2(0.f, 0.f);   // (Gz, du/dz)
+#pragma unroll
+                for (int l = 1; l <= M; ++l) D = tap(g.cz[l - 1], PU[(u + M - 1 + l) % W], PU[(u + M - l) % W], D);
+                const float lv = cur.v2z.y + D.y;
+                const float dtbu = dt * buz;
+                wz = dtbu * lv;
+                if ((k <= z0 - 2) || (k >= z1)) {
+                    float l1 = cur.lppz - dtbu * lv;
+                    wz -= a.pml.ah[0][k] * l1;
+                    if (own) outf[A_LPPZ * plane + ck] = a.pml.bh[0][k] * l1;
                 }
-                if (own) out[A_VX * plane + cell] = vn;
-            }
-        }
-        sWx[r * VXW + ci] = w;
-        sVxn[r * VXW + ci] = vn;
-        if (ci >= M - 1 && ci < M + TX) sPix[r * (TX + 1) + (ci - M + 1)] = pi;
-    }
-    // ---- half-node stage along z
-    for (int i = tid; i < G::NVZ; i += NTH) {
-        int r = i / TX, c = i - r * TX;
-        int k = tz0 - M + r, x = tx0 + c;
-        float w = 0.f, vn = 0.f, pi = 0.f;
-        if (k >= 0 && k < g.Nz && x < g.Nx) {
-            long long cell = (long long)k * pitch + x;
-            bool own = r >= M && r < M + TZ;
-            const float *uc = sUz + (r - M + H) * SX + (c + HX);
-            const float *pc = sP + (r - M + H) * SX + (c + HX);
-            float du = 0.f, Gz = 0.f;
-#pragma unroll
-            for (int l = 1; l <= M; ++l) {
-                du += g.cz[l - 1] * (uc[l * SX] - uc[(1 - l) * SX]);
-                Gz += g.cz[l - 1] * (pc[l * SX] - pc[(1 - l) * SX]);
-            }
-            float lv = __ldg(in + A_LVZ * plane + cell) + du;
-            float bu = 0.5f * (__ldg(a.binv + cell) + __ldg(a.binv + (k + 1 < g.Nz ? cell + pitch : cell)));
-            float dtbu = dt * bu;
-            w = dtbu * lv;
-            if ((k <= z0 - 2) || (k >= z1)) {
-                float l1 = __ldg(in + A_LPPZ * plane + cell) - dtbu * lv;
-                w -= a.pml.ah[0][k] * l1;
-                if (own) out[A_LPPZ * plane + cell] = a.pml.bh[0][k] * l1;
-            }
-            if (own) out[A_LVZ * plane + cell] = lv;
-            pi = Gz * lv;
-            if (recon) {
-                int iz = k - z0, ix = x - x0;
-                if (ix >= 0 && ix < g.nx) {
-                    if (iz >= 0 && iz < g.nz) vn = sVzo[r * TX + c] + dtbu * Gz;
-                    else if ((iz >= -M && iz < 0) || (iz >= g.nz && iz < g.nz + M))
+                piz = D.x * lv;
+                if (recon && xint) {
+                    const int iz = k - z0;
+                    if (iz >= 0 && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
+                    else if (in_xstrip(iz, M, g.nz))
                         vn = band_get(a.bands, a.bands.v, bandprev + band_zstrip(iz, ix, M, g.nz, g.nx));
                 }
-                if (own) out[A_VZ * plane + cell] = vn;
+                if (own) out2[(A_VZ / 2) * p2 + ck] = make_float2(vn, lv);
             }
-        }
-        sWz[r * TX + c] = w;
-        sVzn[r * TX + c] = vn;
-        if (r >= M - 1 && r < M + TZ) sPiz[(r - M + 1) * TX + c] = pi;
-    }
-    __syncthreads();
+            VW[sl] = make_float2(cur.v2z.x, wz);
+            VN[sl] = vn;
+            PIZ[sl] = piz;
+            if (z < zc0) continue;
 
-    // ---- node stage on the own tile
-    const int src = a.src_cell[shot];
-    const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1]
-                             : 0.f;
-    float2 *img = a.img + slot * plane;
-    for (int i = tid; i < TZ * TX; i += NTH) {
-        int r = i / TX, c = i - r * TX;
-        int z = tz0 + r, x = tx0 + c;
-        if (z >= g.Nz || x >= g.Nx) continue;
-        long long cell = (long long)z * pitch + x;
-        const float *vxo = sVxo + r * VXW + c + M;
-        const float *vzo = sVzo + (r + M) * TX + c;
-        const float *wxr = sWx + r * VXW + c + M;
-        const float *wzc = sWz + (r + M) * TX + c;
-        float Q = 0.f, dw = 0.f;
+            // ---- row z: half nodes along x
+            const long long cz = (long long)z * pitch;
+            const float pbn = cur.plz.x;
+            const float lp1 = cur.plz.y;
+            const float kd = cur.kdz;
+            const float kl = kd * lp1;
+            sPU[t] = make_float2(pbn, pmlxn ? kl - aix * (cur.lpsvx - kl) : kl);
+            sB[t] = cur.bx;
+            __syncthreads();
+            float2 vw = make_float2(cur.v2x.x, 0.f);
+            float vxn = 0.f, pix = 0.f;
+            if (vxok) {
+                float2 D = make_float2(0.f, 0.f);   // (Gx, du/dx)
 #pragma unroll
-        for (int l = 1; l <= M; ++l) {
-            Q += g.cx[l - 1] * (vxo[l - 1] - vxo[-l]) + g.cz[l - 1] * (vzo[(l - 1) * TX] - vzo[-l * TX]);
-            dw += g.cx[l - 1] * (wxr[l - 1] - wxr[-l]) + g.cz[l - 1] * (wzc[(l - 1) * TX] - wzc[-l * TX]);
-        }
-        float lp1 = __ldg(in + A_LP * plane + cell);
-        float kd = __ldg(a.kdt + cell);
-        int iz = z - z0, ix = x - x0;
-        bool inner = iz >= 0 && iz < g.nz && ix >= 0 && ix < g.nx;
-        if (inner) {
-            float2 acc = img[cell];
-            acc.x += Q * lp1;
-            acc.y += (sPix[r * (TX + 1) + c + 1] + sPix[r * (TX + 1) + c]) +
-                     (sPiz[(r + 1) * TX + c] + sPiz[r * TX + c]);
-            img[cell] = acc;
-        }
-        out[A_LP * plane + cell] = lp1 + dw;
-        if ((x <= x0 - 1) || (x >= x1))
-            out[A_LPVX * plane + cell] = a.pml.bi[2][x] * (__ldg(in + A_LPVX * plane + cell) - kd * lp1);
-        if ((z <= z0 - 1) || (z >= z1))
-            out[A_LPVZ * plane + cell] = a.pml.bi[0][z] * (__ldg(in + A_LPVZ * plane + cell) - kd * lp1);
-        if (recon) {
-            float pn = 0.f;
-            if (inner) {
-                const float *vxn = sVxn + r * VXW + c + M;
-                const float *vzn = sVzn + (r + M) * TX + c;
+                for (int l = 1; l <= M; ++l) D = tap(g.cx[l - 1], sPU[t + l], sPU[t + 1 - l], D);
+                const float bux = 0.5f * (cur.bx + (x + 1 >= g.Nx ? cur.bx : sB[t + 1]));
+                const float dtbu = dt * bux;
+                const float lv = cur.v2x.y + D.y;
+                float wx = dtbu * lv;
+                if (pmlxh) {
+                    float l1 = cur.lppx - dtbu * lv;
+                    wx -= ahx * l1;
+                    if (outcol) outf[A_LPPX * plane + cz] = bhx * l1;
+                }
+                vw.y = wx;
+                pix = D.x * lv;
+                if (recon) {
+                    const int iz = z - z0;
+                    if (iz >= 0 && iz < g.nz) {
+                        if (xint) vxn = cur.v2x.x + dtbu * D.x;
+                        else if (in_xstrip(ix, M, g.nx))
+                            vxn = band_get(a.bands, a.bands.v, bandprev + band_xstrip(iz, ix, M, g.nz, g.nx));
+                    }
+                }
+                if (outcol) out2[(A_VX / 2) * p2 + cz] = make_float2(vxn, lv);
+            }
+            sVW[t] = vw;
+            sVN[t] = vxn;
+            sPi[t] = pix;
+            __syncthreads();
+
+            // ---- row z: nodes on the output columns
+            if (outcol) {
+                float2 E = make_float2(0.f, 0.f);   // (Q_n, D- w)
                 float qn = 0.f;
 #pragma unroll
-                for (int l = 1; l <= M; ++l)
-                    qn += g.cx[l - 1] * (vxn[l - 1] - vxn[-l]) + g.cz[l - 1] * (vzn[(l - 1) * TX] - vzn[-l * TX]);
-                pn = sP[(r + H) * SX + c + HX] + kd * qn;
-                if (cell == src) pn -= wsrc;
-            } else {
-                long long b = pband_index(iz, ix, M, g.nz, g.nx);
-                if (b >= 0) pn = band_get(a.bands, a.bands.p, bandprev + b);
+                for (int l = 1; l <= M; ++l) {
+                    const int hp = (u + M + l - 1) % W, hm = (u + M - l) % W;
+                    E = tap(g.cx[l - 1], sVW[t + l - 1], sVW[t - l], E);
+                    E = tap(g.cz[l - 1], VW[hp], VW[hm], E);
+                    if (recon) {
+                        qn = tap(g.cx[l - 1], sVN[t + l - 1], sVN[t - l], qn);
+                        qn = tap(g.cz[l - 1], VN[hp], VN[hm], qn);
+                    }
+                }
+                const int iz = z - z0;
+                const bool inner = xint && iz >= 0 && iz < g.nz;
+                if (inner) {
+                    float2 acc = cur.img;
+                    acc.x += E.x * lp1;
+                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[(u + M) % W] + PIZ[(u + M - 1) % W]);
+                    img[cz] = acc;
+                }
+                float pn = 0.f;
+                if (recon) {
+                    if (inner) {
+                        pn = pbn + kd * qn;
+                        if (cz + x == src) pn -= wsrc;
+                    } else {
+                        long long b = pband_index(iz, ix, M, g.nz, g.nx);
+                        if (b >= 0) pn = band_get(a.bands, a.bands.p, bandprev + b);
+                    }
+                }
+                out2[(A_PL / 2) * p2 + cz] = make_float2(pn, lp1 + E.y);
+                if (pmlxn) outf[A_LPVX * plane + cz] = bix * (cur.lpsvx - kl);
+                if ((z <= z0 - 1) || (z >= z1)) outf[A_LPVZ * plane + cz] = a.pml.bi[0][z] * (cur.lpsvz - kl);
             }
-            out[A_P * plane + cell] = pn;
         }
     }
 
     if (recon) {
-        // pre-add the residual of step n-1 at the receivers of this tile
+        // pre-add the residual of step n-1 at the receivers of this CTA
         __syncthreads();
-        int t = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
-        int b = a.trec.ptr[t], e = a.trec.ptr[t + 1];
-        for (int i = b + tid; i < e; i += NTH) {
+        int tile = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+        int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
+        float2 *plo = reinterpret_cast<float2 *>(a.out + slot * a.sstride + A_PL * plane);
+        for (int i = b + t; i < e; i += NTH) {
             int2 rc = a.trec.rec[i];
             if (i > b && a.trec.rec[i - 1].x == rc.x) continue;  // run handled by its first entry
             float add = 0.f;
-            for (int k = i; k < e && a.trec.rec[k].x == rc.x; ++k)
-                add += a.dstage[(long long)a.trec.rec[k].y * g.nt + (n - 1)];
-            out[A_LP * plane + rc.x] += add;
+            for (int q = i; q < e && a.trec.rec[q].x == rc.x; ++q)
+                add += a.dstage[(long long)a.trec.rec[q].y * g.nt + (n - 1)];
+            plo[rc.x].y += add;
         }
     }
 }
 
-template <int M>
-size_t fwd_smem_M(bool born, bool hess)
+// Start state of a reverse pass: (p, 0), (vx, 0), (vz, 0) from the saved
+// background final state [p][vx][vz] of each shot of the batch.
+__global__ void k_pack_adj(const GridDev g, const float *final_state, int shot0, int batch, float *st,
+                           long long sstride)
 {
-    using G = Geo<M>;
-    int nf = born ? 2 : 1;
-    size_t f = (size_t)nf * (G::SZ * G::SX + TZ * G::VXW + G::VZH * TX);
-    if (hess) f += TZ * (TX + 1) + (TZ + 1) * TX;
-    return f * sizeof(float);
-}
-
-template <int M>
-size_t adj_smem_M()
-{
-    using G = Geo<M>;
-    size_t f = 3 * (size_t)G::SZ * G::SX + 3 * (size_t)TZ * G::VXW + 3 * (size_t)G::VZH * TX +
-               TZ * (TX + 1) + (TZ + 1) * TX;
-    return f * sizeof(float);
+    const long long plane = g.plane;
+    const long long n = batch * plane;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long s = i / plane, c = i - s * plane;
+        const float *fs = final_state + (shot0 + s) * 3 * plane;
+        float2 *o = reinterpret_cast<float2 *>(st + s * sstride);
+        o[(A_PL / 2) * plane + c] = make_float2(fs[c], 0.f);
+        o[(A_VX / 2) * plane + c] = make_float2(fs[plane + c], 0.f);
+        o[(A_VZ / 2) * plane + c] = make_float2(fs[2 * plane + c], 0.f);
+    }
 }
 
 template <int M, bool BORN, bool BANDS, bool HESS>
-cudaError_t set_fwd_attr()
+cudaError_t launch_fwd_t(const Step2D &a, dim3 grid, cudaStream_t s)
 {
-    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fwd_smem_M<M>(BORN, HESS));
+    k_fwd2d<M, BORN, BANDS, HESS><<<grid, NTH, kFwdStageBytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int M, bool BORN, bool BANDS, bool HESS>
+cudaError_t attr_fwd()
+{
+    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kFwdStageBytes);
 }
 
 template <int M>
-cudaError_t configure_M()
+cudaError_t attr_M()
 {
     cudaError_t e;
-    if ((e = set_fwd_attr<M, true, false, false>()) != cudaSuccess) return e;
-    if ((e = set_fwd_attr<M, false, true, false>()) != cudaSuccess) return e;
-    if ((e = set_fwd_attr<M, false, true, true>()) != cudaSuccess) return e;
-    if ((e = set_fwd_attr<M, false, false, false>()) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_adj2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)adj_smem_M<M>());
+    if ((e = attr_fwd<M, true, false, false>()) != cudaSuccess) return e;
+    if ((e = attr_fwd<M, false, true, true>()) != cudaSuccess) return e;
+    if ((e = attr_fwd<M, false, true, false>()) != cudaSuccess) return e;
+    if ((e = attr_fwd<M, false, false, false>()) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
 }
 
 template <int M>
-cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool hess,
-                         cudaStream_t s)
+cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool hess, cudaStream_t s)
 {
-    dim3 grid((a.g.Nx + TX - 1) / TX, (a.g.Nz + TZ - 1) / TZ, batch);
-    size_t sm = fwd_smem_M<M>(born, hess);
-    if (born) k_fwd2d<M, true, false, false><<<grid, NTH, sm, s>>>(a);
-    else if (bands && hess) k_fwd2d<M, false, true, true><<<grid, NTH, sm, s>>>(a);
-    else if (bands) k_fwd2d<M, false, true, false><<<grid, NTH, sm, s>>>(a);
-    else k_fwd2d<M, false, false, false><<<grid, NTH, sm, s>>>(a);
-    return cudaGetLastError();
+    dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
+    if (born) return launch_fwd_t<M, true, false, false>(a, grid, s);
+    if (bands && hess) return launch_fwd_t<M, false, true, true>(a, grid, s);
+    if (bands) return launch_fwd_t<M, false, true, false>(a, grid, s);
+    return launch_fwd_t<M, false, false, false>(a, grid, s);
 }
 
 template <int M>
 cudaError_t launch_adj_M(const Step2D &a, int batch, cudaStream_t s)
 {
-    dim3 grid((a.g.Nx + TX - 1) / TX, (a.g.Nz + TZ - 1) / TZ, batch);
-    k_adj2d<M><<<grid, NTH, adj_smem_M<M>(), s>>>(a);
+    dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
+    k_adj2d<M><<<grid, NTH, kAdjStageBytes, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t fwd2d_smem(int M, bool born, bool hess)
-{
-    return M == 2 ? fwd_smem_M<2>(born, hess) : fwd_smem_M<4>(born, hess);
-}
-
-size_t adj2d_smem(int M) { return M == 2 ? adj_smem_M<2>() : adj_smem_M<4>(); }
+int march2d_txo(int M) { return M == 2 ? Cols<2>::TXO : Cols<4>::TXO; }
 
 cudaError_t configure_2d_kernels()
 {
-    cudaError_t e = configure_M<2>();
+    cudaError_t e = attr_M<2>();
     if (e != cudaSuccess) return e;
-    return configure_M<4>();
+    return attr_M<4>();
 }
 
-cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess,
-                         cudaStream_t s)
+cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess, cudaStream_t s)
 {
     if (a.g.M == 2) return launch_fwd_M<2>(a, batch, born, save_bands, hess, s);
     return launch_fwd_M<4>(a, batch, born, save_bands, hess, s);
@@ -652,6 +849,15 @@ cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s)
 {
     if (a.g.M == 2) return launch_adj_M<2>(a, batch, s);
     return launch_adj_M<4>(a, batch, s);
+}
+
+cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int shot0, int batch, float *st,
+                                long long sstride, cudaStream_t s)
+{
+    long long n = batch * g.plane;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    k_pack_adj<<<blocks, 256, 0, s>>>(g, final_state, shot0, batch, st, sstride);
+    return cudaGetLastError();
 }
 
 }  // namespace lsrtm

@@ -38,35 +38,48 @@ __global__ void k_model_prep(GridDev g, const float *vp, const float *rho, float
     }
 }
 
-// dkdt = dt kappa (dlnVp + dlnIp), rr = (dlnIp - dlnVp) / rho on the interior;
-// the arrays are zeroed beforehand, so the pad stays zero.
+// Perturbation map of Sec. 2 interleaved with the background coefficients:
+// kd2 = (dt kappa, dt kappa (dlnVp + dlnIp)), br2 = (1/rho, (dlnIp - dlnVp)/rho),
+// the perturbation parts zero outside the interior.
 __global__ void k_pert_prep(GridDev g, const float *dm, const float *kdt, const float *binv,
-                            float *dkdt, float *rr)
+                            float2 *kd2, float2 *br2)
 {
     long long nint = (long long)g.nz * g.ny * g.nx;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
-         k += (long long)gridDim.x * blockDim.x) {
-        long long c = pad_of(g, k);
-        float m1 = dm[k], m2 = dm[nint + k];
-        dkdt[c] = kdt[c] * (m1 + m2);
-        rr[c] = (m2 - m1) * binv[c];
+    long long ncell = (long long)g.Nz * g.Ny * g.Nx;
+    for (long long c0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; c0 < ncell;
+         c0 += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(c0 % g.Nx);
+        long long t = c0 / g.Nx;
+        int y = (int)(t % g.Ny);
+        int z = (int)(t / g.Ny);
+        long long c = (long long)z * g.rowz + (long long)y * g.pitch + x;
+        int iz = z - g.z0, iy = y - g.y0, ix = x - g.x0;
+        float dk = 0.f, dr = 0.f;
+        if (iz >= 0 && iz < g.nz && iy >= 0 && iy < g.ny && ix >= 0 && ix < g.nx) {
+            long long k = ((long long)iz * g.ny + iy) * g.nx + ix;
+            float m1 = dm[k], m2 = dm[nint + k];
+            dk = kdt[c] * (m1 + m2);
+            dr = (m2 - m1) * binv[c];
+        }
+        kd2[c] = make_float2(kdt[c], dk);
+        br2[c] = make_float2(binv[c], dr);
     }
 }
 
-__global__ void k_inject(GridDev g, TileRecs tr, int shot0, const float *dstage, int n, float *lp,
-                         long long sstride)
+__global__ void k_inject(GridDev g, TileRecs tr, int shot0, const float *dstage, int n, float2 *pl,
+                         long long sstride2)
 {
     int slot = blockIdx.y;
     int t = (shot0 + slot) * tr.ntiles + blockIdx.x;
     int b = tr.ptr[t], e = tr.ptr[t + 1];
-    float *dst = lp + slot * sstride;
+    float2 *dst = pl + slot * sstride2;
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         int2 rc = tr.rec[i];
         if (i > b && tr.rec[i - 1].x == rc.x) continue;
         float add = 0.f;
         for (int k = i; k < e && tr.rec[k].x == rc.x; ++k)
             add += dstage[(long long)tr.rec[k].y * g.nt + n];
-        dst[rc.x] += add;
+        dst[rc.x].y += add;
     }
 }
 
@@ -304,19 +317,19 @@ cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rh
 }
 
 cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt,
-                             const float *binv, float *dkdt, float *rr, cudaStream_t s)
+                             const float *binv, float2 *kd2, float2 *br2, cudaStream_t s)
 {
-    long long n = (long long)g.nz * g.ny * g.nx;
-    k_pert_prep<<<grid_for(n), NT, 0, s>>>(g, dm, kdt, binv, dkdt, rr);
+    long long n = (long long)g.Nz * g.Ny * g.Nx;
+    k_pert_prep<<<grid_for(n), NT, 0, s>>>(g, dm, kdt, binv, kd2, br2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int batch, int shot0,
-                                   const float *dstage, int n, float *lp, long long sstride,
+                                   const float *dstage, int n, float2 *pl, long long sstride2,
                                    cudaStream_t s)
 {
     dim3 grid(tr.ntiles, batch);
-    k_inject<<<grid, 64, 0, s>>>(g, tr, shot0, dstage, n, lp, sstride);
+    k_inject<<<grid, 64, 0, s>>>(g, tr, shot0, dstage, n, pl, sstride2);
     return cudaGetLastError();
 }
 

@@ -56,13 +56,14 @@ struct Step2D {
     Pml pml;
     const float *kdt;     // dt * kappa          [plane]
     const float *binv;    // 1 / rho             [plane]
-    const float *dkdt;    // dt * kappa * dlnk   [plane] (Born only)
-    const float *rr;      // dln rho / rho       [plane] (Born only)
+    const float2 *kd2;    // (dt kappa, dt kappa dln kappa) [plane] (Born only)
+    const float2 *br2;    // (1/rho, dln rho / rho)        [plane] (Born only)
     const float *in;      // ping state, shot slot s at in + s*sstride
     float *out;           // pong state
     float *psiv;          // in-place node CPML memories, slot stride vstride
     long long sstride, vstride;
     int n;                // time step
+    int tzc;              // rows of the z-chunk each CTA marches through
     int shot0;            // global index of slot 0
     const float *wav;     // [nt] or [nshot][nt]
     int wav_per_shot;
@@ -75,26 +76,28 @@ struct Step2D {
     float2 *img;          // [batch][plane] image accumulators (adjoint)
 };
 
-// Tile shapes used by the 2D kernels.
-constexpr int kTX2 = 32;
-constexpr int kTZ2 = 16;
+// 2D kernels: CTAs of kThreads2D threads, one x-column per thread; a CTA owns
+// march2d_txo(M) output columns and a z-chunk of Step2D::tzc rows.
 constexpr int kThreads2D = 256;
+int march2d_txo(int M);
 
 // Launchers (kernels2d.cu). Return the cudaError of the launch.
 cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess,
                          cudaStream_t s);
 cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s);
-size_t fwd2d_smem(int M, bool born, bool hess);
-size_t adj2d_smem(int M);
 cudaError_t configure_2d_kernels();
+// Adjoint start state (p, 0), (vx, 0), (vz, 0) from the saved background final states.
+cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int shot0, int batch,
+                                float *st, long long sstride, cudaStream_t s);
 
 // Utility kernels (kernels_util.cu).
 cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
                               float *binv, cudaStream_t s);
 cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt,
-                             const float *binv, float *dkdt, float *rr, cudaStream_t s);
+                             const float *binv, float2 *kd2, float2 *br2, cudaStream_t s);
+// Adds the residual of step n to lambda_p (the .y of the (p, lambda_p) pairs).
 cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int batch, int shot0,
-                                   const float *dstage, int n, float *lp, long long sstride,
+                                   const float *dstage, int n, float2 *pl, long long sstride2,
                                    cudaStream_t s);
 cudaError_t launch_image_accumulate(const GridDev &g, const float2 *img, int batch,
                                     double2 *acc, cudaStream_t s);
