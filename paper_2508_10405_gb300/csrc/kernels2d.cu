@@ -50,9 +50,22 @@ __device__ __forceinline__ float2 mul_(float a, float2 b) { return __fmul2_rn(f2
 template <class T> __device__ __forceinline__ T zero_();
 template <> __device__ __forceinline__ float zero_<float>() { return 0.f; }
 template <> __device__ __forceinline__ float2 zero_<float2>() { return make_float2(0.f, 0.f); }
-// acc + c (a - b), as two fused multiply-adds
-template <class T>
-__device__ __forceinline__ T tap(float c, T a, T b, T acc) { return fma_(c, a, fma_(-c, b, acc)); }
+__device__ __forceinline__ float sub_(float a, float b) { return a - b; }
+__device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __ffma2_rn(f2(-1.f), b, a); }
+
+// Staggered first difference sum_l c_l (a_l - b_l): the M differences are
+// independent, then one multiply-add chain of depth M (short critical path).
+template <int M, class T, class FA, class FB>
+__device__ __forceinline__ T stencil(const float *c, FA fa, FB fb)
+{
+    T d[M];
+#pragma unroll
+    for (int l = 0; l < M; ++l) d[l] = sub_(fa(l + 1), fb(l + 1));
+    T acc = mul_(c[0], d[0]);
+#pragma unroll
+    for (int l = 1; l < M; ++l) acc = fma_(c[l], d[l], acc);
+    return acc;
+}
 __device__ __forceinline__ float xof(float v) { return v; }
 __device__ __forceinline__ float xof(float2 v) { return v.x; }
 __device__ __forceinline__ float yof(float) { return 0.f; }
@@ -319,9 +332,8 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
             if (colok && k >= 0 && k < g.Nz) {
                 const long long ck = (long long)k * pitch;
                 const bool own = outcol && k >= zc0 && k < zc1;
-                T G = zero_<T>();
-#pragma unroll
-                for (int l = 1; l <= M; ++l) G = tap(g.cz[l - 1], P[(u + M - 1 + l) % W], P[(u + M - l) % W], G);
+                T G = stencil<M, T>(g.cz, [&](int l) { return P[(u + M - 1 + l) % W]; },
+                                    [&](int l) { return P[(u + M - l) % W]; });
                 if ((k <= z0 - 2) || (k >= z1)) {
                     T ps = fma_(a.pml.bh[0][k], cur.psz, mul_(a.pml.ah[0][k], G));
                     if (own) out[oPPZ * pT + ck] = ps;
@@ -356,9 +368,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
             T vxn = zero_<T>();
             float hxq = 0.f;
             if (vxok) {
-                T G = zero_<T>();
-#pragma unroll
-                for (int l = 1; l <= M; ++l) G = tap(g.cx[l - 1], sP[t + l], sP[t + 1 - l], G);
+                T G = stencil<M, T>(g.cx, [&](int l) { return sP[t + l]; }, [&](int l) { return sP[t + 1 - l]; });
                 const bool last = x + 1 >= g.Nx;
                 const R bn = last ? cur.brz : sB[t + 1];
                 const float bux = 0.5f * (xof(cur.brz) + xof(bn));
@@ -392,12 +402,9 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
 
             // ---- row z: pressure on the output columns
             if (outcol) {
-                T qx = zero_<T>(), qz = zero_<T>();
-#pragma unroll
-                for (int l = 1; l <= M; ++l) {
-                    qx = tap(g.cx[l - 1], sV[t + l - 1], sV[t - l], qx);
-                    qz = tap(g.cz[l - 1], VZ[(u + M + l - 1) % W], VZ[(u + M - l) % W], qz);
-                }
+                T qx = stencil<M, T>(g.cx, [&](int l) { return sV[t + l - 1]; }, [&](int l) { return sV[t - l]; });
+                T qz = stencil<M, T>(g.cz, [&](int l) { return VZ[(u + M + l - 1) % W]; },
+                                     [&](int l) { return VZ[(u + M - l) % W]; });
                 if (pmlxn) {
                     T ps = fma_(bix, psiv[oPVX * pT + cz], mul_(aix, qx));
                     psiv[oPVX * pT + cz] = ps;
@@ -645,9 +652,9 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
             if (colok && k >= 0 && k < g.Nz) {
                 const long long ck = (long long)k * pitch;
                 const bool own = outcol && k >= zc0 && k < zc1;
-                float2 D = make_float2(0.f, 0.f);   // (Gz, du/dz)
-#pragma unroll
-                for (int l = 1; l <= M; ++l) D = tap(g.cz[l - 1], PU[(u + M - 1 + l) % W], PU[(u + M - l) % W], D);
+                // (Gz, du/dz)
+                const float2 D = stencil<M, float2>(g.cz, [&](int l) { return PU[(u + M - 1 + l) % W]; },
+                                                    [&](int l) { return PU[(u + M - l) % W]; });
                 const float lv = cur.v2z.y + D.y;
                 const float dtbu = dt * buz;
                 wz = dtbu * lv;
@@ -682,9 +689,9 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
             float2 vw = make_float2(cur.v2x.x, 0.f);
             float vxn = 0.f, pix = 0.f;
             if (vxok) {
-                float2 D = make_float2(0.f, 0.f);   // (Gx, du/dx)
-#pragma unroll
-                for (int l = 1; l <= M; ++l) D = tap(g.cx[l - 1], sPU[t + l], sPU[t + 1 - l], D);
+                // (Gx, du/dx)
+                const float2 D = stencil<M, float2>(g.cx, [&](int l) { return sPU[t + l]; },
+                                                    [&](int l) { return sPU[t + 1 - l]; });
                 const float bux = 0.5f * (cur.bx + (x + 1 >= g.Nx ? cur.bx : sB[t + 1]));
                 const float dtbu = dt * bux;
                 const float lv = cur.v2x.y + D.y;
@@ -713,18 +720,17 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
 
             // ---- row z: nodes on the output columns
             if (outcol) {
-                float2 E = make_float2(0.f, 0.f);   // (Q_n, D- w)
+                // (Q_n, D- w) along x and z
+                const float2 Ex = stencil<M, float2>(g.cx, [&](int l) { return sVW[t + l - 1]; },
+                                                     [&](int l) { return sVW[t - l]; });
+                const float2 Ez = stencil<M, float2>(g.cz, [&](int l) { return VW[(u + M + l - 1) % W]; },
+                                                     [&](int l) { return VW[(u + M - l) % W]; });
+                const float2 E = add_(Ex, Ez);
                 float qn = 0.f;
-#pragma unroll
-                for (int l = 1; l <= M; ++l) {
-                    const int hp = (u + M + l - 1) % W, hm = (u + M - l) % W;
-                    E = tap(g.cx[l - 1], sVW[t + l - 1], sVW[t - l], E);
-                    E = tap(g.cz[l - 1], VW[hp], VW[hm], E);
-                    if (recon) {
-                        qn = tap(g.cx[l - 1], sVN[t + l - 1], sVN[t - l], qn);
-                        qn = tap(g.cz[l - 1], VN[hp], VN[hm], qn);
-                    }
-                }
+                if (recon)
+                    qn = stencil<M, float>(g.cx, [&](int l) { return sVN[t + l - 1]; }, [&](int l) { return sVN[t - l]; }) +
+                         stencil<M, float>(g.cz, [&](int l) { return VN[(u + M + l - 1) % W]; },
+                                           [&](int l) { return VN[(u + M - l) % W]; });
                 const int iz = z - z0;
                 const bool inner = xint && iz >= 0 && iz < g.nz;
                 if (inner) {
