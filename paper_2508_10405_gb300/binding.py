@@ -28,7 +28,8 @@ PLAN_BATCHED, PLAN_PLAIN = 0, 1
 EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_remigrate",
            "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
-           "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error"]
+           "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
+           "lsrtm_born_static"]
 
 
 class LsrtmError(RuntimeError):
@@ -93,6 +94,7 @@ def load_library(path: str | None = None):
     L.lsrtm_timing_enable.argtypes = [vp, ctypes.c_int]
     L.lsrtm_timing_read.argtypes = [vp, ctypes.POINTER(Timings), ctypes.c_int]
     L.lsrtm_set_stream.argtypes = [vp, vp]
+    L.lsrtm_born_static.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp, vp, vp]
     L.lsrtm_workspace_bytes.argtypes = [vp]
     L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
     L.lsrtm_kernel_launches.argtypes = [vp]

@@ -1036,3 +1036,8 @@ void lsrtm_destroy(lsrtm_handle *h)
 const char *lsrtm_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+namespace lsrtm {
+// Lets other translation units of the library report through lsrtm_last_error.
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace lsrtm
