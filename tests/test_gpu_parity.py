@@ -49,6 +49,7 @@ def test_born_matches_oracle(case):
     h = handle(w)
     d = cpu(h.born(torch.tensor(w.dm, dtype=torch.float32, device="cuda")))
     ref = oracle.born(w, w.dm)
+    print(f"Born {name}: rel L2 {rel(d, ref):.3e}")
     assert rel(d, ref) < TOL, (name, rel(d, ref))
 
 
@@ -59,6 +60,7 @@ def test_adjoint_matches_oracle(case):
     h = handle(w)
     g = cpu(h.adjoint(torch.tensor(dres, dtype=torch.float32, device="cuda")))
     ref = oracle.adjoint(w, dres)
+    print(f"migration {name}: rel L2 {rel(g, ref):.3e}")
     assert rel(g, ref) < TOL, (name, rel(g, ref))
 
 
@@ -86,6 +88,7 @@ def test_dot_product_fp32(case):
     d = torch.tensor(rng.standard_normal((w.geom.nrec_total, w.nt)), dtype=torch.float32,
                      device="cuda")
     r1, r2 = dot_tests(handle(w), m, d)
+    print(f"FP32 dot tests {name}: {r1:.3e} (d = L m), {r2:.3e} (random d, Cauchy-Schwarz scale)")
     assert r1 < 1e-6 and r2 < 1e-6, (name, r1, r2)
 
 
@@ -213,6 +216,8 @@ def test_bf16_bands_error_stated():
     g32 = cpu(handle(w).adjoint(dt))
     g16 = cpu(handle(w, band_precision=BAND_BF16).adjoint(dt))
     ref = oracle.adjoint(w, dres)
+    print(f"BF16 bands: image rel L2 {rel(g16, ref):.3e} vs oracle, {rel(g16, g32):.3e} vs FP32 bands; "
+          f"FP32 bands {rel(g32, ref):.3e} vs oracle")
     assert rel(g16, ref) < 1e-2
     assert rel(g16, g32) < 1e-2
 
