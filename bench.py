@@ -192,11 +192,12 @@ def cpu_sample(w, seconds, reps=1):
 
 def workload(args):
     kw = {}
-    if args.shots is not None:
-        kw["nshot"] = args.shots
     if args.nt is not None:
         kw["nt"] = args.nt
-    return li.preset(args.workload, **kw)
+    w = li.preset(args.workload, **kw)
+    if args.shots is not None and args.shots < w.geom.nshot:
+        w.geom = w.geom.subset(list(range(args.shots)))
+    return w
 
 
 def reference_arm(args, rank, world):

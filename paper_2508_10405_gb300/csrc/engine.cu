@@ -52,6 +52,7 @@ lsrtm_status fail(lsrtm_status st, const std::string &msg)
 // planes (forward).
 constexpr int kStatePlanes2D = 10;
 constexpr int kPsivPlanes2D = 4;
+constexpr int kStatePlanes3D = 20;
 
 enum GraphKind { G_BORN = 0, G_BG = 1, G_BG_HESS = 2, G_ADJ = 3 };
 
@@ -78,7 +79,10 @@ struct lsrtm_handle {
     int2 *trec = nullptr;
     TileRecs trv{};
     float src_scale = 0.f;
-    int txo = 0, tzc = 0;        // CTA output columns and z-chunk rows
+    int txo = 0, tzc = 0;        // CTA output columns and z-chunk rows (2D)
+    // 3D receiver maps: per shot and node, the first of its receivers in rcell/rrow
+    int *rmap = nullptr, *rptr = nullptr, *rcell = nullptr, *rrow = nullptr;
+    int fs_planes = 3;           // planes of the saved background final state per shot
     // wavefield slots
     int batch = 1;
     float *st[2] = {nullptr, nullptr};
@@ -277,6 +281,34 @@ Step2D step_args(lsrtm_handle *h, int shot0)
     return a;
 }
 
+Step3D step3_args(lsrtm_handle *h, int shot0)
+{
+    Step3D a{};
+    a.g = h->g;
+    a.pml = h->pml;
+    a.kdt = h->kdt;
+    a.binv = h->binv;
+    a.kd2 = h->kd2;
+    a.br2 = h->br2;
+    a.st = h->st[0];
+    a.sstride = h->sstride;
+    a.shot0 = shot0;
+    a.wav = h->wav;
+    a.wav_per_shot = h->cfg.wavelet_per_shot;
+    a.src_cell = h->src_cell;
+    a.src_scale = h->src_scale;
+    a.bands = h->bands;
+    a.hess = h->hess;
+    a.dstage = h->dstage;
+    a.rmap = h->rmap;
+    a.rptr = h->rptr;
+    a.rcell = h->rcell;
+    a.rrow = h->rrow;
+    return a;
+}
+
+bool is3d(const lsrtm_handle *h) { return h->g.ndim == 3; }
+
 bool use_graphs(const lsrtm_handle *h) { return h->cfg.plan == LSRTM_PLAN_BATCHED; }
 
 cudaEvent_t take_event(lsrtm_handle *h)
@@ -301,6 +333,14 @@ int timing_kind(int graph_kind)
 
 // Runs `body` (which enqueues the nt-step loop of one batch on h->work),
 // captured once into a CUDA graph per (kind, batch) and replayed afterwards.
+// Kernel launches one nt-step loop of this kind contains.
+long long loop_launches(const lsrtm_handle *h, int kind)
+{
+    const long long nt = h->g.nt;
+    if (h->g.ndim != 3) return nt;
+    return kind == G_ADJ ? 2 * nt - 1 : 2 * nt;
+}
+
 template <class F>
 lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
 {
@@ -336,11 +376,11 @@ lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
         }
         CU(cudaGraphLaunch(exec, h->work));
     }
-    h->launches += h->g.nt;
+    h->launches += loop_launches(h, kind);
     if (h->timing && ea && eb) {
         CU(cudaEventRecord(eb, h->work));
         double cells = (double)bs * h->g.Nz * h->g.Ny * h->g.Nx * h->g.nt;
-        h->pending.push_back({timing_kind(kind), ea, eb, (long long)h->g.nt, cells});
+        h->pending.push_back({timing_kind(kind), ea, eb, loop_launches(h, kind), cells});
     } else {
         if (ea) h->event_pool.push_back(ea);
         if (eb) h->event_pool.push_back(eb);
@@ -354,8 +394,8 @@ lsrtm_status zero_slots(lsrtm_handle *h, int bs)
 {
     size_t sb = (size_t)bs * h->sstride * sizeof(float);
     CU(cudaMemsetAsync(h->st[0], 0, sb, h->work));
-    CU(cudaMemsetAsync(h->st[1], 0, sb, h->work));
-    CU(cudaMemsetAsync(h->psiv, 0, (size_t)bs * h->vstride * sizeof(float), h->work));
+    if (h->st[1]) CU(cudaMemsetAsync(h->st[1], 0, sb, h->work));
+    if (h->psiv) CU(cudaMemsetAsync(h->psiv, 0, (size_t)bs * h->vstride * sizeof(float), h->work));
     return LSRTM_OK;
 }
 
@@ -371,24 +411,49 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
         int bs = batch_size(h, s0);
         CHECK(zero_slots(h, bs));
         if (hess) CU(cudaMemsetAsync(h->hess, 0, (size_t)bs * plane * sizeof(float), h->work));
-        CHECK(run_loop(h, hess ? G_BG_HESS : G_BG, s0, bs, [&]() -> lsrtm_status {
-            Step2D a = step_args(h, s0);
-            for (int n = 0; n < nt; ++n) {
-                a.n = n;
-                a.in = h->st[n & 1];
-                a.out = h->st[(n + 1) & 1];
-                CU(launch_fwd2d(a, bs, false, true, hess, h->work));
+        if (is3d(h)) {
+            // in place: p^{nt-1} is copied out between the two stages of the last step
+            CHECK(run_loop(h, hess ? G_BG_HESS : G_BG, s0, bs, [&]() -> lsrtm_status {
+                Step3D a = step3_args(h, s0);
+                for (int n = 0; n < nt; ++n) {
+                    a.n = n;
+                    if (n + 1 < nt) {
+                        CU(launch_fwd3d(a, bs, false, true, hess, 3, h->work));
+                        continue;
+                    }
+                    CU(launch_fwd3d(a, bs, false, true, hess, 1, h->work));
+                    for (int s = 0; s < bs; ++s)
+                        CU(cudaMemcpyAsync(h->final_state + (size_t)(s0 + s) * 4 * plane, h->st[0] + s * h->sstride,
+                                           plane * sizeof(float), cudaMemcpyDeviceToDevice, h->work));
+                    CU(launch_fwd3d(a, bs, false, true, hess, 2, h->work));
+                }
+                return LSRTM_OK;
+            }));
+            for (int s = 0; s < bs; ++s)
+                CU(cudaMemcpyAsync(h->final_state + (size_t)(s0 + s) * 4 * plane + plane,
+                                   h->st[0] + s * h->sstride + 1 * plane, 3 * plane * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, h->work));
+        } else {
+            CHECK(run_loop(h, hess ? G_BG_HESS : G_BG, s0, bs, [&]() -> lsrtm_status {
+                Step2D a = step_args(h, s0);
+                for (int n = 0; n < nt; ++n) {
+                    a.n = n;
+                    a.in = h->st[n & 1];
+                    a.out = h->st[(n + 1) & 1];
+                    CU(launch_fwd2d(a, bs, false, true, hess, h->work));
+                }
+                return LSRTM_OK;
+            }));
+            // final state: p^{nt-1} is the input of the last step, v^{nt-1/2} its output
+            const float *pin = h->st[(nt - 1) & 1];
+            const float *vout = h->st[nt & 1];
+            for (int s = 0; s < bs; ++s) {
+                float *fs = h->final_state + (size_t)(s0 + s) * 3 * plane;
+                CU(cudaMemcpyAsync(fs, pin + s * h->sstride, plane * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   h->work));
+                CU(cudaMemcpyAsync(fs + plane, vout + s * h->sstride + 1 * plane, 2 * plane * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, h->work));
             }
-            return LSRTM_OK;
-        }));
-        // final state: p^{nt-1} is the input of the last step, v^{nt-1/2} its output
-        const float *pin = h->st[(nt - 1) & 1];
-        const float *vout = h->st[nt & 1];
-        for (int s = 0; s < bs; ++s) {
-            float *fs = h->final_state + (size_t)(s0 + s) * 3 * plane;
-            CU(cudaMemcpyAsync(fs, pin + s * h->sstride, plane * sizeof(float), cudaMemcpyDeviceToDevice, h->work));
-            CU(cudaMemcpyAsync(fs + plane, vout + s * h->sstride + 1 * plane, 2 * plane * sizeof(float),
-                               cudaMemcpyDeviceToDevice, h->work));
         }
         if (hess) {
             CU(launch_hess_accumulate(h->g, h->hess, bs, h->hess_acc, h->work));
@@ -413,6 +478,14 @@ lsrtm_status born_core(lsrtm_handle *h)
         int bs = batch_size(h, s0);
         CHECK(zero_slots(h, bs));
         CHECK(run_loop(h, G_BORN, s0, bs, [&]() -> lsrtm_status {
+            if (is3d(h)) {
+                Step3D a = step3_args(h, s0);
+                for (int n = 0; n < nt; ++n) {
+                    a.n = n;
+                    CU(launch_fwd3d(a, bs, true, false, false, 3, h->work));
+                }
+                return LSRTM_OK;
+            }
             Step2D a = step_args(h, s0);
             for (int n = 0; n < nt; ++n) {
                 a.n = n;
@@ -438,23 +511,40 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
     for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
         int bs = batch_size(h, s0);
         CHECK(zero_slots(h, bs));
-        CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
-        CU(launch_pack_adjoint(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
-        CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1,
-                                  reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
-        h->launches += 2;
-        CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
-            Step2D a = step_args(h, s0);
-            for (int i = 0; i < nt; ++i) {
-                a.n = nt - 1 - i;
-                a.in = h->st[i & 1];
-                a.out = h->st[(i + 1) & 1];
-                CU(launch_adj2d(a, bs, h->work));
-            }
-            return LSRTM_OK;
-        }));
-        CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
-        h->launches++;
+        if (h->img) CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
+        if (is3d(h)) {
+            CU(launch_pack_adjoint3d(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
+            Step3D a0 = step3_args(h, s0);
+            CU(launch_adj3d_init(a0, bs, h->work));
+            h->launches += 2;
+            CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
+                Step3D a = step3_args(h, s0);
+                for (int i = 0; i < nt; ++i) {
+                    a.n = nt - 1 - i;
+                    CU(launch_adj3d(a, bs, h->work));
+                }
+                return LSRTM_OK;
+            }));
+            CU(launch_image_accumulate3d(h->g, h->st[0], h->sstride, bs, h->img_acc, h->work));
+            h->launches++;
+        } else {
+            CU(launch_pack_adjoint(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
+            CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1,
+                                      reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
+            h->launches += 2;
+            CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
+                Step2D a = step_args(h, s0);
+                for (int i = 0; i < nt; ++i) {
+                    a.n = nt - 1 - i;
+                    a.in = h->st[i & 1];
+                    a.out = h->st[(i + 1) & 1];
+                    CU(launch_adj2d(a, bs, h->work));
+                }
+                return LSRTM_OK;
+            }));
+            CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
+            h->launches++;
+        }
     }
     CU(launch_image_finalize(h->g, h->img_acc, h->kdt, h->binv, gout, h->work));
     h->launches++;
@@ -483,8 +573,8 @@ lsrtm_status check_finite(lsrtm_handle *h, const float *x, long long n, const ch
 lsrtm_status validate_cfg(const lsrtm_config *c)
 {
     if (!c) return fail(LSRTM_ERR_ARG, "null config");
-    if (c->ndim != 2)
-        return fail(LSRTM_ERR_ARG, "ndim must be 2 (the 3D kernels are not part of this build)");
+    if (c->ndim != 2 && c->ndim != 3) return fail(LSRTM_ERR_ARG, "ndim must be 2 or 3");
+    if (c->ndim == 3 && (c->ny < 1 || !(c->dy > 0))) return fail(LSRTM_ERR_ARG, "3D needs ny >= 1 and dy > 0");
     if (c->fd_order != 4 && c->fd_order != 8) return fail(LSRTM_ERR_ARG, "fd_order must be 4 or 8");
     if (c->nz < 1 || c->nx < 1 || c->nt < 1) return fail(LSRTM_ERR_ARG, "empty grid or nt < 1");
     if (c->npml < c->fd_order / 2) return fail(LSRTM_ERR_ARG, "npml must be >= fd_order/2");
@@ -519,6 +609,46 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         long long k = geo->src_idx[s];
         if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "source outside the interior grid");
         src[s] = (int)pad_cell(k);
+    }
+    if (g.ndim == 3) {
+        // per shot: receivers sorted by cell, and a node map to the first receiver at each node
+        std::vector<int> rptr(h->nshot + 1, 0), rcell, rrow;
+        rcell.reserve(h->nrec_total);
+        rrow.reserve(h->nrec_total);
+        for (int s = 0; s < h->nshot; ++s) {
+            std::vector<std::pair<long long, int>> L;
+            for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
+                long long k = geo->rec_idx[r];
+                if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
+                L.emplace_back(pad_cell(k), r);
+            }
+            std::stable_sort(L.begin(), L.end(),
+                             [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) {
+                                 return a.first < b.first;
+                             });
+            for (auto &e : L) {
+                rcell.push_back((int)e.first);
+                rrow.push_back(e.second);
+            }
+            rptr[s + 1] = (int)rcell.size();
+        }
+        CHECK(dalloc_t(h, &h->src_cell, src.size()));
+        CHECK(dalloc_t(h, &h->rptr, rptr.size()));
+        CHECK(dalloc_t(h, &h->rcell, std::max<size_t>(rcell.size(), 1)));
+        CHECK(dalloc_t(h, &h->rrow, std::max<size_t>(rrow.size(), 1)));
+        CHECK(dalloc_t(h, &h->rmap, (size_t)h->nshot * g.plane));
+        CU(cudaMemsetAsync(h->rmap, 0xff, (size_t)h->nshot * g.plane * sizeof(int), h->work));   // -1
+        CU(cudaMemcpyAsync(h->src_cell, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+        CU(cudaMemcpyAsync(h->rptr, rptr.data(), rptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+        if (!rcell.empty()) {
+            CU(cudaMemcpyAsync(h->rcell, rcell.data(), rcell.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+            CU(cudaMemcpyAsync(h->rrow, rrow.data(), rrow.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+        }
+        // first receiver of each node of each shot
+        for (int s = 0; s < h->nshot; ++s)
+            CU(launch_rmap_scatter(h->rmap + (size_t)s * g.plane, h->rcell, rptr[s], rptr[s + 1], h->work));
+        CU(cudaStreamSynchronize(h->work));
+        return LSRTM_OK;
     }
     int ntx = (g.Nx + h->txo - 1) / h->txo, ntz = (g.Nz + h->tzc - 1) / h->tzc;
     int ntiles = ntx * ntz;
@@ -576,14 +706,15 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     GridDev &g = h->g;
     g.ndim = cfg->ndim;
     g.M = cfg->fd_order / 2;
+    const bool d3 = cfg->ndim == 3;
     g.nz = cfg->nz;
-    g.ny = 1;
+    g.ny = d3 ? cfg->ny : 1;
     g.nx = cfg->nx;
     g.z0 = cfg->npml;
-    g.y0 = 0;
+    g.y0 = d3 ? cfg->npml : 0;
     g.x0 = cfg->npml;
     g.Nz = g.nz + 2 * cfg->npml;
-    g.Ny = 1;
+    g.Ny = d3 ? g.ny + 2 * cfg->npml : 1;
     g.Nx = g.nx + 2 * cfg->npml;
     g.pitch = (g.Nx + 31) / 32 * 32;
     g.rowz = (long long)g.Ny * g.pitch;
@@ -605,7 +736,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         int nchunk = std::max(1, (g.Nz + 56) / 112);
         h->tzc = (g.Nz + nchunk - 1) / nchunk;
     }
-    h->src_scale = (float)(cfg->dt / (cfg->dz * cfg->dx));
+    h->src_scale = (float)(d3 ? cfg->dt / (cfg->dz * cfg->dy * cfg->dx) : cfg->dt / (cfg->dz * cfg->dx));
 
     // model on the device
     CHECK(dalloc_t(h, &h->scratch1, 2 * h->nint));
@@ -626,6 +757,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     }
     {
         double s = 0.0, inv2 = 1.0 / (cfg->dz * cfg->dz) + 1.0 / (cfg->dx * cfg->dx);
+        if (d3) inv2 += 1.0 / (cfg->dy * cfg->dy);
         for (int l = 0; l < g.M; ++l) s += std::fabs(c[l]);
         double lim = 1.0 / (vmax * std::sqrt(inv2) * s);
         if (!(cfg->dt < lim)) {
@@ -688,19 +820,24 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     CHECK(dalloc_t(h, &h->dotwork, 152 * 4 + 32));
 
     // bands and final states for every shot
-    h->bands.nb = 2LL * g.M * (g.nz + g.nx);
+    h->bands.nb = d3 ? 2LL * g.M * ((long long)g.nz * g.ny + (long long)g.nz * g.nx + (long long)g.ny * g.nx)
+                     : 2LL * g.M * (g.nz + g.nx);
     h->bands.bf16 = (cfg->plan == LSRTM_PLAN_BATCHED && cfg->band_precision == LSRTM_BAND_BF16) ? 1 : 0;
     size_t esz = h->bands.bf16 ? 2 : 4;
     size_t band_bytes = (size_t)h->nshot * g.nt * h->bands.nb * esz;
     CHECK(dalloc(h, &h->band_mem, 2 * band_bytes));
     h->bands.p = h->band_mem;
     h->bands.v = static_cast<char *>(h->band_mem) + band_bytes;
-    CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * 3 * g.plane));
+    h->fs_planes = d3 ? 4 : 3;
+    CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * h->fs_planes * g.plane));
 
     // wavefield slots: as many shots per batch as the budget allows
-    h->sstride = kStatePlanes2D * g.plane;
-    h->vstride = kPsivPlanes2D * g.plane;
-    size_t per_slot = (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
+    // 2D: ping-pong state + in-place node CPML planes + image plane; 3D: one in-place state
+    // of 20 planes (pairs, CPML memories, images) + the pseudo-Hessian plane
+    h->sstride = (d3 ? kStatePlanes3D : kStatePlanes2D) * g.plane;
+    h->vstride = d3 ? 0 : kPsivPlanes2D * g.plane;
+    size_t per_slot = d3 ? ((size_t)h->sstride + g.plane) * sizeof(float)
+                         : (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
     int batch = cfg->plan == LSRTM_PLAN_PLAIN ? 1 : (cfg->shots_per_batch > 0 ? cfg->shots_per_batch : h->nshot);
     batch = std::min(batch, h->nshot);
     size_t cg_bytes = (5 * 2 * (size_t)h->nint + (size_t)nd) * sizeof(float);
@@ -712,9 +849,11 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     }
     h->batch = batch;
     CHECK(dalloc_t(h, &h->st[0], (size_t)batch * h->sstride));
-    CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride));
-    CHECK(dalloc_t(h, &h->psiv, (size_t)batch * h->vstride));
-    CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
+    if (!d3) {
+        CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride));
+        CHECK(dalloc_t(h, &h->psiv, (size_t)batch * h->vstride));
+        CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
+    }
     CHECK(dalloc_t(h, &h->hess, (size_t)batch * g.plane));
     CU(cudaStreamSynchronize(h->work));
     return LSRTM_OK;

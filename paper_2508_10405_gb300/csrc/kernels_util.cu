@@ -298,6 +298,13 @@ __global__ void k_precond(const float *h, const float *hmax, float eps, long lon
     }
 }
 
+// rmap[rcell[q]] = q for the first entry q of every run of equal cells in [q0, q1).
+__global__ void k_rmap_scatter(int *rmap, const int *rcell, int q0, int q1)
+{
+    for (int q = q0 + blockIdx.x * blockDim.x + threadIdx.x; q < q1; q += gridDim.x * blockDim.x)
+        if (q == q0 || rcell[q - 1] != rcell[q]) rmap[rcell[q]] = q;
+}
+
 int grid_for(long long n)
 {
     long long b = (n + NT - 1) / NT;
@@ -373,6 +380,13 @@ cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaS
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s)
 {
     k_nonfinite<<<grid_for(n), NT, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmap_scatter(int *rmap, const int *rcell, int q0, int q1, cudaStream_t s)
+{
+    if (q1 <= q0) return cudaSuccess;
+    k_rmap_scatter<<<grid_for(q1 - q0), NT, 0, s>>>(rmap, rcell, q0, q1);
     return cudaGetLastError();
 }
 

@@ -76,6 +76,39 @@ struct Step2D {
     float2 *img;          // [batch][plane] image accumulators (adjoint)
 };
 
+// Arguments of the 3D time-step kernels (state updated in place).
+struct Step3D {
+    GridDev g;
+    Pml pml;
+    const float *kdt, *binv;
+    const float2 *kd2, *br2;  // Born pairs, as in Step2D
+    float *st;                // slot 0 of the batch; slot stride sstride floats
+    long long sstride;
+    int n;
+    int shot0;
+    const float *wav;
+    int wav_per_shot;
+    const int *src_cell;
+    float src_scale;
+    Bands bands;
+    float *hess;              // [batch][plane]
+    float *dstage;            // records (forward) or residual (adjoint), [nrec_total][nt]
+    const int *rmap;          // [nshot][plane]: first entry of the node's receivers in rcell/rrow, or -1
+    const int *rptr;          // [nshot+1] per-shot ranges of rcell/rrow
+    const int *rcell;         // receiver cells, sorted by cell within a shot
+    const int *rrow;          // global receiver rows
+};
+
+// 3D launchers (kernels3d.cu). stages: 1 = velocity stage, 2 = pressure stage, 3 = both.
+cudaError_t launch_fwd3d(const Step3D &a, int batch, bool born, bool bands, bool hess, int stages,
+                         cudaStream_t s);
+cudaError_t launch_adj3d_init(const Step3D &a, int batch, cudaStream_t s);
+cudaError_t launch_adj3d(const Step3D &a, int batch, cudaStream_t s);
+cudaError_t launch_pack_adjoint3d(const GridDev &g, const float *final_state, int shot0, int batch,
+                                  float *st, long long sstride, cudaStream_t s);
+cudaError_t launch_image_accumulate3d(const GridDev &g, const float *st, long long sstride, int batch,
+                                      double2 *acc, cudaStream_t s);
+
 // 2D kernels: CTAs of kThreads2D threads, one x-column per thread; a CTA owns
 // march2d_txo(M) output columns and a z-chunk of Step2D::tzc rows.
 constexpr int kThreads2D = 256;
@@ -110,6 +143,8 @@ cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s);
 cudaError_t launch_comb(const GridDev &g, int param, int spacing, float *m, cudaStream_t s);
+// rmap[rcell[q]] = q for the first receiver q of each node in [q0, q1) (3D receiver maps).
+cudaError_t launch_rmap_scatter(int *rmap, const int *rcell, int q0, int q1, cudaStream_t s);
 
 // FP64-accumulated vector kernels for the Krylov driver.
 cudaError_t launch_dot(const float *x, const float *y, long long n, double *out, double *work,
