@@ -78,6 +78,8 @@ typedef struct {
     int plan;                /* LSRTM_PLAN_* */
     int shots_per_batch;     /* 0 = automatic */
     int wavelet_per_shot;    /* 0: wavelet [nt] shared; 1: wavelet [nshot][nt] */
+    int checkpoint_interval; /* steps K between checkpoints in checkpoint mode;
+                                0 = automatic (minimises checkpoint + segment-band memory) */
 } lsrtm_config;
 
 typedef struct {
@@ -197,6 +199,14 @@ lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
 
 /* Bytes of device workspace the handle holds. */
 size_t lsrtm_workspace_bytes(const lsrtm_handle *h);
+
+/* How the handle reconstructs the background in reverse time (chosen at
+ * creation from recon_mode and the memory available):
+ *   *mode     LSRTM_RECON_BOUNDARY or LSRTM_RECON_CHECKPOINT (never AUTO)
+ *   *interval checkpoint interval K (0 in boundary mode)
+ *   *batch    shots per batch
+ * Any output pointer may be NULL. Returns LSRTM_ERR_ARG for a NULL handle. */
+lsrtm_status lsrtm_reconstruction(const lsrtm_handle *h, int *mode, int *interval, int *batch);
 
 /* Kernel launches issued by this handle since creation (graph replays count
  * every kernel node they contain). */

@@ -29,7 +29,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
-           "lsrtm_born_static"]
+           "lsrtm_born_static", "lsrtm_reconstruction"]
 
 
 class LsrtmError(RuntimeError):
@@ -46,7 +46,7 @@ class Config(ctypes.Structure):
         ("npml", ctypes.c_int), ("f0", ctypes.c_double), ("pml_vmax", ctypes.c_double),
         ("band_precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
         ("recon_mode", ctypes.c_int), ("plan", ctypes.c_int), ("shots_per_batch", ctypes.c_int),
-        ("wavelet_per_shot", ctypes.c_int),
+        ("wavelet_per_shot", ctypes.c_int), ("checkpoint_interval", ctypes.c_int),
     ]
 
 
@@ -95,6 +95,8 @@ def load_library(path: str | None = None):
     L.lsrtm_timing_read.argtypes = [vp, ctypes.POINTER(Timings), ctypes.c_int]
     L.lsrtm_set_stream.argtypes = [vp, vp]
     L.lsrtm_born_static.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp, vp, vp]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
     L.lsrtm_workspace_bytes.argtypes = [vp]
     L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
     L.lsrtm_kernel_launches.argtypes = [vp]
@@ -146,8 +148,8 @@ class Lsrtm:
 
     def __init__(self, *, ndim, nz, nx, ny=1, dz, dx, dy=None, dt, nt, fd_order, npml, f0,
                  vp, rho, wavelet, src_idx, rec_ptr, rec_idx, pml_vmax=None,
-                 band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_BOUNDARY,
-                 plan=PLAN_BATCHED, shots_per_batch=0, stream=None):
+                 band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_AUTO,
+                 plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, stream=None):
         import torch
         self._lib = load_library()
         self._h = ctypes.c_void_p()
@@ -159,7 +161,7 @@ class Lsrtm:
         self.cfg = Config(ndim, nz, ny if ndim == 3 else 1, nx, dz, dy or dx, dx, dt, nt,
                           fd_order, npml, f0, float(pml_vmax), band_precision,
                           int(hbm_budget_bytes), recon_mode, plan, shots_per_batch,
-                          1 if np.ndim(wavelet) == 2 else 0)
+                          1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval))
         self._src = np.ascontiguousarray(src_idx, dtype=np.int32)
         self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
         self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)
@@ -210,6 +212,12 @@ class Lsrtm:
 
     def kernel_launches(self) -> int:
         return int(self._lib.lsrtm_kernel_launches(self._h))
+
+    def reconstruction(self) -> dict:
+        """{"mode": RECON_BOUNDARY | RECON_CHECKPOINT, "interval": K, "batch": shots per batch}."""
+        m, k, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lsrtm_reconstruction(self._h, ctypes.byref(m), ctypes.byref(k), ctypes.byref(b)))
+        return {"mode": m.value, "interval": k.value, "batch": b.value}
 
     # -- operators
     def born(self, dm, out=None):

@@ -100,6 +100,13 @@ struct lsrtm_handle {
     void *band_mem = nullptr;
     float *final_state = nullptr;
     bool bg_cached = false;
+    // checkpointed reconstruction (App. A alternative when the bands do not fit)
+    bool ckpt = false;
+    int ck_K = 0, ck_nseg = 0, ck_planes = 0;
+    float *rec[2] = {nullptr, nullptr};   // background state for the recomputation
+    float *rec_psiv = nullptr;
+    float *ck_mem = nullptr;              // [nseg][batch][ck_planes][plane]
+    Bands segbands{};                     // bands of one segment of one batch
     // staging
     float *dstage = nullptr;     // [nrec_total][nt]
     float *mstage = nullptr;     // [2][nint]
@@ -342,7 +349,21 @@ long long loop_launches(const lsrtm_handle *h, int kind)
 }
 
 template <class F>
+lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs, long long nlaunch,
+                        long long nsteps, F &&body);
+
+template <class F>
 lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
+{
+    return run_loop_n(h, kind, timing_kind(kind), shot0, bs, loop_launches(h, kind), h->g.nt, body);
+}
+
+// Runs `body` (kernel launches of one loop over a batch), captured once into a
+// CUDA graph per (kind, batch) and replayed afterwards; nlaunch kernel
+// launches and nsteps time steps of the batch are accounted to timing kind tkind.
+template <class F>
+lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs, long long nlaunch,
+                        long long nsteps, F &&body)
 {
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (h->timing) {
@@ -376,11 +397,11 @@ lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
         }
         CU(cudaGraphLaunch(exec, h->work));
     }
-    h->launches += loop_launches(h, kind);
+    h->launches += nlaunch;
     if (h->timing && ea && eb) {
         CU(cudaEventRecord(eb, h->work));
-        double cells = (double)bs * h->g.Nz * h->g.Ny * h->g.Nx * h->g.nt;
-        h->pending.push_back({timing_kind(kind), ea, eb, loop_launches(h, kind), cells});
+        double cells = (double)bs * h->g.Nz * h->g.Ny * h->g.Nx * (double)nsteps;
+        h->pending.push_back({tkind, ea, eb, nlaunch, cells});
     } else {
         if (ea) h->event_pool.push_back(ea);
         if (eb) h->event_pool.push_back(eb);
@@ -499,10 +520,238 @@ lsrtm_status born_core(lsrtm_handle *h)
     return LSRTM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpointed reconstruction. The forward background pass of a batch saves
+// the full background state every K steps; the reverse pass then walks the
+// K-step segments from last to first: it restores the segment's checkpoint,
+// recomputes the background forward over the segment while saving its
+// boundary bands (the same kernel and inputs as the boundary mode, so the
+// same bits), and runs the reverse steps that read those bands.
+// ---------------------------------------------------------------------------
+
+float *ck_slot_base(lsrtm_handle *h, int j) { return h->ck_mem + (size_t)j * h->batch * h->ck_planes * h->g.plane; }
+
+// Copies `planes` contiguous planes of each of bs slots (slot stride sstride
+// floats) into, or out of, planes [p0, p0 + planes) of checkpoint j.
+lsrtm_status ck_copy(lsrtm_handle *h, int j, float *slots, long long sstride, int planes, int p0, int bs,
+                     bool save)
+{
+    const size_t fb = (size_t)h->g.plane * sizeof(float);
+    float *ck = ck_slot_base(h, j) + (size_t)p0 * h->g.plane;
+    const size_t ckpitch = (size_t)h->ck_planes * fb, spitch = (size_t)sstride * sizeof(float);
+    if (save)
+        CU(cudaMemcpy2DAsync(ck, ckpitch, slots, spitch, planes * fb, bs, cudaMemcpyDeviceToDevice, h->work));
+    else
+        CU(cudaMemcpy2DAsync(slots, spitch, ck, ckpitch, planes * fb, bs, cudaMemcpyDeviceToDevice, h->work));
+    return LSRTM_OK;
+}
+
+enum { G_CKF = 4, G_CKF_HESS = 5, G_SEG = 100 };
+
+// Forward background pass of one batch in the main slots: checkpoints every K
+// steps, the final state (p^{nt-1}, v^{nt-1/2}) of each shot of the batch into
+// the batch-local final-state store, and optionally the pseudo-Hessian.
+lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
+{
+    const long long plane = h->g.plane;
+    const int nt = h->g.nt, K = h->ck_K;
+    CHECK(zero_slots(h, bs));
+    if (hess) CU(cudaMemsetAsync(h->hess, 0, (size_t)bs * plane * sizeof(float), h->work));
+    if (is3d(h)) {
+        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, 2LL * nt, nt, [&]() -> lsrtm_status {
+            Step3D a = step3_args(h, s0);
+            for (int n = 0; n < nt; ++n) {
+                a.n = n;
+                if (n % K == 0) CHECK(ck_copy(h, n / K, h->st[0], h->sstride, 10, 0, bs, true));
+                if (n + 1 < nt) {
+                    CU(launch_fwd3d(a, bs, false, false, hess, 3, h->work));
+                    continue;
+                }
+                CU(launch_fwd3d(a, bs, false, false, hess, 1, h->work));
+                CU(cudaMemcpy2DAsync(h->final_state, 4 * plane * sizeof(float), h->st[0], h->sstride * sizeof(float),
+                                     plane * sizeof(float), bs, cudaMemcpyDeviceToDevice, h->work));
+                CU(launch_fwd3d(a, bs, false, false, hess, 2, h->work));
+            }
+            return LSRTM_OK;
+        }));
+        CU(cudaMemcpy2DAsync(h->final_state + plane, 4 * plane * sizeof(float), h->st[0] + plane,
+                             h->sstride * sizeof(float), 3 * plane * sizeof(float), bs, cudaMemcpyDeviceToDevice,
+                             h->work));
+    } else {
+        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, nt, nt, [&]() -> lsrtm_status {
+            Step2D a = step_args(h, s0);
+            for (int n = 0; n < nt; ++n) {
+                a.n = n;
+                a.in = h->st[n & 1];
+                a.out = h->st[(n + 1) & 1];
+                if (n % K == 0) {
+                    CHECK(ck_copy(h, n / K, h->st[n & 1], h->sstride, 5, 0, bs, true));
+                    CHECK(ck_copy(h, n / K, h->psiv, h->vstride, 2, 5, bs, true));
+                }
+                CU(launch_fwd2d(a, bs, false, false, hess, h->work));
+            }
+            return LSRTM_OK;
+        }));
+        CU(cudaMemcpy2DAsync(h->final_state, 3 * plane * sizeof(float), h->st[(nt - 1) & 1],
+                             h->sstride * sizeof(float), plane * sizeof(float), bs, cudaMemcpyDeviceToDevice,
+                             h->work));
+        CU(cudaMemcpy2DAsync(h->final_state + plane, 3 * plane * sizeof(float), h->st[nt & 1] + plane,
+                             h->sstride * sizeof(float), 2 * plane * sizeof(float), bs, cudaMemcpyDeviceToDevice,
+                             h->work));
+    }
+    if (hess) {
+        CU(launch_hess_accumulate(h->g, h->hess, bs, h->hess_acc, h->work));
+        h->launches++;
+    }
+    return LSRTM_OK;
+}
+
+// Reverse steps of segment j: n from min((j+1)K, nt-1) down to jK+1 (down to
+// 0 for the first segment); they read the bands of steps jK .. hi-1.
+void seg_range(const lsrtm_handle *h, int j, int *t0, int *hi, int *lo)
+{
+    *t0 = j * h->ck_K;
+    *hi = std::min((j + 1) * h->ck_K, h->g.nt - 1);
+    *lo = j == 0 ? 0 : *t0 + 1;
+}
+
+// Restores checkpoint j and recomputes the background over steps t0 .. hi-1
+// into the segment band buffer.
+lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
+{
+    int t0, hi, lo;
+    seg_range(h, j, &t0, &hi, &lo);
+    const long long plane = h->g.plane;
+    const long long c = hi - t0;
+    Bands sb = h->segbands;
+    sb.shot0 = s0;
+    sb.t0 = t0;
+    const bool d3 = is3d(h);
+    return run_loop_n(h, G_SEG + 2 * j, 1, s0, bs, d3 ? 2 * c : c, c, [&]() -> lsrtm_status {
+        if (d3) {
+            CHECK(ck_copy(h, j, h->rec[0], 10 * plane, 10, 0, bs, false));
+            Step3D a = step3_args(h, s0);
+            a.st = h->rec[0];
+            a.sstride = 10 * plane;
+            a.bands = sb;
+            for (int n = t0; n < hi; ++n) {
+                a.n = n;
+                CU(launch_fwd3d(a, bs, false, true, false, 3, h->work));
+            }
+            return LSRTM_OK;
+        }
+        CHECK(ck_copy(h, j, h->rec[t0 & 1], 5 * plane, 5, 0, bs, false));
+        CHECK(ck_copy(h, j, h->rec_psiv, 2 * plane, 2, 5, bs, false));
+        Step2D a = step_args(h, s0);
+        a.sstride = 5 * plane;
+        a.vstride = 2 * plane;
+        a.psiv = h->rec_psiv;
+        a.bands = sb;
+        for (int n = t0; n < hi; ++n) {
+            a.n = n;
+            a.in = h->rec[n & 1];
+            a.out = h->rec[(n + 1) & 1];
+            CU(launch_fwd2d(a, bs, false, true, false, h->work));
+        }
+        return LSRTM_OK;
+    });
+}
+
+// The reverse (adjoint) steps of segment j.
+lsrtm_status ck_reverse(lsrtm_handle *h, int s0, int bs, int j)
+{
+    int t0, hi, lo;
+    seg_range(h, j, &t0, &hi, &lo);
+    const int nt = h->g.nt;
+    const long long r = hi - lo + 1;
+    Bands sb = h->segbands;
+    sb.shot0 = s0;
+    sb.t0 = t0;
+    const bool d3 = is3d(h);
+    return run_loop_n(h, G_SEG + 2 * j + 1, 2, s0, bs, d3 ? 2 * r - (lo == 0 ? 1 : 0) : r, r,
+                      [&]() -> lsrtm_status {
+        if (d3) {
+            Step3D a = step3_args(h, s0);
+            a.bands = sb;
+            for (int n = hi; n >= lo; --n) {
+                a.n = n;
+                CU(launch_adj3d(a, bs, h->work));
+            }
+            return LSRTM_OK;
+        }
+        Step2D a = step_args(h, s0);
+        a.bands = sb;
+        for (int n = hi; n >= lo; --n) {
+            const int i = nt - 1 - n;
+            a.n = n;
+            a.in = h->st[i & 1];
+            a.out = h->st[(i + 1) & 1];
+            CU(launch_adj2d(a, bs, h->work));
+        }
+        return LSRTM_OK;
+    });
+}
+
+// Pseudo-Hessian only (checkpoint mode has no cached background pass).
+lsrtm_status ck_hessian(lsrtm_handle *h)
+{
+    CU(cudaMemsetAsync(h->hess_acc, 0, h->nint * sizeof(double), h->work));
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) CHECK(ck_forward(h, s0, batch_size(h, s0), true));
+    CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+    h->launches++;
+    h->hess_ready = true;
+    return LSRTM_OK;
+}
+
+lsrtm_status adjoint_core_ckpt(lsrtm_handle *h, float *gout, bool want_hess)
+{
+    const long long plane = h->g.plane;
+    const int nt = h->g.nt;
+    const bool hess = want_hess && !h->hess_ready;
+    if (hess) CU(cudaMemsetAsync(h->hess_acc, 0, h->nint * sizeof(double), h->work));
+    CU(cudaMemsetAsync(h->img_acc, 0, h->nint * sizeof(double2), h->work));
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
+        int bs = batch_size(h, s0);
+        CHECK(ck_forward(h, s0, bs, hess));
+        CHECK(zero_slots(h, bs));
+        if (h->img) CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
+        if (is3d(h)) {
+            CU(launch_pack_adjoint3d(h->g, h->final_state, 0, bs, h->st[0], h->sstride, h->work));
+            CU(launch_adj3d_init(step3_args(h, s0), bs, h->work));
+        } else {
+            CU(launch_pack_adjoint(h->g, h->final_state, 0, bs, h->st[0], h->sstride, h->work));
+            CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1,
+                                      reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
+        }
+        h->launches += 2;
+        for (int j = h->ck_nseg - 1; j >= 0; --j) {
+            int t0, hi, lo;
+            seg_range(h, j, &t0, &hi, &lo);
+            if (hi < lo) continue;
+            CHECK(ck_recompute(h, s0, bs, j));
+            CHECK(ck_reverse(h, s0, bs, j));
+        }
+        if (is3d(h))
+            CU(launch_image_accumulate3d(h->g, h->st[0], h->sstride, bs, h->img_acc, h->work));
+        else
+            CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
+        h->launches++;
+    }
+    if (hess) {
+        CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+        h->launches++;
+        h->hess_ready = true;
+    }
+    CU(launch_image_finalize(h->g, h->img_acc, h->kdt, h->binv, gout, h->work));
+    h->launches++;
+    return LSRTM_OK;
+}
+
 // L^T of the data in h->dstage; stacked images into h->img_acc, then the
 // chain rule into gout ([2][nint], device).
 lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
 {
+    if (h->ckpt) return adjoint_core_ckpt(h, gout, want_hess);
     const long long plane = h->g.plane;
     const int nt = h->g.nt;
     if (!h->bg_cached || h->cfg.plan == LSRTM_PLAN_PLAIN || (want_hess && !h->hess_ready))
@@ -581,11 +830,13 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
     if (!(c->dt > 0) || !(c->dx > 0) || !(c->dz > 0)) return fail(LSRTM_ERR_ARG, "non-positive spacing or dt");
     if (c->band_precision != LSRTM_BAND_FP32 && c->band_precision != LSRTM_BAND_BF16)
         return fail(LSRTM_ERR_ARG, "band_precision must be 0 (fp32) or 1 (bf16)");
-    if (c->recon_mode != LSRTM_RECON_BOUNDARY && c->recon_mode != LSRTM_RECON_AUTO)
-        return fail(LSRTM_ERR_ARG, "only boundary-band reconstruction is available");
+    if (c->recon_mode != LSRTM_RECON_BOUNDARY && c->recon_mode != LSRTM_RECON_CHECKPOINT &&
+        c->recon_mode != LSRTM_RECON_AUTO)
+        return fail(LSRTM_ERR_ARG, "recon_mode must be 0 (boundary), 1 (checkpoint) or 2 (auto)");
     if (c->plan != LSRTM_PLAN_BATCHED && c->plan != LSRTM_PLAN_PLAIN)
         return fail(LSRTM_ERR_ARG, "unknown plan");
     if (c->shots_per_batch < 0) return fail(LSRTM_ERR_ARG, "shots_per_batch < 0");
+    if (c->checkpoint_interval < 0) return fail(LSRTM_ERR_ARG, "checkpoint_interval < 0");
     return LSRTM_OK;
 }
 
@@ -819,19 +1070,18 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     }
     CHECK(dalloc_t(h, &h->dotwork, 152 * 4 + 32));
 
-    // bands and final states for every shot
+    // Reconstruction of the background in reverse time: boundary bands of
+    // every shot over all nt steps (cached across L^T calls), or, when those do
+    // not fit, full-state checkpoints every K steps per batch from which the
+    // bands of one K-step segment at a time are recomputed.
     h->bands.nb = d3 ? 2LL * g.M * ((long long)g.nz * g.ny + (long long)g.nz * g.nx + (long long)g.ny * g.nx)
                      : 2LL * g.M * (g.nz + g.nx);
     h->bands.bf16 = (cfg->plan == LSRTM_PLAN_BATCHED && cfg->band_precision == LSRTM_BAND_BF16) ? 1 : 0;
-    size_t esz = h->bands.bf16 ? 2 : 4;
-    size_t band_bytes = (size_t)h->nshot * g.nt * h->bands.nb * esz;
-    CHECK(dalloc(h, &h->band_mem, 2 * band_bytes));
-    h->bands.p = h->band_mem;
-    h->bands.v = static_cast<char *>(h->band_mem) + band_bytes;
+    const size_t esz = h->bands.bf16 ? 2 : 4;
+    const size_t fbytes = (size_t)g.plane * sizeof(float);
     h->fs_planes = d3 ? 4 : 3;
-    CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * h->fs_planes * g.plane));
 
-    // wavefield slots: as many shots per batch as the budget allows
+    // wavefield slots
     // 2D: ping-pong state + in-place node CPML planes + image plane; 3D: one in-place state
     // of 20 planes (pairs, CPML memories, images) + the pseudo-Hessian plane
     h->sstride = (d3 ? kStatePlanes3D : kStatePlanes2D) * g.plane;
@@ -841,13 +1091,74 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     int batch = cfg->plan == LSRTM_PLAN_PLAIN ? 1 : (cfg->shots_per_batch > 0 ? cfg->shots_per_batch : h->nshot);
     batch = std::min(batch, h->nshot);
     size_t cg_bytes = (5 * 2 * (size_t)h->nint + (size_t)nd) * sizeof(float);
+    long long avail;   // bytes left for bands, checkpoints and slots
     if (cfg->hbm_budget_bytes) {
-        long long room = (long long)cfg->hbm_budget_bytes - (long long)h->bytes - (long long)cg_bytes;
-        long long fit = room > 0 ? room / (long long)per_slot : 0;
-        if (fit < 1) return fail(LSRTM_ERR_OOM, "hbm_budget_bytes too small for one wavefield slot");
+        avail = (long long)cfg->hbm_budget_bytes - (long long)h->bytes - (long long)cg_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        CU(cudaMemGetInfo(&fr, &tot));
+        avail = (long long)(0.92 * (double)fr) - (long long)cg_bytes;
+    }
+    const size_t band_full = 2 * (size_t)h->nshot * g.nt * h->bands.nb * esz;
+    const size_t fs_full = (size_t)h->nshot * h->fs_planes * fbytes;
+    bool ckpt = cfg->recon_mode == LSRTM_RECON_CHECKPOINT;
+    if (cfg->recon_mode == LSRTM_RECON_AUTO) ckpt = (long long)(band_full + fs_full + per_slot) > avail;
+    h->ckpt = ckpt;
+    if (!ckpt) {
+        CHECK(dalloc(h, &h->band_mem, band_full));
+        h->bands.p = h->band_mem;
+        h->bands.v = static_cast<char *>(h->band_mem) + band_full / 2;
+        h->bands.shot0 = 0;
+        h->bands.t0 = 0;
+        h->bands.nsteps = g.nt;
+        CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * h->fs_planes * g.plane));
+        avail -= (long long)(band_full + fs_full);
+    } else {
+        // checkpoint: the background planes of a forward state (2D: p vx vz psi_px
+        // psi_pz + the two node CPML memories; 3D: p, v, psi_p, psi_v)
+        h->ck_planes = d3 ? 10 : 7;
+        const double seg_step = 2.0 * (double)h->bands.nb * esz;           // band bytes per step
+        const double ck_one = (double)h->ck_planes * fbytes;               // bytes per checkpoint
+        int K = cfg->checkpoint_interval > 0
+                    ? cfg->checkpoint_interval
+                    : (int)std::lround(std::sqrt((double)g.nt * ck_one / seg_step));
+        K = std::max(1, std::min(K, g.nt));
+        h->ck_K = K;
+        h->ck_nseg = (g.nt + K - 1) / K;
+        // recomputation state: 2D 5 + 5 ping-pong planes and 2 CPML planes; 3D 10 in place
+        size_t rec_slot = (d3 ? 10 : 12) * fbytes;
+        size_t ck_slot = (size_t)h->ck_nseg * h->ck_planes * fbytes + (size_t)K * (size_t)seg_step +
+                         rec_slot + h->fs_planes * fbytes;
+        per_slot += ck_slot;
+    }
+    if (avail < (long long)per_slot)
+        return fail(LSRTM_ERR_OOM, cfg->hbm_budget_bytes ? "hbm_budget_bytes too small for one wavefield slot"
+                                                         : "device memory too small for one wavefield slot");
+    {
+        long long fit = avail / (long long)per_slot;
         if (fit < batch) batch = (int)fit;
     }
     h->batch = batch;
+    if (ckpt) {
+        const size_t segb = (size_t)batch * h->ck_K * h->bands.nb * esz;
+        CHECK(dalloc(h, &h->band_mem, 2 * segb));
+        h->segbands = h->bands;
+        h->segbands.p = h->band_mem;
+        h->segbands.v = static_cast<char *>(h->band_mem) + segb;
+        h->segbands.nsteps = h->ck_K;
+        h->bands = h->segbands;
+        h->bands.shot0 = 0;
+        h->bands.t0 = 0;
+        CHECK(dalloc_t(h, &h->ck_mem, (size_t)h->ck_nseg * batch * h->ck_planes * g.plane));
+        CHECK(dalloc_t(h, &h->final_state, (size_t)batch * h->fs_planes * g.plane));
+        if (d3) {
+            CHECK(dalloc_t(h, &h->rec[0], (size_t)batch * 10 * g.plane));
+        } else {
+            CHECK(dalloc_t(h, &h->rec[0], (size_t)batch * 5 * g.plane));
+            CHECK(dalloc_t(h, &h->rec[1], (size_t)batch * 5 * g.plane));
+            CHECK(dalloc_t(h, &h->rec_psiv, (size_t)batch * 2 * g.plane));
+        }
+    }
     CHECK(dalloc_t(h, &h->st[0], (size_t)batch * h->sstride));
     if (!d3) {
         CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride));
@@ -990,7 +1301,7 @@ lsrtm_status cg_begin_impl(lsrtm_handle *h, const float *d, const float *x0, int
         h->launches++;
     }
     if (precond) {
-        if (!h->hess_ready) CHECK(bg_forward(h, true));
+        if (!h->hess_ready) CHECK(h->ckpt ? ck_hessian(h) : bg_forward(h, true));
         CU(cudaMemsetAsync(h->fscal, 0, sizeof(float), s));
         CU(launch_max_abs_reduce(h->hess_img, h->nint, h->fscal, s));
         CU(launch_precond_build(h->hess_img, h->fscal, 1e-3f, h->nint, h->cg_minv, s));
@@ -1148,6 +1459,15 @@ lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream)
 {
     if (!h) return fail(LSRTM_ERR_ARG, "null handle");
     h->user = (cudaStream_t)stream;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_reconstruction(const lsrtm_handle *h, int *mode, int *interval, int *batch)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    if (mode) *mode = h->ckpt ? LSRTM_RECON_CHECKPOINT : LSRTM_RECON_BOUNDARY;
+    if (interval) *interval = h->ckpt ? h->ck_K : 0;
+    if (batch) *batch = h->batch;
     return LSRTM_OK;
 }
 

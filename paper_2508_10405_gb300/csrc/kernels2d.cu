@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
     const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
     const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
     const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
-    const long long bandoff = ((long long)shot * g.nt + a.n) * a.bands.nb;
+    const long long bandoff = band_base(a.bands, shot, a.n);
     const int src = a.src_cell[shot];
     const float wsrc = a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + a.n];
     constexpr int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
     const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
     const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
-    const long long bandprev = ((long long)shot * g.nt + (n - 1)) * a.bands.nb;
+    const long long bandprev = band_base(a.bands, shot, n - 1);
     const int src = a.src_cell[shot];
     const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1] : 0.f;
     const float2 *imgs = a.img + slot * plane;   // image accumulators of this slot
@@ -812,6 +812,7 @@ cudaError_t attr_M()
     if ((e = attr_fwd<M, true, false, false>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, true, true>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, true, false>()) != cudaSuccess) return e;
+    if ((e = attr_fwd<M, false, false, true>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, false, false>()) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_adj2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
 }
@@ -823,6 +824,7 @@ cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool
     if (born) return launch_fwd_t<M, true, false, false>(a, grid, s);
     if (bands && hess) return launch_fwd_t<M, false, true, true>(a, grid, s);
     if (bands) return launch_fwd_t<M, false, true, false>(a, grid, s);
+    if (hess) return launch_fwd_t<M, false, false, true>(a, grid, s);
     return launch_fwd_t<M, false, false, false>(a, grid, s);
 }
 

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k3_v(const Step3D a)
     const T *P = S + (BORN ? B3_P / 2 : G3_P) * plane;
     const R *br = BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv);
     const int shot = a.shot0 + c.slot;
-    const long long bandoff = ((long long)shot * g.nt + a.n) * a.bands.nb;
+    const long long bandoff = band_base(a.bands, shot, a.n);
     const float dt = g.dt;
     const R b0 = br[cc];
 #pragma unroll
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k3_p(const Step3D a)
     const int iz = c.z - g.z0, iy = c.y - g.y0, ix = c.x - g.x0;
     if (BANDS) {
         long long b = pband3(g, iz, iy, ix);
-        if (b >= 0) band_put(a.bands, a.bands.p, ((long long)shot * g.nt + a.n) * a.bands.nb + b, xof(p0));
+        if (b >= 0) band_put(a.bands, a.bands.p, band_base(a.bands, shot, a.n) + b, xof(p0));
     }
     if (HESS) {
         if (iz >= 0 && iz < g.nz && iy >= 0 && iy < g.ny && ix >= 0 && ix < g.nx) {
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k3_a(const Step3D a)
     const int shot = a.shot0 + c.slot;
     const float dt = g.dt;
     const bool recon = a.n > 0;
-    const long long bandprev = ((long long)shot * g.nt + (a.n - 1)) * a.bands.nb;
+    const long long bandprev = band_base(a.bands, shot, a.n - 1);
     const float b0 = a.binv[cc];
     const int iz = c.z - g.z0, iy = c.y - g.y0, ix = c.x - g.x0;
     for (int d = 0; d < 3; ++d) {
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
             pn -= a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1];
     } else {
         long long b = pband3(g, c.z - g.z0, c.y - g.y0, c.x - g.x0);
-        if (b >= 0) pn = band_get(a.bands, a.bands.p, ((long long)shot * g.nt + (n - 1)) * a.bands.nb + b);
+        if (b >= 0) pn = band_get(a.bands, a.bands.p, band_base(a.bands, shot, n - 1) + b);
     }
     const float lpn = lp3 + residual_at(a, shot, cc, n - 1);
     if (in) st[A3_IMK * plane + cc] += E.x * lpn;
@@ -510,11 +510,13 @@ cudaError_t launch_fwd3d(const Step3D &a, int batch, bool born, bool bands, bool
         if (born) L3(2, true, false, false);
         else if (bands && hess) L3(2, false, true, true);
         else if (bands) L3(2, false, true, false);
+        else if (hess) L3(2, false, false, true);
         else L3(2, false, false, false);
     } else {
         if (born) L3(4, true, false, false);
         else if (bands && hess) L3(4, false, true, true);
         else if (bands) L3(4, false, true, false);
+        else if (hess) L3(4, false, false, true);
         else L3(4, false, false, false);
     }
 #undef L3

@@ -36,12 +36,20 @@ struct Pml {
 // band each hold NB values laid out as strips:
 //   2D: [x-left M*nz][x-right M*nz][z-top M*nx][z-bottom M*nx]
 //   3D: [x-faces 2*M*nz*ny][y-faces 2*M*nz*nx][z-faces 2*M*ny*nx]
+// The buffers hold steps [t0, t0 + nsteps) of shots [shot0, ...): the band of
+// shot s at step n starts at ((s - shot0) * nsteps + (n - t0)) * NB.
 struct Bands {
-    void *p;              // [nshot][nt][NB]
-    void *v;              // [nshot][nt][NB]
+    void *p;              // [shots][nsteps][NB]
+    void *v;              // [shots][nsteps][NB]
     long long nb;         // NB
     int bf16;             // element type: 0 float, 1 bf16
+    int shot0, t0, nsteps;
 };
+
+__host__ __device__ inline long long band_base(const Bands &b, int shot, int n)
+{
+    return ((long long)(shot - b.shot0) * b.nsteps + (n - b.t0)) * b.nb;
+}
 
 // Receivers grouped by (shot, tile): CSR over shot*ntiles + tile.
 struct TileRecs {

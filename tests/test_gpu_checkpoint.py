@@ -1,0 +1,155 @@
+"""Checkpointed reconstruction of the background in reverse time.
+
+In checkpoint mode the forward pass keeps full background states every K
+steps and L^T recomputes the boundary bands of one K-step segment at a time
+from them. The recomputation runs the same kernels on the same inputs as the
+boundary mode's forward pass, so the images must equal the boundary mode's to
+FP32 rounding (they are compared bit for bit and within 1e-6), and the oracle
+within the parity tolerance. Intervals cover one step per segment, a last
+segment left empty ((nt - 1) divisible by K), one segment, the automatic
+choice, and ragged shot batches."""
+import numpy as np
+import pytest
+
+import lsrtm_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+
+CASES = {
+    "2d_o4": dict(nz=20, nx=27, nt=90, order=4, npml=5, nshot=3, seed=211),
+    "2d_o8": dict(nz=23, nx=19, nt=75, order=8, npml=6, nshot=3, seed=212),
+    "3d_o4": dict(ndim=3, nz=12, ny=10, nx=14, nt=70, order=4, npml=5, nshot=2, seed=213),
+}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cpu(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def handle(w, **kw):
+    from paper_2508_10405_gb300 import Lsrtm
+    return Lsrtm.from_workload(w, **kw)
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    w = li.small_case(**CASES[request.param])
+    rng = np.random.default_rng(9)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    return request.param, w, dres
+
+
+def _intervals(nt):
+    # 1 step per segment; (nt - 1) % K == 0 leaves the last segment empty;
+    # a single segment; a ragged last segment; automatic
+    return [1, nt - 1, nt, 16, 0]
+
+
+def test_checkpoint_equals_boundary_and_oracle(case):
+    from paper_2508_10405_gb300 import RECON_BOUNDARY, RECON_CHECKPOINT
+    name, w, dres = case
+    d = torch.tensor(dres, dtype=torch.float32, device="cuda")
+    hb = handle(w, recon_mode=RECON_BOUNDARY)
+    assert hb.reconstruction()["mode"] == RECON_BOUNDARY
+    gb = hb.adjoint(d)
+    ref = oracle.adjoint(w, dres)
+    assert rel(cpu(gb), ref) < TOL
+    for K in _intervals(w.nt):
+        hc = handle(w, recon_mode=RECON_CHECKPOINT, checkpoint_interval=K)
+        info = hc.reconstruction()
+        assert info["mode"] == RECON_CHECKPOINT and info["interval"] >= 1
+        gc = hc.adjoint(d)
+        e_b = rel(cpu(gc), cpu(gb))
+        e_o = rel(cpu(gc), ref)
+        same = bool(torch.equal(gc, gb))
+        print(f"{name} K={info['interval']}: vs boundary mode {e_b:.3e} (bitwise {same}), vs oracle {e_o:.3e}")
+        assert e_b < 1e-6
+        assert e_o < TOL
+        # a second call reuses the captured graphs
+        assert torch.equal(hc.adjoint(d), gc)
+        hc.close()
+    hb.close()
+
+
+def test_checkpoint_ragged_batches_and_hessian():
+    from paper_2508_10405_gb300 import RECON_BOUNDARY, RECON_CHECKPOINT
+    w = li.small_case(**CASES["2d_o8"])
+    rng = np.random.default_rng(10)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    d = torch.tensor(dres, dtype=torch.float32, device="cuda")
+    hb = handle(w, recon_mode=RECON_BOUNDARY, shots_per_batch=2)
+    hc = handle(w, recon_mode=RECON_CHECKPOINT, shots_per_batch=2, checkpoint_interval=11)
+    assert hc.reconstruction()["batch"] == 2
+    gb, phb = hb.adjoint(d, pseudo_hessian=True)
+    gc, phc = hc.adjoint(d, pseudo_hessian=True)
+    print(f"ragged batches: image {rel(cpu(gc), cpu(gb)):.3e}, pseudo-Hessian {rel(cpu(phc), cpu(phb)):.3e}")
+    assert rel(cpu(gc), cpu(gb)) < 1e-6
+    assert rel(cpu(phc), cpu(phb)) < 1e-6
+    assert rel(cpu(phc), oracle.pseudo_hessian(w)) < TOL
+    # preconditioned CGNR builds the pseudo-Hessian through the checkpoint pass
+    dobs = oracle.born(w, w.dm)
+    dt = torch.tensor(dobs, dtype=torch.float32, device="cuda")
+    hc2 = handle(w, recon_mode=RECON_CHECKPOINT, checkpoint_interval=7)
+    xb, mb = hb.cg_solve(dt, 3, precond=True)
+    xc, mc = hc2.cg_solve(dt, 3, precond=True)
+    print(f"PCGNR checkpoint vs boundary: x {rel(cpu(xc), cpu(xb)):.3e}, misfits {mc} {mb}")
+    assert np.allclose(mc, mb, rtol=1e-5, atol=1e-7)
+    assert rel(cpu(xc), cpu(xb)) < 1e-5
+    for h in (hb, hc, hc2):
+        h.close()
+
+
+def test_auto_mode_follows_the_budget():
+    from paper_2508_10405_gb300 import RECON_AUTO, RECON_BOUNDARY, RECON_CHECKPOINT, LsrtmError
+    w = li.small_case(nz=60, nx=80, nt=600, order=8, npml=8, nshot=4, seed=214)
+    h = handle(w, recon_mode=RECON_AUTO)
+    assert h.reconstruction()["mode"] == RECON_BOUNDARY
+    full = h.workspace_bytes()
+    h.close()
+    # a budget below the band store forces checkpoints
+    h = handle(w, recon_mode=RECON_AUTO, hbm_budget_bytes=int(0.6 * full))
+    info = h.reconstruction()
+    print(f"boundary workspace {full / 1e6:.1f} MB; at 60%: {info}, {h.workspace_bytes() / 1e6:.1f} MB")
+    assert info["mode"] == RECON_CHECKPOINT
+    assert h.workspace_bytes() <= int(0.6 * full)
+    rng = np.random.default_rng(11)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    g = cpu(h.adjoint(torch.tensor(dres, dtype=torch.float32, device="cuda")))
+    assert rel(g, oracle.adjoint(w, dres)) < TOL
+    h.close()
+    with pytest.raises(LsrtmError):
+        handle(w, recon_mode=RECON_BOUNDARY, hbm_budget_bytes=int(0.6 * full))
+
+
+def test_checkpoint_autograd_workload_under_cap():
+    """The autograd workload (200 x 200, 16 shots, nt = 1500) under a 128 MB
+    workspace cap: checkpoints, batches of a few shots, and the same image as
+    the boundary mode with all shots in one batch."""
+    from paper_2508_10405_gb300 import RECON_AUTO, RECON_BOUNDARY, RECON_CHECKPOINT
+    w = li.preset(3)
+    rng = np.random.default_rng(12)
+    dres = rng.standard_normal((w.geom.nrec_total, w.nt))
+    d = torch.tensor(dres, dtype=torch.float32, device="cuda")
+    hb = handle(w, recon_mode=RECON_BOUNDARY)
+    gb = hb.adjoint(d)
+    hb.close()
+    hc = handle(w, recon_mode=RECON_AUTO, hbm_budget_bytes=128 << 20)
+    info = hc.reconstruction()
+    print(f"autograd workload at 128 MB: {info}, workspace {hc.workspace_bytes() / 1e6:.1f} MB")
+    assert info["mode"] == RECON_CHECKPOINT and info["batch"] < w.geom.nshot
+    gc = hc.adjoint(d)
+    e = rel(cpu(gc), cpu(gb))
+    print(f"checkpoint (batches of {info['batch']}) vs boundary (one batch): {e:.3e}")
+    assert e < 1e-6
+    hc.close()
