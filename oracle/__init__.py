@@ -13,6 +13,8 @@ Layers:
   * this module: ctypes marshalling plus textbook FP64 numpy routines built on
     those operators: CGLS/CGNR and its diagonally preconditioned variant
     (Sec. 3), the spike comb and PSF / remigration probes (App. D).
+  * ``deblur.py``: the nonstationary 11 x 11 deblurring filters of App. E
+    (FP64 normal equations per comb window, bilinear valence blending).
 
 Pinned by the ``-m "not gpu"`` tests against: textbook staggered FD
 coefficients, the 2D and 3D homogeneous Green's functions, the normal
