@@ -197,6 +197,33 @@ lsrtm_status lsrtm_born_static(const lsrtm_config *cfg, const float *vp, const f
 /* Replaces the stream used by later calls. */
 lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
 
+/* Nonstationary deblurring (image-domain LSRTM, App. E) of a 2D image pair.
+ * App. E connects the reference image m' = m_rtm and the remigrated image
+ * m'' = L^T L m' by a convolution with the inverse of a locally
+ * translation-invariant Hessian. Per comb node (z_k, x_k) = (s/2 + i s,
+ * s/2 + j s) a flen x flen filter f_k minimises, over the pixels p within s
+ * of the node (clipped to the image),
+ *     sum_p ((f * m'')(p) - m'(p))^2 + eps_k ||f||^2,
+ *     (f * g)(p) = sum_{|a|,|b|<=flen/2} f[a][b] g(p - (a, b)), g = 0 outside,
+ *     eps_k = eps * trace(A^T A) / flen^2,
+ * through FP64 normal equations and a Cholesky factorisation (a window with
+ * m'' = 0 gets the zero filter). Then
+ *     dm_out = sum_k w_k (f_k * m_rtm) / sum_k w_k,
+ *     w_k(p) = max(0, 1 - |z - z_k|/s) max(0, 1 - |x - x_k|/s),
+ * each parameter plane filtered on its own (FP32 apply).
+ *   m_rtm, m_remig : [2][nz][nx] (host or device; read only)
+ *   spacing s      : node spacing and window half-width, 2 <= s <= 48
+ *   flen           : odd filter length, 1 <= flen <= 11
+ *   eps            : relative Tikhonov weight (>= 0; 1e-3 is typical)
+ *   dm_out         : [2][nz][nx] output (host or device)
+ *   filters        : optional [2][nkz][nkx][flen][flen] output, nk = number
+ *                    of nodes along the axis (NULL to skip)
+ * Errors: LSRTM_ERR_ARG for 3D handles or parameters out of range;
+ * LSRTM_ERR_NONFINITE if a factorisation met a non-positive pivot (those
+ * filters are zero; the other outputs are written). Synchronous. */
+lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_remig, int spacing, int flen,
+                          double eps, float *dm_out, float *filters);
+
 /* Bytes of device workspace the handle holds. */
 size_t lsrtm_workspace_bytes(const lsrtm_handle *h);
 

@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "Geometry", "preset", "PRESETS", "ricker", "gardner_rho",
-    "gaussian_blobs", "small_case",
+    "gaussian_blobs", "small_case", "image_pair",
 ]
 
 
@@ -385,3 +385,35 @@ def small_case(ndim=2, nz=24, nx=30, ny=1, nt=120, order=4, npml=6, nshot=2, see
                     np.concatenate(idx).astype(np.int32))
     return Workload("small", ndim, nz, ny_, nx, dx, dx, dx, dt, nt, order, npml, f0,
                     vp, rho, dm, ricker(nt, dt, f0), geom)
+
+
+def image_pair(nz: int = 300, nx: int = 2000, seed: int = 5, nrefl: int = 40,
+               noise: float = 0.01) -> tuple[np.ndarray, np.ndarray]:
+    """A two-parameter image pair shaped like the marine-line workload's
+    migrated image and its remigration, for the deblurring filters.
+
+    m_rtm: [2, nz, nx] thin dipping reflectors with random amplitudes (the
+    two planes share positions, different amplitudes). m_remig: each plane
+    blurred by a Gaussian whose width grows with depth from 1 to 3 cells
+    (the Hessian's resolution loss with depth), dimmed with depth, plus
+    seeded white noise of relative size `noise`."""
+    rng = np.random.default_rng(seed)
+    zz = np.arange(nz, dtype=np.float64)[:, None]
+    xx = np.arange(nx, dtype=np.float64)[None, :]
+    m = np.zeros((2, nz, nx))
+    for _ in range(nrefl):
+        z0 = rng.uniform(0.05 * nz, 0.95 * nz)
+        dip = rng.uniform(-0.15, 0.15)
+        zl = z0 + dip * (xx - nx / 2)
+        line = np.exp(-0.5 * ((zz - zl) / 0.6) ** 2)
+        amps = rng.uniform(-0.1, 0.1, size=2)
+        m[0] += amps[0] * line
+        m[1] += amps[1] * line
+    depth = zz / max(nz - 1, 1)
+    remig = np.zeros_like(m)
+    for q in range(2):
+        b1 = _smooth(m[q], 1.0)
+        b3 = _smooth(m[q], 3.0)
+        remig[q] = ((1.0 - depth) * b1 + depth * b3) * (1.0 - 0.5 * depth)
+        remig[q] += noise * np.abs(remig[q]).max() * rng.standard_normal((nz, nx))
+    return m, remig

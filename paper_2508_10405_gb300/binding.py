@@ -29,7 +29,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
-           "lsrtm_born_static", "lsrtm_reconstruction"]
+           "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur"]
 
 
 class LsrtmError(RuntimeError):
@@ -97,6 +97,7 @@ def load_library(path: str | None = None):
     L.lsrtm_born_static.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp, vp, vp]
     ip = ctypes.POINTER(ctypes.c_int)
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
+    L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
     L.lsrtm_workspace_bytes.argtypes = [vp]
     L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
     L.lsrtm_kernel_launches.argtypes = [vp]
@@ -252,6 +253,21 @@ class Lsrtm:
         out = self._empty((2,) + self.shape) if out is None else out
         _check(self._lib.lsrtm_remigrate(self._h, _ptr(m), _ptr(out)))
         return out
+
+    def deblur(self, m_rtm, m_remig, spacing=20, flen=11, eps=1e-3, return_filters=False):
+        """Nonstationary deblurring filters (App. E): flen x flen filters per
+        comb node from FP64 normal equations, blended image of m_rtm.
+        Returns dm (and the filters [2, nkz, nkx, flen, flen] on request)."""
+        self._sync_stream()
+        a, b = _f32(m_rtm), _f32(m_remig)
+        out = self._empty((2,) + self.shape)
+        filt = None
+        if return_filters:
+            nk = [len(range(spacing // 2, n, spacing)) for n in self.shape]
+            filt = self._empty((2, nk[0], nk[1], flen, flen))
+        _check(self._lib.lsrtm_deblur(self._h, _ptr(a), _ptr(b), int(spacing), int(flen), float(eps),
+                                      _ptr(out), None if filt is None else _ptr(filt)))
+        return (out, filt) if return_filters else out
 
     def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3):
         """CGNR / PCGNR; returns (dm, misfit history of length niter+1)."""

@@ -1,0 +1,224 @@
+// Nonstationary deblurring filters (App. E) on the GPU.
+//
+// App. E relates the reference image m' and the remigrated image m'' = H m'
+// by a convolution with the inverse of a locally translation-invariant
+// Hessian, f * m'' ~= m'. Per comb node k (spacing s, nodes at s/2 + i s) a
+// flen x flen FIR filter solves, over the window of pixels within s of the
+// node (clipped to the image),
+//     min_f  sum_p ((f * m'')(p) - m'(p))^2 + eps_k ||f||^2,
+//     (f * g)(p) = sum_{|a|,|b|<=h} f[a,b] g(p - (a,b)), g = 0 outside,
+//     eps_k = eps * trace(A^T A) / flen^2,
+// through its FP64 normal equations (A^T A + eps_k I) f = A^T m'. The image
+// delta m = sum_k w_k (f_k * m_rtm) / sum_k w_k blends the filtered blocks with
+// bilinear valence weights w_k(p) = max(0, 1 - |z - z_k|/s) max(0, 1 - |x - x_k|/s).
+//
+// k_deblur_solve: one CTA per (node, parameter plane). The window's patch of
+// m'' (window + h on each side, zero outside the image) sits in shared memory
+// as float; each thread accumulates entries of the upper triangle of A^T A in
+// FP64 (products of two floats are exact in FP64); the matrix, factorised in
+// place by a right-looking Cholesky, and the right-hand side stay in shared
+// memory (121 x 121 doubles = 117 KB for flen = 11).
+// k_deblur_apply: one thread per pixel and plane; FP32 taps, at most four
+// covering nodes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lsrtm_internal.cuh"
+
+namespace lsrtm {
+
+namespace {
+
+constexpr int kSolveThreads = 256;
+
+__global__ void __launch_bounds__(kSolveThreads) k_deblur_solve(const float *mref, const float *mrem, int nz,
+                                                                 int nx, int s, int flen, double eps,
+                                                                 float *filt, int *flag)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = flen * flen, h = flen / 2;
+    const int nkz = gridDim.y, nkx = gridDim.x;
+    const int param = blockIdx.z;
+    const int zk = s / 2 + (int)blockIdx.y * s, xk = s / 2 + (int)blockIdx.x * s;
+    const int z0 = max(0, zk - s), z1 = min(nz, zk + s + 1);
+    const int x0 = max(0, xk - s), x1 = min(nx, xk + s + 1);
+    const int WZ = z1 - z0, WX = x1 - x0;
+    const int PZ = WZ + 2 * h, PX = WX + 2 * h;
+    double *G = reinterpret_cast<double *>(smem);   // [n][n]
+    double *rhs = G + n * n;                        // [n]
+    double *red = rhs + n;                          // [2]: trace, pivot status
+    float *P = reinterpret_cast<float *>(red + 2);  // [PZ][PX]
+    const long long plane = (long long)nz * nx;
+    const float *m2 = mrem + param * plane;
+    const float *m1 = mref + param * plane;
+    const int t = threadIdx.x;
+
+    for (int i = t; i < PZ * PX; i += blockDim.x) {
+        int pz = i / PX, px = i - pz * PX;
+        int z = z0 - h + pz, x = x0 - h + px;
+        P[i] = (z >= 0 && z < nz && x >= 0 && x < nx) ? m2[(long long)z * nx + x] : 0.f;
+    }
+    if (t == 0) {
+        red[0] = 0.0;
+        red[1] = 0.0;
+    }
+    __syncthreads();
+
+    // A[p, u] = m''(p - (a, b)) = P[pz + h - a][px + h - b], u = (a + h) flen + (b + h)
+    for (int e = t; e < n * n; e += blockDim.x) {
+        const int u = e / n, v = e - u * n;
+        if (v < u) continue;
+        const int ozu = 2 * h - u / flen, oxu = 2 * h - u % flen;
+        const int ozv = 2 * h - v / flen, oxv = 2 * h - v % flen;
+        double acc = 0.0;
+        for (int pz = 0; pz < WZ; ++pz) {
+            const float *ru = P + (pz + ozu) * PX + oxu;
+            const float *rv = P + (pz + ozv) * PX + oxv;
+            for (int px = 0; px < WX; ++px) acc = fma((double)ru[px], (double)rv[px], acc);
+        }
+        G[u * n + v] = acc;
+        G[v * n + u] = acc;
+    }
+    for (int u = t; u < n; u += blockDim.x) {
+        const int ozu = 2 * h - u / flen, oxu = 2 * h - u % flen;
+        double acc = 0.0;
+        for (int pz = 0; pz < WZ; ++pz) {
+            const float *ru = P + (pz + ozu) * PX + oxu;
+            const float *r1 = m1 + (long long)(z0 + pz) * nx + x0;
+            for (int px = 0; px < WX; ++px) acc = fma((double)ru[px], (double)r1[px], acc);
+        }
+        rhs[u] = acc;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double tr = 0.0;
+        for (int u = 0; u < n; ++u) tr += G[u * n + u];
+        red[0] = tr;
+    }
+    __syncthreads();
+    const double tr = red[0];
+    float *out = filt + (((long long)param * nkz + blockIdx.y) * nkx + blockIdx.x) * n;
+    if (tr == 0.0) {   // all-zero remigrated window: zero filter
+        for (int u = t; u < n; u += blockDim.x) out[u] = 0.f;
+        return;
+    }
+    const double reg = eps * tr / n;
+    for (int u = t; u < n; u += blockDim.x) G[u * n + u] += reg;
+    __syncthreads();
+
+    // Cholesky G = L L^T, L in the lower triangle
+    for (int k = 0; k < n; ++k) {
+        if (t == 0) {
+            double d = G[k * n + k];
+            if (!(d > 0.0)) {
+                red[1] = 1.0;
+                d = 1.0;
+            }
+            G[k * n + k] = sqrt(d);
+        }
+        __syncthreads();
+        const double dk = G[k * n + k];
+        for (int i = k + 1 + t; i < n; i += blockDim.x) G[i * n + k] /= dk;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = t; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j <= i) G[i * n + j] -= G[i * n + k] * G[j * n + k];
+        }
+        __syncthreads();
+    }
+    // L y = rhs, then L^T f = y (in place in rhs)
+    for (int k = 0; k < n; ++k) {
+        if (t == 0) rhs[k] /= G[k * n + k];
+        __syncthreads();
+        const double yk = rhs[k];
+        for (int i = k + 1 + t; i < n; i += blockDim.x) rhs[i] -= G[i * n + k] * yk;
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        if (t == 0) rhs[k] /= G[k * n + k];
+        __syncthreads();
+        const double fk = rhs[k];
+        for (int i = t; i < k; i += blockDim.x) rhs[i] -= G[k * n + i] * fk;
+        __syncthreads();
+    }
+    const bool bad = red[1] != 0.0;
+    if (bad && t == 0) atomicOr(flag, 1);
+    for (int u = t; u < n; u += blockDim.x) out[u] = bad ? 0.f : (float)rhs[u];
+}
+
+__global__ void k_deblur_apply(const float *mref, const float *filt, int nz, int nx, int s, int flen, int nkz,
+                               int nkx, float *out)
+{
+    const long long plane = (long long)nz * nx;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= plane) return;
+    const int param = blockIdx.y;
+    const int z = (int)(i / nx), x = (int)(i - (long long)(i / nx) * nx);
+    const int n = flen * flen, h = flen / 2;
+    const float *m1 = mref + param * plane;
+    // covering nodes: the nearest node at or above, and the next one, per axis
+    int kz[2], kx[2];
+    float wz[2], wx[2];
+    const int iz = z >= s / 2 ? (z - s / 2) / s : -1, ix = x >= s / 2 ? (x - s / 2) / s : -1;
+    for (int q = 0; q < 2; ++q) {
+        kz[q] = iz + q;
+        kx[q] = ix + q;
+        wz[q] = (kz[q] >= 0 && kz[q] < nkz) ? fmaxf(0.f, 1.f - fabsf((float)(z - (s / 2 + kz[q] * s))) / s) : 0.f;
+        wx[q] = (kx[q] >= 0 && kx[q] < nkx) ? fmaxf(0.f, 1.f - fabsf((float)(x - (s / 2 + kx[q] * s))) / s) : 0.f;
+    }
+    const float *fk[4];
+    float w[4];
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float den = 0.f;
+    for (int q = 0; q < 4; ++q) {
+        const int a = q >> 1, b = q & 1;
+        w[q] = wz[a] * wx[b];
+        fk[q] = w[q] > 0.f ? filt + (((long long)param * nkz + kz[a]) * nkx + kx[b]) * n : nullptr;
+        den += w[q];
+    }
+    for (int a = -h; a <= h; ++a) {
+        const int zz = z - a;
+        if (zz < 0 || zz >= nz) continue;
+        for (int b = -h; b <= h; ++b) {
+            const int xx = x - b;
+            if (xx < 0 || xx >= nx) continue;
+            const float v = m1[(long long)zz * nx + xx];
+            const int u = (a + h) * flen + (b + h);
+            for (int q = 0; q < 4; ++q)
+                if (fk[q]) acc[q] = fmaf(fk[q][u], v, acc[q]);
+        }
+    }
+    float num = 0.f;
+    for (int q = 0; q < 4; ++q) num = fmaf(w[q], acc[q], num);
+    out[param * plane + i] = den > 0.f ? num / den : 0.f;
+}
+
+}  // namespace
+
+size_t deblur_solve_smem(int nz, int nx, int s, int flen)
+{
+    const int n = flen * flen, h = flen / 2;
+    const int wz = std::min(nz, 2 * s + 1), wx = std::min(nx, 2 * s + 1);
+    return ((size_t)n * n + n + 2) * sizeof(double) + (size_t)(wz + 2 * h) * (wx + 2 * h) * sizeof(float);
+}
+
+int deblur_nodes(int n, int s) { return n > s / 2 ? (n - 1 - s / 2) / s + 1 : 0; }
+
+cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, int s, int flen, double eps,
+                          float *filt, float *out, int *flag, cudaStream_t st)
+{
+    const int nkz = deblur_nodes(nz, s), nkx = deblur_nodes(nx, s);
+    const size_t sm = deblur_solve_smem(nz, nx, s, flen);
+    cudaError_t e = cudaFuncSetAttribute(k_deblur_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_deblur_solve<<<dim3(nkx, nkz, 2), kSolveThreads, sm, st>>>(mref, mrem, nz, nx, s, flen, eps, filt, flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long plane = (long long)nz * nx;
+    k_deblur_apply<<<dim3((unsigned)((plane + 255) / 256), 2), 256, 0, st>>>(mref, filt, nz, nx, s, flen, nkz, nkx,
+                                                                              out);
+    return cudaGetLastError();
+}
+
+}  // namespace lsrtm

@@ -112,6 +112,9 @@ struct lsrtm_handle {
     float *mstage = nullptr;     // [2][nint]
     float *gstage = nullptr;     // [2][nint]
     float *scratch1 = nullptr;   // [nint]
+    float *db_filt = nullptr;    // deblurring filters, grown on demand
+    size_t db_cap = 0;
+    float *db_out = nullptr;     // [2][nint]
     // Krylov
     float *cg_x = nullptr, *cg_s = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_minv = nullptr;
     float *cg_r = nullptr;
@@ -1459,6 +1462,43 @@ lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream)
 {
     if (!h) return fail(LSRTM_ERR_ARG, "null handle");
     h->user = (cudaStream_t)stream;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_remig, int spacing, int flen,
+                          double eps, float *dm_out, float *filters)
+{
+    if (!h || !m_rtm || !m_remig || !dm_out) return fail(LSRTM_ERR_ARG, "null argument");
+    if (h->g.ndim != 2) return fail(LSRTM_ERR_ARG, "lsrtm_deblur supports 2D images only");
+    if (flen < 1 || flen > 11 || flen % 2 == 0) return fail(LSRTM_ERR_ARG, "flen must be odd and in [1, 11]");
+    if (spacing < 2 || spacing > 48) return fail(LSRTM_ERR_ARG, "spacing must be in [2, 48]");
+    if (!(eps >= 0.0)) return fail(LSRTM_ERR_ARG, "eps must be >= 0");
+    const int nz = h->g.nz, nx = h->g.nx;
+    if (nz <= spacing / 2 || nx <= spacing / 2)
+        return fail(LSRTM_ERR_ARG, "image smaller than half the node spacing: no deblurring node");
+    const int nkz = deblur_nodes(nz, spacing), nkx = deblur_nodes(nx, spacing);
+    const size_t nf = 2 * (size_t)nkz * nkx * flen * flen;
+    CHECK(begin_call(h));
+    if (nf > h->db_cap) {
+        CHECK(dalloc_t(h, &h->db_filt, nf));
+        h->db_cap = nf;
+    }
+    if (!h->db_out) CHECK(dalloc_t(h, &h->db_out, 2 * (size_t)h->nint));
+    const float *a, *b;
+    CHECK(stage_in(h, m_rtm, h->mstage, 2 * h->nint, &a));
+    CHECK(stage_in(h, m_remig, h->gstage, 2 * h->nint, &b));
+    CU(cudaMemsetAsync(h->flag, 0, sizeof(int), h->work));
+    const bool odev = is_device_ptr(dm_out);
+    float *od = odev ? dm_out : h->db_out;
+    CU(launch_deblur(a, b, nz, nx, spacing, flen, eps, h->db_filt, od, h->flag, h->work));
+    h->launches += 2;
+    if (!odev) CHECK(copy_out(h, dm_out, od, 2 * h->nint));
+    if (filters) CHECK(copy_out(h, filters, h->db_filt, nf));
+    int flag = 0;
+    CU(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+    CHECK(end_call(h, true));
+    if (flag) return fail(LSRTM_ERR_NONFINITE, "deblurring normal equations not positive definite (eps too small "
+                                              "or non-finite images); those filters are set to zero");
     return LSRTM_OK;
 }
 

@@ -131,6 +131,15 @@ cudaError_t configure_2d_kernels();
 cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int shot0, int batch,
                                 float *st, long long sstride, cudaStream_t s);
 
+// Nonstationary deblurring filters (deblur.cu): per comb node of spacing s a
+// flen x flen filter from FP64 normal equations over the node's window of
+// the [2][nz][nx] images, then the valence-weighted filtered image.
+// filt: [2][nkz][nkx][flen*flen]; flag |= 1 where a factorisation failed.
+int deblur_nodes(int n, int s);
+size_t deblur_solve_smem(int nz, int nx, int s, int flen);
+cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, int s, int flen, double eps,
+                          float *filt, float *out, int *flag, cudaStream_t st);
+
 // Utility kernels (kernels_util.cu).
 cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
                               float *binv, cudaStream_t s);
