@@ -163,6 +163,9 @@ def model(w, vp=None, rho=None, geom=None, wavelet=None, nt=None, vmax=None,
 
 def born(w, dm, vp=None, rho=None, geom=None, nt=None, vmax=None) -> np.ndarray:
     """d = L dm; dm [2, *shape] = (dln Vp, dln Ip); d [nrec_total, nt]."""
+    geom = w.geom if geom is None else geom
+    if windowed(geom):
+        return _born_windowed(w, dm, vp, rho, geom, nt, vmax)
     a = _Args(w, vp, rho, geom, None, nt, vmax)
     dm = _f64(dm).reshape(2, -1)
     d = np.zeros((a.geom.nrec_total, a.nt))
@@ -173,6 +176,11 @@ def born(w, dm, vp=None, rho=None, geom=None, nt=None, vmax=None) -> np.ndarray:
 def adjoint(w, d, vp=None, rho=None, geom=None, nt=None, vmax=None, raw=False):
     """g = L^T d as [2, *shape] (dln Vp, dln Ip). With raw=True also returns
     (g_kappa, g_rho) before the chain rule."""
+    geom = w.geom if geom is None else geom
+    if windowed(geom):
+        if raw:
+            raise ValueError("raw images are not provided for windowed geometries")
+        return _adjoint_windowed(w, d, vp, rho, geom, nt, vmax)
     a = _Args(w, vp, rho, geom, None, nt, vmax)
     d = _f64(d).reshape(a.geom.nrec_total, a.nt)
     g = np.zeros((2, w.nint))
@@ -184,10 +192,79 @@ def adjoint(w, d, vp=None, rho=None, geom=None, nt=None, vmax=None, raw=False):
     return g.reshape(shape)
 
 
+# ---------------------------------------------------------------------------
+# Per-shot aperture windows. A shot with window [x0, x0 + nx_w) of interior
+# columns is modelled on the sub-model vp[..., x0:x0+nx_w] (and rho, dm),
+# padded with CPML and edge replication of that sub-model exactly as a full
+# model is; its records are that sub-problem's records and its image is added
+# into the window's columns. The CPML damping keeps the full model's
+# maximum velocity. Source and receivers must lie inside the window.
+
+
+def windowed(geom) -> bool:
+    return geom is not None and getattr(geom, "win_x0", None) is not None
+
+
+def _window_case(w, geom, s, vp, rho, vmax):
+    import dataclasses
+    x0 = int(geom.win_x0[s])
+    nxw = int(geom.win_nx[s])
+    if x0 < 0 or nxw < 1 or x0 + nxw > w.nx:
+        raise ValueError(f"shot {s}: window outside the model")
+    vp = w.vp if vp is None else vp
+    rho = w.rho if rho is None else rho
+
+    def local(k):
+        k = np.asarray(k, np.int64)
+        ix = k % w.nx
+        rest = k // w.nx
+        if np.any(ix < x0) or np.any(ix >= x0 + nxw):
+            raise ValueError(f"shot {s}: source or receiver outside its window")
+        return (rest * nxw + (ix - x0)).astype(np.int32)
+
+    r = geom.rec_idx[geom.rec_ptr[s]:geom.rec_ptr[s + 1]]
+    g1 = type(geom)(src_idx=local([geom.src_idx[s]]), rec_ptr=np.array([0, r.size], np.int32),
+                    rec_idx=local(r))
+    wav = w.wavelet if np.ndim(w.wavelet) == 1 else np.asarray(w.wavelet)[s]
+    sub = dataclasses.replace(w, nx=nxw, vp=np.ascontiguousarray(vp[..., x0:x0 + nxw]),
+                              rho=np.ascontiguousarray(rho[..., x0:x0 + nxw]),
+                              dm=None, wavelet=wav, geom=g1)
+    vmax = float(np.max(vp)) if vmax is None else vmax
+    return sub, x0, nxw, vmax
+
+
+def _born_windowed(w, dm, vp, rho, geom, nt, vmax):
+    dm = _f64(dm).reshape((2,) + tuple(w.shape))
+    ntt = int(w.nt if nt is None else nt)
+    d = np.zeros((geom.nrec_total, ntt))
+    for s in range(geom.nshot):
+        sub, x0, nxw, vm = _window_case(w, geom, s, vp, rho, vmax)
+        d[geom.rec_ptr[s]:geom.rec_ptr[s + 1]] = born(
+            sub, np.ascontiguousarray(dm[..., x0:x0 + nxw]), nt=nt, vmax=vm)
+    return d
+
+
+def _adjoint_windowed(w, d, vp, rho, geom, nt, vmax):
+    ntt = int(w.nt if nt is None else nt)
+    d = _f64(d).reshape(geom.nrec_total, ntt)
+    g = np.zeros((2,) + tuple(w.shape))
+    for s in range(geom.nshot):
+        sub, x0, nxw, vm = _window_case(w, geom, s, vp, rho, vmax)
+        g[..., x0:x0 + nxw] += adjoint(sub, d[geom.rec_ptr[s]:geom.rec_ptr[s + 1]], nt=nt, vmax=vm)
+    return g
+
+
 def pseudo_hessian(w, vp=None, rho=None, geom=None, nt=None, vmax=None,
                    src_ptr=None, src_idx=None) -> np.ndarray:
     """Pseudo-Hessian diagonal (App. B), interior shape; serves both planes.
     A custom source list (CSR) may replace the one-source geometry."""
+    g0 = w.geom if geom is None else geom
+    if src_ptr is None and windowed(g0):
+        h = np.zeros(tuple(w.shape))
+        for s in range(g0.nshot):
+            sub, x0, nxw, vm = _window_case(w, g0, s, vp, rho, vmax)
+            h[..., x0:x0 + nxw] += pseudo_hessian(sub, nt=nt, vmax=vm)
+        return h
     a = _Args(w, vp, rho, geom, None, nt, vmax)
     h = np.zeros(w.nint)
     args = list(a.common()[:8])
