@@ -87,6 +87,16 @@ typedef struct {
     const int *src_idx;  /* host [nshot]: flat interior index of each shot's source */
     const int *rec_ptr;  /* host [nshot+1]: CSR offsets into rec_idx */
     const int *rec_idx;  /* host [rec_ptr[nshot]]: flat interior receiver indices */
+    /* Optional per-shot aperture windows (2D, boundary-band reconstruction;
+     * both NULL = every shot spans the model). Shot s is modelled on the
+     * sub-model of interior columns [win_x0[s], win_x0[s] + win_nx[s]) with
+     * its own CPML and edge replication of that sub-model; its source and
+     * receivers must lie inside it, its records are that sub-problem's and
+     * its image is added into those columns. The CPML damping uses the
+     * configuration's pml_vmax for every shot. Shots of different window
+     * widths advance in the same launches. */
+    const int *win_x0;   /* host [nshot] first interior column, or NULL */
+    const int *win_nx;   /* host [nshot] window width in columns, or NULL */
 } lsrtm_geometry;
 
 typedef struct lsrtm_handle lsrtm_handle;

@@ -63,7 +63,8 @@ class Timings(ctypes.Structure):
 
 class GeometryC(ctypes.Structure):
     _fields_ = [("nshot", ctypes.c_int), ("src_idx", ctypes.POINTER(ctypes.c_int)),
-                ("rec_ptr", ctypes.POINTER(ctypes.c_int)), ("rec_idx", ctypes.POINTER(ctypes.c_int))]
+                ("rec_ptr", ctypes.POINTER(ctypes.c_int)), ("rec_idx", ctypes.POINTER(ctypes.c_int)),
+                ("win_x0", ctypes.POINTER(ctypes.c_int)), ("win_nx", ctypes.POINTER(ctypes.c_int))]
 
 
 _LIB = None
@@ -148,7 +149,7 @@ class Lsrtm:
     (default: torch's current stream)."""
 
     def __init__(self, *, ndim, nz, nx, ny=1, dz, dx, dy=None, dt, nt, fd_order, npml, f0,
-                 vp, rho, wavelet, src_idx, rec_ptr, rec_idx, pml_vmax=None,
+                 vp, rho, wavelet, src_idx, rec_ptr, rec_idx, win_x0=None, win_nx=None, pml_vmax=None,
                  band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_AUTO,
                  plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, stream=None):
         import torch
@@ -167,8 +168,12 @@ class Lsrtm:
         self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
         self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)
         ip = ctypes.POINTER(ctypes.c_int)
+        self._wx0 = None if win_x0 is None else np.ascontiguousarray(win_x0, dtype=np.int32)
+        self._wnx = None if win_nx is None else np.ascontiguousarray(win_nx, dtype=np.int32)
         geo = GeometryC(len(self._src), self._src.ctypes.data_as(ip), self._rp.ctypes.data_as(ip),
-                        self._ri.ctypes.data_as(ip))
+                        self._ri.ctypes.data_as(ip),
+                        None if self._wx0 is None else self._wx0.ctypes.data_as(ip),
+                        None if self._wnx is None else self._wnx.ctypes.data_as(ip))
         self.nshot = len(self._src)
         self.nrec_total = int(self._rp[-1])
         self.nt = nt
@@ -194,7 +199,8 @@ class Lsrtm:
         return cls(ndim=w.ndim, nz=w.nz, ny=w.ny, nx=w.nx, dz=w.dz, dy=w.dy, dx=w.dx, dt=w.dt,
                    nt=w.nt, fd_order=w.order, npml=w.npml, f0=w.f0, vp=w.vp, rho=w.rho,
                    wavelet=w.wavelet, src_idx=w.geom.src_idx, rec_ptr=w.geom.rec_ptr,
-                   rec_idx=w.geom.rec_idx, **kw)
+                   rec_idx=w.geom.rec_idx, win_x0=getattr(w.geom, "win_x0", None),
+                   win_nx=getattr(w.geom, "win_nx", None), **kw)
 
     # -- helpers
     def _empty(self, shape):

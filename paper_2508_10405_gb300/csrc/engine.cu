@@ -60,7 +60,12 @@ enum GraphKind { G_BORN = 0, G_BG = 1, G_BG_HESS = 2, G_ADJ = 3 };
 
 struct lsrtm_handle {
     lsrtm_config cfg{};
-    GridDev g{};
+    GridDev g{};                 // grid of the wavefield slots (the widest aperture window)
+    GridDev gm{};                // grid of the model and the images
+    // per-shot aperture windows (2D)
+    bool win = false;
+    int *win_x0_d = nullptr, *win_nx_d = nullptr;
+    std::vector<int> win_x0_h, win_nx_h;
     cudaStream_t user = nullptr;
     cudaStream_t work = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -288,6 +293,8 @@ Step2D step_args(lsrtm_handle *h, int shot0)
     a.hess = h->hess;
     a.img = h->img;
     a.tzc = h->tzc;
+    a.win_nx = h->win ? h->win_nx_d : nullptr;
+    a.pml_xstride = h->win ? h->g.Nx : 0;
     return a;
 }
 
@@ -358,7 +365,27 @@ lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs,
 template <class F>
 lsrtm_status run_loop(lsrtm_handle *h, int kind, int shot0, int bs, F &&body)
 {
-    return run_loop_n(h, kind, timing_kind(kind), shot0, bs, loop_launches(h, kind), h->g.nt, body);
+    return run_loop_n(h, kind, timing_kind(kind), shot0, bs, loop_launches(h, kind) + (h->win ? 1 : 0), h->g.nt,
+                      body);
+}
+
+// Padded cells one time step of a batch advances (each windowed shot on its own grid).
+double batch_cells(const lsrtm_handle *h, int shot0, int bs)
+{
+    if (!h->win) return (double)bs * h->g.Nz * h->g.Ny * h->g.Nx;
+    double c = 0.0;
+    for (int s = shot0; s < shot0 + bs; ++s) c += (double)h->g.Nz * (h->win_nx_h[s] + 2 * h->g.x0);
+    return c;
+}
+
+// Copies each windowed shot's model into its slots (a no-op without windows).
+lsrtm_status gather_model(lsrtm_handle *h, int shot0, int bs, bool born)
+{
+    if (!h->win) return LSRTM_OK;
+    CU(launch_window_model(h->gm, h->g, h->win_x0_d, h->win_nx_d, shot0, bs, h->kdt, h->binv,
+                           born ? h->kd2 : nullptr, born ? h->br2 : nullptr, h->st[0], h->st[1], h->sstride,
+                           h->work));
+    return LSRTM_OK;
 }
 
 // Runs `body` (kernel launches of one loop over a batch), captured once into a
@@ -403,7 +430,7 @@ lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs,
     h->launches += nlaunch;
     if (h->timing && ea && eb) {
         CU(cudaEventRecord(eb, h->work));
-        double cells = (double)bs * h->g.Nz * h->g.Ny * h->g.Nx * (double)nsteps;
+        double cells = batch_cells(h, shot0, bs) * (double)nsteps;
         h->pending.push_back({tkind, ea, eb, nlaunch, cells});
     } else {
         if (ea) h->event_pool.push_back(ea);
@@ -459,6 +486,7 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                                    cudaMemcpyDeviceToDevice, h->work));
         } else {
             CHECK(run_loop(h, hess ? G_BG_HESS : G_BG, s0, bs, [&]() -> lsrtm_status {
+                CHECK(gather_model(h, s0, bs, false));
                 Step2D a = step_args(h, s0);
                 for (int n = 0; n < nt; ++n) {
                     a.n = n;
@@ -480,12 +508,13 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
             }
         }
         if (hess) {
-            CU(launch_hess_accumulate(h->g, h->hess, bs, h->hess_acc, h->work));
+            CU(launch_hess_accumulate(h->gm, h->g, h->hess, bs, s0, h->win ? h->win_x0_d : nullptr, h->win_nx_d,
+                                      h->hess_acc, h->work));
             h->launches++;
         }
     }
     if (hess) {
-        CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+        CU(launch_hess_finalize(h->gm, h->hess_acc, h->hess_img, h->work));
         h->launches++;
         h->hess_ready = true;
     }
@@ -510,6 +539,7 @@ lsrtm_status born_core(lsrtm_handle *h)
                 }
                 return LSRTM_OK;
             }
+            CHECK(gather_model(h, s0, bs, true));
             Step2D a = step_args(h, s0);
             for (int n = 0; n < nt; ++n) {
                 a.n = n;
@@ -603,7 +633,7 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
                              h->work));
     }
     if (hess) {
-        CU(launch_hess_accumulate(h->g, h->hess, bs, h->hess_acc, h->work));
+        CU(launch_hess_accumulate(h->gm, h->g, h->hess, bs, s0, nullptr, nullptr, h->hess_acc, h->work));
         h->launches++;
     }
     return LSRTM_OK;
@@ -700,7 +730,7 @@ lsrtm_status ck_hessian(lsrtm_handle *h)
 {
     CU(cudaMemsetAsync(h->hess_acc, 0, h->nint * sizeof(double), h->work));
     for (int s0 = 0; s0 < h->nshot; s0 += h->batch) CHECK(ck_forward(h, s0, batch_size(h, s0), true));
-    CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+    CU(launch_hess_finalize(h->gm, h->hess_acc, h->hess_img, h->work));
     h->launches++;
     h->hess_ready = true;
     return LSRTM_OK;
@@ -737,15 +767,15 @@ lsrtm_status adjoint_core_ckpt(lsrtm_handle *h, float *gout, bool want_hess)
         if (is3d(h))
             CU(launch_image_accumulate3d(h->g, h->st[0], h->sstride, bs, h->img_acc, h->work));
         else
-            CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
+            CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, nullptr, nullptr, h->img_acc, h->work));
         h->launches++;
     }
     if (hess) {
-        CU(launch_hess_finalize(h->g, h->hess_acc, h->hess_img, h->work));
+        CU(launch_hess_finalize(h->gm, h->hess_acc, h->hess_img, h->work));
         h->launches++;
         h->hess_ready = true;
     }
-    CU(launch_image_finalize(h->g, h->img_acc, h->kdt, h->binv, gout, h->work));
+    CU(launch_image_finalize(h->gm, h->img_acc, h->kdt, h->binv, gout, h->work));
     h->launches++;
     return LSRTM_OK;
 }
@@ -785,6 +815,7 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
                                       reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
             h->launches += 2;
             CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
+                CHECK(gather_model(h, s0, bs, false));
                 Step2D a = step_args(h, s0);
                 for (int i = 0; i < nt; ++i) {
                     a.n = nt - 1 - i;
@@ -794,18 +825,19 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
                 }
                 return LSRTM_OK;
             }));
-            CU(launch_image_accumulate(h->g, h->img, bs, h->img_acc, h->work));
+            CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, h->win ? h->win_x0_d : nullptr, h->win_nx_d,
+                                       h->img_acc, h->work));
             h->launches++;
         }
     }
-    CU(launch_image_finalize(h->g, h->img_acc, h->kdt, h->binv, gout, h->work));
+    CU(launch_image_finalize(h->gm, h->img_acc, h->kdt, h->binv, gout, h->work));
     h->launches++;
     return LSRTM_OK;
 }
 
 lsrtm_status prep_perturbation(lsrtm_handle *h, const float *dm_dev)
 {
-    CU(launch_pert_prep(h->g, dm_dev, h->kdt, h->binv, h->kd2, h->br2, h->work));
+    CU(launch_pert_prep(h->gm, dm_dev, h->kdt, h->binv, h->kd2, h->br2, h->work));
     h->launches++;
     return LSRTM_OK;
 }
@@ -854,15 +886,23 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         if (geo->rec_ptr[s + 1] < geo->rec_ptr[s]) return fail(LSRTM_ERR_GEOMETRY, "rec_ptr not monotone");
     h->nrec_total = geo->rec_ptr[h->nshot];
     h->rec_ptr.assign(geo->rec_ptr, geo->rec_ptr + h->nshot + 1);
-    auto pad_cell = [&](long long k) {
-        long long ix = k % g.nx, t = k / g.nx, iy = t % g.ny, iz = t / g.ny;
+    const GridDev &gm = h->gm;
+    // cell of interior point k in shot s's slot grid (its window), or -1 outside the window
+    auto pad_cell = [&](long long k, int s) -> long long {
+        long long ix = k % gm.nx, t = k / gm.nx, iy = t % gm.ny, iz = t / gm.ny;
+        if (h->win) {
+            ix -= h->win_x0_h[s];
+            if (ix < 0 || ix >= h->win_nx_h[s]) return -1;
+        }
         return (iz + g.z0) * g.rowz + (iy + g.y0) * g.pitch + (ix + g.x0);
     };
     std::vector<int> src(h->nshot);
     for (int s = 0; s < h->nshot; ++s) {
         long long k = geo->src_idx[s];
         if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "source outside the interior grid");
-        src[s] = (int)pad_cell(k);
+        long long c = pad_cell(k, s);
+        if (c < 0) return fail(LSRTM_ERR_GEOMETRY, "source outside its shot's aperture window");
+        src[s] = (int)c;
     }
     if (g.ndim == 3) {
         // per shot: receivers sorted by cell, and a node map to the first receiver at each node
@@ -874,7 +914,7 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
             for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
                 long long k = geo->rec_idx[r];
                 if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
-                L.emplace_back(pad_cell(k), r);
+                L.emplace_back(pad_cell(k, s), r);
             }
             std::stable_sort(L.begin(), L.end(),
                              [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) {
@@ -911,7 +951,8 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
             long long k = geo->rec_idx[r];
             if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
-            long long cell = pad_cell(k);
+            long long cell = pad_cell(k, s);
+            if (cell < 0) return fail(LSRTM_ERR_GEOMETRY, "receiver outside its shot's aperture window");
             int z = (int)(cell / g.rowz), x = (int)(cell % g.pitch);
             int t = (z / h->tzc) * ntx + x / h->txo;
             lists[(size_t)s * ntiles + t].push_back(make_int2((int)cell, r));
@@ -936,6 +977,38 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
     h->trv.ptr = h->trec_ptr;
     h->trv.rec = h->trec;
     h->trv.ntiles = ntiles;
+    return LSRTM_OK;
+}
+
+// Aperture windows: validates them, keeps host and device copies and turns
+// h->g into the slot grid of the widest window (h->gm stays the model grid).
+lsrtm_status setup_windows(lsrtm_handle *h, const lsrtm_geometry *geo)
+{
+    if (!geo || (!geo->win_x0 && !geo->win_nx)) return LSRTM_OK;
+    if (!geo->win_x0 || !geo->win_nx) return fail(LSRTM_ERR_ARG, "win_x0 and win_nx must both be given or both NULL");
+    if (h->g.ndim != 2) return fail(LSRTM_ERR_ARG, "aperture windows are supported in 2D only");
+    if (geo->nshot < 1) return fail(LSRTM_ERR_ARG, "invalid geometry");
+    h->win_x0_h.assign(geo->win_x0, geo->win_x0 + geo->nshot);
+    h->win_nx_h.assign(geo->win_nx, geo->win_nx + geo->nshot);
+    int wmax = 0;
+    for (int s = 0; s < geo->nshot; ++s) {
+        int x0 = h->win_x0_h[s], nx = h->win_nx_h[s];
+        if (x0 < 0 || nx < 1 || (long long)x0 + nx > h->gm.nx)
+            return fail(LSRTM_ERR_GEOMETRY, "aperture window outside the model");
+        wmax = std::max(wmax, nx);
+    }
+    h->win = true;
+    GridDev &g = h->g;
+    g.nx = wmax;
+    g.Nx = wmax + 2 * g.x0;
+    g.pitch = (g.Nx + 31) / 32 * 32;
+    g.rowz = (long long)g.Ny * g.pitch;
+    g.plane = (long long)g.Nz * g.rowz;
+    CHECK(dalloc_t(h, &h->win_x0_d, geo->nshot));
+    CHECK(dalloc_t(h, &h->win_nx_d, geo->nshot));
+    CU(cudaMemcpyAsync(h->win_x0_d, h->win_x0_h.data(), geo->nshot * sizeof(int), cudaMemcpyHostToDevice, h->work));
+    CU(cudaMemcpyAsync(h->win_nx_d, h->win_nx_h.data(), geo->nshot * sizeof(int), cudaMemcpyHostToDevice, h->work));
+    CU(cudaStreamSynchronize(h->work));
     return LSRTM_OK;
 }
 
@@ -1026,6 +1099,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     CHECK(dalloc_t(h, &h->br2, g.plane));
     CU(launch_model_prep(g, vp_d, rho_d, h->kdt, h->binv, h->work));
     h->launches++;
+    h->gm = g;
+    CHECK(setup_windows(h, geo));
 
     // CPML profiles: per direction ai bi ah bh
     {
@@ -1050,6 +1125,25 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         }
         CU(cudaMemcpyAsync(h->pml_buf, prof.data(), tot * sizeof(float), cudaMemcpyHostToDevice, h->work));
         CU(cudaStreamSynchronize(h->work));
+    }
+    if (h->win) {
+        // x profiles of every shot's own window: [4][nshot][Nx] (ai, bi, ah, bh)
+        const int nwin = (int)h->win_nx_h.size();
+        const size_t stride = (size_t)g.Nx, per = (size_t)nwin * stride;
+        std::vector<float> prof(4 * per, 0.f);
+        for (int s = 0; s < nwin; ++s) {
+            float *b = prof.data() + (size_t)s * stride;
+            cpml_profile(h->win_nx_h[s] + 2 * g.x0, g.x0, h->win_nx_h[s], cfg->npml, cfg->dx, vmax, cfg->f0,
+                         cfg->dt, b, b + per, b + 2 * per, b + 3 * per);
+        }
+        float *px;
+        CHECK(dalloc_t(h, &px, 4 * per));
+        CU(cudaMemcpyAsync(px, prof.data(), 4 * per * sizeof(float), cudaMemcpyHostToDevice, h->work));
+        CU(cudaStreamSynchronize(h->work));
+        h->pml.ai[2] = px;
+        h->pml.bi[2] = px + per;
+        h->pml.ah[2] = px + 2 * per;
+        h->pml.bh[2] = px + 3 * per;
     }
 
     CHECK(build_geometry(h, geo));
@@ -1087,7 +1181,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     // wavefield slots
     // 2D: ping-pong state + in-place node CPML planes + image plane; 3D: one in-place state
     // of 20 planes (pairs, CPML memories, images) + the pseudo-Hessian plane
-    h->sstride = (d3 ? kStatePlanes3D : kStatePlanes2D) * g.plane;
+    h->sstride = (d3 ? kStatePlanes3D : (h->win ? kWinStatePlanes2D : kStatePlanes2D)) * g.plane;
     h->vstride = d3 ? 0 : kPsivPlanes2D * g.plane;
     size_t per_slot = d3 ? ((size_t)h->sstride + g.plane) * sizeof(float)
                          : (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
@@ -1105,7 +1199,9 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     const size_t band_full = 2 * (size_t)h->nshot * g.nt * h->bands.nb * esz;
     const size_t fs_full = (size_t)h->nshot * h->fs_planes * fbytes;
     bool ckpt = cfg->recon_mode == LSRTM_RECON_CHECKPOINT;
-    if (cfg->recon_mode == LSRTM_RECON_AUTO) ckpt = (long long)(band_full + fs_full + per_slot) > avail;
+    if (cfg->recon_mode == LSRTM_RECON_AUTO) ckpt = !h->win && (long long)(band_full + fs_full + per_slot) > avail;
+    if (ckpt && h->win)
+        return fail(LSRTM_ERR_ARG, "checkpoint reconstruction does not support aperture windows");
     h->ckpt = ckpt;
     if (!ckpt) {
         CHECK(dalloc(h, &h->band_mem, band_full));
@@ -1260,7 +1356,7 @@ lsrtm_status lsrtm_psf(lsrtm_handle *h, int param, int spacing, float *psf)
     if (param != 0 && param != 1) return fail(LSRTM_ERR_ARG, "param must be 0 (Vp) or 1 (Ip)");
     if (spacing < 1) return fail(LSRTM_ERR_ARG, "spacing must be >= 1");
     CHECK(begin_call(h));
-    CU(launch_comb(h->g, param, spacing, h->mstage, h->work));
+    CU(launch_comb(h->gm, param, spacing, h->mstage, h->work));
     h->launches++;
     CHECK(prep_perturbation(h, h->mstage));
     CHECK(born_core(h));

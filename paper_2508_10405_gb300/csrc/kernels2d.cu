@@ -38,6 +38,10 @@ enum { G_P = 0, G_VX = 1, G_VZ = 2, G_PPX = 3, G_PPZ = 4 };
 enum { G_PVX = 0, G_PVZ = 1 };
 // Adjoint: float2 pairs (background, lambda) and float lambda CPML memories.
 enum { A_PL = 0, A_VX = 2, A_VZ = 4, A_LPPX = 6, A_LPPZ = 7, A_LPVX = 8, A_LPVZ = 9 };
+// Slots of aperture-windowed shots carry the window's own model after the
+// state: dt kappa and 1/rho (float planes), and the Born pairs (float2).
+enum { W_KDT = 10, W_BINV = 11, W_KD2 = 12, W_BR2 = 14 };
+static_assert(W_BR2 + 2 == kWinStatePlanes2D, "window slot layout");
 
 // ---- packed arithmetic for T = float or float2
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -171,7 +175,7 @@ struct FwdRow {
     K kd;     // dt kappa (, dt kappa dlnk) at row z
 };
 
-template <int M, bool BORN>
+template <int M, bool BORN, bool WIN>
 __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float *in, int xc, int z,
                                           int zc0, int zc1, bool colok, bool vxok, bool outcol,
                                           bool pmlxh)
@@ -184,8 +188,10 @@ __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float
     const int W = 2 * M;
     char *sl = st + threadIdx.x * 8;
     const T *fin = reinterpret_cast<const T *>(in);
-    const R *br = BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv);
-    const K *kk = BORN ? reinterpret_cast<const K *>(a.kd2) : reinterpret_cast<const K *>(a.kdt);
+    const R *br = WIN ? reinterpret_cast<const R *>(in + (BORN ? W_BR2 : W_BINV) * g.plane)
+                      : (BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv));
+    const K *kk = WIN ? reinterpret_cast<const K *>(in + (BORN ? W_KD2 : W_KDT) * g.plane)
+                      : (BORN ? reinterpret_cast<const K *>(a.kd2) : reinterpret_cast<const K *>(a.kdt));
     const long long pT = g.plane;   // cells per plane: the stride of one (pair) field in units of T
     const int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
     const int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
@@ -233,7 +239,7 @@ __device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
     return r;
 }
 
-template <int M, bool BORN, bool BANDS, bool HESS>
+template <int M, bool BORN, bool BANDS, bool HESS, bool WIN>
 __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
 {
     using C = Cols<M>;
@@ -248,14 +254,18 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
 
     const GridDev &g = a.g;
     const int t = threadIdx.x;
+    const int slot = blockIdx.z, shot = a.shot0 + slot;
+    // padded and interior widths of this shot's grid (its aperture window)
+    const int Nx = WIN ? a.win_nx[shot] + 2 * g.x0 : g.Nx;
+    const int nx = WIN ? Nx - 2 * g.x0 : g.nx;
+    if (WIN && (int)blockIdx.x * TXO >= Nx) return;   // no output column in this shot's window
     const int x = (int)blockIdx.x * TXO - HXP + t;
-    const bool colok = x >= 0 && x < g.Nx;
+    const bool colok = x >= 0 && x < Nx;
     const bool outcol = colok && t >= HXP && t < HXP + TXO;
     const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
     const int zc0 = (int)blockIdx.y * a.tzc;
     const int zc1 = min(zc0 + a.tzc, g.Nz);
     const int zstart = zc0 - W;
-    const int slot = blockIdx.z, shot = a.shot0 + slot;
     const long long plane = g.plane;
     const long long pT = plane;   // cells per plane: the stride of one (pair) field in units of T
     const int pitch = g.pitch;
@@ -264,12 +274,13 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
     T *out = reinterpret_cast<T *>(a.out + slot * a.sstride) + xc;
     T *psiv = reinterpret_cast<T *>(a.psiv + slot * a.vstride) + xc;
     const float dt = g.dt;
-    const int x0 = g.x0, x1 = g.x0 + g.nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const int x0 = g.x0, x1 = g.x0 + nx, z0 = g.z0, z1 = g.z0 + g.nz;
     const int ix = x - x0;
     const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
     const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
-    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
-    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
+    const int px = WIN ? shot * a.pml_xstride + x : x;   // x CPML profiles of this shot's window
+    const float ahx = pmlxh ? a.pml.ah[2][px] : 0.f, bhx = pmlxh ? a.pml.bh[2][px] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][px] : 0.f, bix = pmlxn ? a.pml.bi[2][px] : 0.f;
     const long long bandoff = band_base(a.bands, shot, a.n);
     const int src = a.src_cell[shot];
     const float wsrc = a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + a.n];
@@ -295,7 +306,8 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
     }
     R br_old = zero_<R>();
     {
-        const R *br = BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv);
+        const R *br = WIN ? reinterpret_cast<const R *>(in + (BORN ? W_BR2 : W_BINV) * plane)
+                          : (BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv));
         int k = zstart + M - 1;
         if (colok && k >= 0 && k < g.Nz) br_old = br[(long long)k * pitch + xc];
     }
@@ -303,7 +315,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
 #pragma unroll
     for (int j = 0; j < PD - 1; ++j) {
         if (zstart + j < zc1)
-            fwd_issue<M, BORN>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
+            fwd_issue<M, BORN, WIN>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
                                outcol, pmlxh);
         cp_commit();
     }
@@ -315,7 +327,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
             if (z >= zc1) break;
             const int zi = z + PD - 1;
             if (zi < zc1)
-                fwd_issue<M, BORN>(stages + ((zi - zstart) % PD) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
+                fwd_issue<M, BORN, WIN>(stages + ((zi - zstart) % PD) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
                                    colok, vxok, outcol, pmlxh);
             cp_commit();
             cp_wait_row();
@@ -346,8 +358,8 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                     out[oVZ * pT + ck] = vzn;
                     if (BANDS) {
                         int iz = k - z0;
-                        if (ix >= 0 && ix < g.nx && in_xstrip(iz, M, g.nz))
-                            band_put(a.bands, a.bands.v, bandoff + band_zstrip(iz, ix, M, g.nz, g.nx), xof(vzn));
+                        if (ix >= 0 && ix < nx && in_xstrip(iz, M, g.nz))
+                            band_put(a.bands, a.bands.v, bandoff + band_zstrip(iz, ix, M, g.nz, nx), xof(vzn));
                     }
                 }
                 if (HESS) {
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
             float hxq = 0.f;
             if (vxok) {
                 T G = stencil<M, T>(g.cx, [&](int l) { return sP[t + l]; }, [&](int l) { return sP[t + 1 - l]; });
-                const bool last = x + 1 >= g.Nx;
+                const bool last = x + 1 >= Nx;
                 const R bn = last ? cur.brz : sB[t + 1];
                 const float bux = 0.5f * (xof(cur.brz) + xof(bn));
                 if (pmlxh) {
@@ -387,8 +399,8 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                     out[oVX * pT + cz] = vxn;
                     if (BANDS) {
                         int iz = z - z0;
-                        if (iz >= 0 && iz < g.nz && in_xstrip(ix, M, g.nx))
-                            band_put(a.bands, a.bands.v, bandoff + band_xstrip(iz, ix, M, g.nz, g.nx), xof(vxn));
+                        if (iz >= 0 && iz < g.nz && in_xstrip(ix, M, nx))
+                            band_put(a.bands, a.bands.v, bandoff + band_xstrip(iz, ix, M, g.nz, nx), xof(vxn));
                     }
                 }
                 if (HESS) {
@@ -426,12 +438,12 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                 }
                 out[oP * pT + cz] = pn;
                 if (BANDS) {
-                    long long b = pband_index(z - z0, ix, M, g.nz, g.nx);
+                    long long b = pband_index(z - z0, ix, M, g.nz, nx);
                     if (b >= 0) band_put(a.bands, a.bands.p, bandoff + b, xof(p0));
                 }
                 if (HESS) {
                     int iz = z - z0;
-                    if (iz >= 0 && iz < g.nz && ix >= 0 && ix < g.nx) {
+                    if (iz >= 0 && iz < g.nz && ix >= 0 && ix < nx) {
                         float bx0 = xof(cur.brz);
                         float hr = 0.5f * ((sH[t] + sH[t - 1]) + (HZ[(u + M) % W] + HZ[(u + M - 1) % W])) /
                                    (bx0 * bx0);
@@ -476,7 +488,7 @@ struct AdjRow {
     float kdr, lpvzr, bz, lppz, kdz, lpsvx, lpsvz, bx, lppx;
 };
 
-template <int M>
+template <int M, bool WIN>
 __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const float2 *img, const float *in,
                                           int xc, int z, int zc0, int zc1, bool colok, bool vxok,
                                           bool outcol, bool pmlxh, bool pmlxn, bool inner_col)
@@ -508,14 +520,16 @@ __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const floa
     cpa(s2 + 2 * NTH, in2 + (A_PL / 2) * p2 + cz, okz);
     cpa(s2 + 3 * NTH, in2 + (A_VX / 2) * p2 + cz, okv);
     cpa(s2 + 4 * NTH, img + cz, outcol && main && inner_col && iz >= 0 && iz < g.nz);
-    cpa(s1 + 0 * NTH, a.kdt + cr, okr);
+    const float *kdt = WIN ? in + W_KDT * plane : a.kdt;
+    const float *binv = WIN ? in + W_BINV * plane : a.binv;
+    cpa(s1 + 0 * NTH, kdt + cr, okr);
     cpa(s1 + 1 * NTH, in + A_LPVZ * plane + cr, okr && ((zr <= z0 - 1) || (zr >= z1)));
-    cpa(s1 + 2 * NTH, a.binv + ck1, okk1);
+    cpa(s1 + 2 * NTH, binv + ck1, okk1);
     cpa(s1 + 3 * NTH, in + A_LPPZ * plane + ck, okk && ((k <= z0 - 2) || (k >= z1)));
-    cpa(s1 + 4 * NTH, a.kdt + cz, okz);
+    cpa(s1 + 4 * NTH, kdt + cz, okz);
     cpa(s1 + 5 * NTH, in + A_LPVX * plane + cz, okz && pmlxn);
     cpa(s1 + 6 * NTH, in + A_LPVZ * plane + cz, outcol && main && ((z <= z0 - 1) || (z >= z1)));
-    cpa(s1 + 7 * NTH, a.binv + cz, okz);
+    cpa(s1 + 7 * NTH, binv + cz, okz);
     cpa(s1 + 8 * NTH, in + A_LPPX * plane + cz, okv && pmlxh);
 }
 
@@ -542,7 +556,7 @@ __device__ __forceinline__ AdjRow adj_read(const float *st)
     return r;
 }
 
-template <int M>
+template <int M, bool WIN>
 __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
 {
     using C = Cols<M>;
@@ -556,14 +570,18 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
 
     const GridDev &g = a.g;
     const int t = threadIdx.x;
+    const int slot = blockIdx.z, shot = a.shot0 + slot;
+    // padded and interior widths of this shot's grid (its aperture window)
+    const int Nx = WIN ? a.win_nx[shot] + 2 * g.x0 : g.Nx;
+    const int nx = WIN ? Nx - 2 * g.x0 : g.nx;
+    if (WIN && (int)blockIdx.x * TXO >= Nx) return;   // no output column in this shot's window
     const int x = (int)blockIdx.x * TXO - HXP + t;
-    const bool colok = x >= 0 && x < g.Nx;
+    const bool colok = x >= 0 && x < Nx;
     const bool outcol = colok && t >= HXP && t < HXP + TXO;
     const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
     const int zc0 = (int)blockIdx.y * a.tzc;
     const int zc1 = min(zc0 + a.tzc, g.Nz);
     const int zstart = zc0 - W;
-    const int slot = blockIdx.z, shot = a.shot0 + slot;
     const long long plane = g.plane;
     const long long p2 = plane;   // stride of one pair field in float2 units
     const int pitch = g.pitch;
@@ -574,13 +592,14 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     const float dt = g.dt;
     const int n = a.n;
     const bool recon = n > 0;
-    const int x0 = g.x0, x1 = g.x0 + g.nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const int x0 = g.x0, x1 = g.x0 + nx, z0 = g.z0, z1 = g.z0 + g.nz;
     const int ix = x - x0;
-    const bool xint = ix >= 0 && ix < g.nx;
+    const bool xint = ix >= 0 && ix < nx;
     const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
     const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
-    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
-    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
+    const int px = WIN ? shot * a.pml_xstride + x : x;   // x CPML profiles of this shot's window
+    const float ahx = pmlxh ? a.pml.ah[2][px] : 0.f, bhx = pmlxh ? a.pml.bh[2][px] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][px] : 0.f, bix = pmlxn ? a.pml.bi[2][px] : 0.f;
     const long long bandprev = band_base(a.bands, shot, n - 1);
     const int src = a.src_cell[shot];
     const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1] : 0.f;
@@ -611,7 +630,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
             const bool ok = colok && r >= 0 && r < g.Nz;
             const long long cr = ok ? (long long)r * pitch + xc : 0;
             const float2 pl = ok ? in2[(A_PL / 2) * p2 + cr] : make_float2(0.f, 0.f);
-            const float kd = ok ? a.kdt[cr] : 0.f;
+            const float kd = ok ? (WIN ? in[W_KDT * plane + cr] : a.kdt[cr]) : 0.f;
             const float lpvz = (ok && ((r <= z0 - 1) || (r >= z1))) ? in[A_LPVZ * plane + cr] : 0.f;
             PU[j] = pu_node(r, pl, kd, lpvz);
         }
@@ -619,13 +638,14 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     float bz_old = 0.f;
     {
         int k = zstart + M - 1;
-        if (colok && k >= 0 && k < g.Nz) bz_old = a.binv[(long long)k * pitch + xc];
+        if (colok && k >= 0 && k < g.Nz)
+            bz_old = WIN ? in[W_BINV * plane + (long long)k * pitch + xc] : a.binv[(long long)k * pitch + xc];
     }
 
 #pragma unroll
     for (int j = 0; j < PD - 1; ++j) {
         if (zstart + j < zc1)
-            adj_issue<M>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
+            adj_issue<M, WIN>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
                          outcol, pmlxh, pmlxn, xint);
         cp_commit();
     }
@@ -637,7 +657,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
             if (z >= zc1) break;
             const int zi = z + PD - 1;
             if (zi < zc1)
-                adj_issue<M>(stagef + ((zi - zstart) % PD) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
+                adj_issue<M, WIN>(stagef + ((zi - zstart) % PD) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
                              colok, vxok, outcol, pmlxh, pmlxn, xint);
             cp_commit();
             cp_wait_row();
@@ -668,7 +688,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                     const int iz = k - z0;
                     if (iz >= 0 && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
                     else if (in_xstrip(iz, M, g.nz))
-                        vn = band_get(a.bands, a.bands.v, bandprev + band_zstrip(iz, ix, M, g.nz, g.nx));
+                        vn = band_get(a.bands, a.bands.v, bandprev + band_zstrip(iz, ix, M, g.nz, nx));
                 }
                 if (own) out2[(A_VZ / 2) * p2 + ck] = make_float2(vn, lv);
             }
@@ -692,7 +712,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                 // (Gx, du/dx)
                 const float2 D = stencil<M, float2>(g.cx, [&](int l) { return sPU[t + l]; },
                                                     [&](int l) { return sPU[t + 1 - l]; });
-                const float bux = 0.5f * (cur.bx + (x + 1 >= g.Nx ? cur.bx : sB[t + 1]));
+                const float bux = 0.5f * (cur.bx + (x + 1 >= Nx ? cur.bx : sB[t + 1]));
                 const float dtbu = dt * bux;
                 const float lv = cur.v2x.y + D.y;
                 float wx = dtbu * lv;
@@ -707,8 +727,8 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                     const int iz = z - z0;
                     if (iz >= 0 && iz < g.nz) {
                         if (xint) vxn = cur.v2x.x + dtbu * D.x;
-                        else if (in_xstrip(ix, M, g.nx))
-                            vxn = band_get(a.bands, a.bands.v, bandprev + band_xstrip(iz, ix, M, g.nz, g.nx));
+                        else if (in_xstrip(ix, M, nx))
+                            vxn = band_get(a.bands, a.bands.v, bandprev + band_xstrip(iz, ix, M, g.nz, nx));
                     }
                 }
                 if (outcol) out2[(A_VX / 2) * p2 + cz] = make_float2(vxn, lv);
@@ -745,7 +765,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                         pn = pbn + kd * qn;
                         if (cz + x == src) pn -= wsrc;
                     } else {
-                        long long b = pband_index(iz, ix, M, g.nz, g.nx);
+                        long long b = pband_index(iz, ix, M, g.nz, nx);
                         if (b >= 0) pn = band_get(a.bands, a.bands.p, bandprev + b);
                     }
                 }
@@ -791,17 +811,20 @@ __global__ void k_pack_adj(const GridDev g, const float *final_state, int shot0,
     }
 }
 
-template <int M, bool BORN, bool BANDS, bool HESS>
+template <int M, bool BORN, bool BANDS, bool HESS, bool WIN>
 cudaError_t launch_fwd_t(const Step2D &a, dim3 grid, cudaStream_t s)
 {
-    k_fwd2d<M, BORN, BANDS, HESS><<<grid, NTH, kFwdStageBytes, s>>>(a);
+    k_fwd2d<M, BORN, BANDS, HESS, WIN><<<grid, NTH, kFwdStageBytes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int M, bool BORN, bool BANDS, bool HESS>
 cudaError_t attr_fwd()
 {
-    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdStageBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kFwdStageBytes);
 }
 
@@ -814,26 +837,81 @@ cudaError_t attr_M()
     if ((e = attr_fwd<M, false, true, false>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, false, true>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, false, false>()) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_adj2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
+    if ((e = cudaFuncSetAttribute(k_adj2d<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kAdjStageBytes)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_adj2d<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
+}
+
+template <int M, bool WIN>
+cudaError_t launch_fwd_MW(const Step2D &a, dim3 grid, bool born, bool bands, bool hess, cudaStream_t s)
+{
+    if (born) return launch_fwd_t<M, true, false, false, WIN>(a, grid, s);
+    if (bands && hess) return launch_fwd_t<M, false, true, true, WIN>(a, grid, s);
+    if (bands) return launch_fwd_t<M, false, true, false, WIN>(a, grid, s);
+    if (hess) return launch_fwd_t<M, false, false, true, WIN>(a, grid, s);
+    return launch_fwd_t<M, false, false, false, WIN>(a, grid, s);
 }
 
 template <int M>
 cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool hess, cudaStream_t s)
 {
     dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
-    if (born) return launch_fwd_t<M, true, false, false>(a, grid, s);
-    if (bands && hess) return launch_fwd_t<M, false, true, true>(a, grid, s);
-    if (bands) return launch_fwd_t<M, false, true, false>(a, grid, s);
-    if (hess) return launch_fwd_t<M, false, false, true>(a, grid, s);
-    return launch_fwd_t<M, false, false, false>(a, grid, s);
+    if (a.win_nx) return launch_fwd_MW<M, true>(a, grid, born, bands, hess, s);
+    return launch_fwd_MW<M, false>(a, grid, born, bands, hess, s);
 }
 
 template <int M>
 cudaError_t launch_adj_M(const Step2D &a, int batch, cudaStream_t s)
 {
     dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
-    k_adj2d<M><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    if (a.win_nx)
+        k_adj2d<M, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    else
+        k_adj2d<M, false><<<grid, NTH, kAdjStageBytes, s>>>(a);
     return cudaGetLastError();
+}
+
+__global__ void k_window_model(const GridDev gm, const GridDev g, const int *win_x0, const int *win_nx, int shot0,
+                               int batch, const float *kdt, const float *binv, const float2 *kd2,
+                               const float2 *br2, float *st0, float *st1, long long sstride)
+{
+    const long long plane = g.plane;
+    const long long n = (long long)batch * plane;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int slot = (int)(i / plane);
+        const long long c = i - (long long)slot * plane;
+        const int z = (int)(c / g.pitch), x = (int)(c - (long long)z * g.pitch);
+        const int shot = shot0 + slot;
+        const int nxw = win_nx[shot], Nxw = nxw + 2 * g.x0;
+        float k = 0.f, b = 0.f;
+        float2 k2 = make_float2(0.f, 0.f), b2 = make_float2(0.f, 0.f);
+        if (x < Nxw) {
+            const int xi = min(max(x - g.x0, 0), nxw - 1);
+            const long long cm = (long long)z * gm.pitch + gm.x0 + win_x0[shot] + xi;
+            const bool inner = x >= g.x0 && x < g.x0 + nxw;
+            k = kdt[cm];
+            b = binv[cm];
+            if (kd2) {
+                k2 = kd2[cm];
+                b2 = br2[cm];
+                if (!inner) {
+                    k2.y = 0.f;
+                    b2.y = 0.f;
+                }
+            }
+        }
+        for (int q = 0; q < 2; ++q) {
+            float *o = (q ? st1 : st0) + slot * sstride;
+            o[W_KDT * plane + c] = k;
+            o[W_BINV * plane + c] = b;
+            if (kd2) {
+                reinterpret_cast<float2 *>(o + W_KD2 * plane)[c] = k2;
+                reinterpret_cast<float2 *>(o + W_BR2 * plane)[c] = b2;
+            }
+        }
+    }
 }
 
 }  // namespace
@@ -857,6 +935,17 @@ cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s)
 {
     if (a.g.M == 2) return launch_adj_M<2>(a, batch, s);
     return launch_adj_M<4>(a, batch, s);
+}
+
+cudaError_t launch_window_model(const GridDev &gm, const GridDev &g, const int *win_x0, const int *win_nx,
+                                int shot0, int batch, const float *kdt, const float *binv, const float2 *kd2,
+                                const float2 *br2, float *st0, float *st1, long long sstride, cudaStream_t s)
+{
+    long long n = batch * g.plane;
+    int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    k_window_model<<<blocks, 256, 0, s>>>(gm, g, win_x0, win_nx, shot0, batch, kdt, binv, kd2, br2, st0, st1,
+                                          sstride);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int shot0, int batch, float *st,

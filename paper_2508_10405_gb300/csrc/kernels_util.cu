@@ -83,14 +83,29 @@ __global__ void k_inject(GridDev g, TileRecs tr, int shot0, const float *dstage,
     }
 }
 
-__global__ void k_image_acc(GridDev g, const float2 *img, int batch, double2 *acc)
+// Cell of interior point k (of the model grid gm) in slot b's grid g, or -1
+// when it lies outside that shot's aperture window (win_x0 null: no windows,
+// gm and g are the same grid).
+__device__ inline long long slot_cell(const GridDev &gm, const GridDev &g, long long k, int shot,
+                                      const int *win_x0, const int *win_nx)
 {
-    long long nint = (long long)g.nz * g.ny * g.nx;
+    if (!win_x0) return pad_of(g, k);
+    const int ix = (int)(k % gm.nx), iz = (int)(k / gm.nx);
+    const int xl = ix - win_x0[shot];
+    if (xl < 0 || xl >= win_nx[shot]) return -1;
+    return (long long)(iz + g.z0) * g.pitch + g.x0 + xl;
+}
+
+__global__ void k_image_acc(GridDev gm, GridDev g, const float2 *img, int batch, int shot0, const int *win_x0,
+                            const int *win_nx, double2 *acc)
+{
+    long long nint = (long long)gm.nz * gm.ny * gm.nx;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
          k += (long long)gridDim.x * blockDim.x) {
-        long long c = pad_of(g, k);
         double2 s = acc[k];
         for (int b = 0; b < batch; ++b) {
+            long long c = slot_cell(gm, g, k, shot0 + b, win_x0, win_nx);
+            if (c < 0) continue;
             float2 v = img[b * g.plane + c];
             s.x += v.x;
             s.y += v.y;
@@ -115,14 +130,17 @@ __global__ void k_image_fin(GridDev g, const double2 *acc, const float *kdt, con
     }
 }
 
-__global__ void k_hess_acc(GridDev g, const float *hess, int batch, double *acc)
+__global__ void k_hess_acc(GridDev gm, GridDev g, const float *hess, int batch, int shot0, const int *win_x0,
+                           const int *win_nx, double *acc)
 {
-    long long nint = (long long)g.nz * g.ny * g.nx;
+    long long nint = (long long)gm.nz * gm.ny * gm.nx;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nint;
          k += (long long)gridDim.x * blockDim.x) {
-        long long c = pad_of(g, k);
         double s = acc[k];
-        for (int b = 0; b < batch; ++b) s += hess[b * g.plane + c];
+        for (int b = 0; b < batch; ++b) {
+            long long c = slot_cell(gm, g, k, shot0 + b, win_x0, win_nx);
+            if (c >= 0) s += hess[b * g.plane + c];
+        }
         acc[k] = s;
     }
 }
@@ -340,11 +358,11 @@ cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int bat
     return cudaGetLastError();
 }
 
-cudaError_t launch_image_accumulate(const GridDev &g, const float2 *img, int batch,
-                                    double2 *acc, cudaStream_t s)
+cudaError_t launch_image_accumulate(const GridDev &gm, const GridDev &g, const float2 *img, int batch, int shot0,
+                                    const int *win_x0, const int *win_nx, double2 *acc, cudaStream_t s)
 {
-    long long n = (long long)g.nz * g.ny * g.nx;
-    k_image_acc<<<grid_for(n), NT, 0, s>>>(g, img, batch, acc);
+    long long n = (long long)gm.nz * gm.ny * gm.nx;
+    k_image_acc<<<grid_for(n), NT, 0, s>>>(gm, g, img, batch, shot0, win_x0, win_nx, acc);
     return cudaGetLastError();
 }
 
@@ -356,11 +374,11 @@ cudaError_t launch_image_finalize(const GridDev &g, const double2 *acc, const fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_hess_accumulate(const GridDev &g, const float *hess, int batch, double *acc,
-                                   cudaStream_t s)
+cudaError_t launch_hess_accumulate(const GridDev &gm, const GridDev &g, const float *hess, int batch, int shot0,
+                                   const int *win_x0, const int *win_nx, double *acc, cudaStream_t s)
 {
-    long long n = (long long)g.nz * g.ny * g.nx;
-    k_hess_acc<<<grid_for(n), NT, 0, s>>>(g, hess, batch, acc);
+    long long n = (long long)gm.nz * gm.ny * gm.nx;
+    k_hess_acc<<<grid_for(n), NT, 0, s>>>(gm, g, hess, batch, shot0, win_x0, win_nx, acc);
     return cudaGetLastError();
 }
 

@@ -82,7 +82,17 @@ struct Step2D {
     Bands bands;
     float *hess;          // [batch][plane] pseudo-Hessian accumulators (or null)
     float2 *img;          // [batch][plane] image accumulators (adjoint)
+    // Aperture windows (null: every shot spans the whole model). A windowed
+    // shot runs on its own grid of win_nx[shot] + 2 npml columns; its model
+    // planes sit in its slot after the state (kWinStatePlanes2D planes per
+    // slot) and its x CPML profiles at pml.*[2] + shot * pml_xstride.
+    const int *win_nx;
+    int pml_xstride;
 };
+
+// Planes of a 2D slot when shots have aperture windows: the 10 state planes,
+// then dt kappa, 1/rho and the two Born pairs of the shot's window.
+constexpr int kWinStatePlanes2D = 16;
 
 // Arguments of the 3D time-step kernels (state updated in place).
 struct Step3D {
@@ -127,6 +137,14 @@ cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands,
                          cudaStream_t s);
 cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s);
 cudaError_t configure_2d_kernels();
+// Copies each windowed shot's model into its slot (both ping-pong buffers):
+// column x of the shot's grid takes model column npml + x0 + clamp(x - npml,
+// 0, nx_w - 1) of the full padded planes (edge replication of the window);
+// the Born perturbation (.y of the pairs) is kept on the window interior only
+// and zeroed in its pad; columns beyond the shot's grid are zero.
+cudaError_t launch_window_model(const GridDev &gm, const GridDev &g, const int *win_x0, const int *win_nx,
+                                int shot0, int batch, const float *kdt, const float *binv, const float2 *kd2,
+                                const float2 *br2, float *st0, float *st1, long long sstride, cudaStream_t s);
 // Adjoint start state (p, 0), (vx, 0), (vz, 0) from the saved background final states.
 cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int shot0, int batch,
                                 float *st, long long sstride, cudaStream_t s);
@@ -149,12 +167,15 @@ cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt
 cudaError_t launch_inject_residual(const GridDev &g, const TileRecs &tr, int batch, int shot0,
                                    const float *dstage, int n, float2 *pl, long long sstride2,
                                    cudaStream_t s);
-cudaError_t launch_image_accumulate(const GridDev &g, const float2 *img, int batch,
-                                    double2 *acc, cudaStream_t s);
+// Stacks the batch's per-slot images (grid g) into the FP64 interior image of
+// the model grid gm; with aperture windows (win_x0 non-null) slot b covers the
+// columns [win_x0, win_x0 + win_nx) of shot shot0 + b.
+cudaError_t launch_image_accumulate(const GridDev &gm, const GridDev &g, const float2 *img, int batch, int shot0,
+                                    const int *win_x0, const int *win_nx, double2 *acc, cudaStream_t s);
 cudaError_t launch_image_finalize(const GridDev &g, const double2 *acc, const float *kdt,
                                   const float *binv, float *gout, cudaStream_t s);
-cudaError_t launch_hess_accumulate(const GridDev &g, const float *hess, int batch, double *acc,
-                                   cudaStream_t s);
+cudaError_t launch_hess_accumulate(const GridDev &gm, const GridDev &g, const float *hess, int batch, int shot0,
+                                   const int *win_x0, const int *win_nx, double *acc, cudaStream_t s);
 cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out,
                                  cudaStream_t s);
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);

@@ -214,6 +214,7 @@ extern "C" lsrtm_status lsrtm_born_static(const lsrtm_config *cfg, const float *
     const long long nint = (long long)g.nz * g.nx;
     // geometry checks (host arrays)
     if (geom->nshot < 1 || !geom->src_idx || !geom->rec_ptr) return fail(LSRTM_ERR_ARG, "invalid geometry");
+    if (geom->win_x0 || geom->win_nx) return fail(LSRTM_ERR_ARG, "lsrtm_born_static does not take aperture windows");
     const int nshot = geom->nshot;
     if (geom->rec_ptr[0] != 0) return fail(LSRTM_ERR_GEOMETRY, "rec_ptr[0] must be 0");
     for (int s = 0; s < nshot; ++s) {
