@@ -21,6 +21,7 @@ the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -60,6 +61,11 @@ def parse():
     ap.add_argument("--shots", type=int, default=None,
                     help="override the shot count (smaller cases for profiling)")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps")
+    ap.add_argument("--plan", choices=["batched", "plain"], default="batched",
+                    help="execution plan of the timed handle")
+    ap.add_argument("--plain-shots", type=int, default=4,
+                    help="shots on which the plain per-shot FP32 plan is timed for the "
+                         "per-iteration comparison (0: skip)")
     return ap.parse_args()
 
 
@@ -159,14 +165,24 @@ def ncu_traffic(kernel, cells_per_launch):
         return None
 
 
+def shot_cells(w):
+    """Padded cells of every shot's grid (its aperture window where it has one)."""
+    n = np.full(w.geom.nshot, float(w.padded_cells))
+    if getattr(w.geom, "win_nx", None) is not None:
+        n = (w.nz + 2.0 * w.npml) * (np.asarray(w.geom.win_nx, np.float64) + 2.0 * w.npml)
+    return n
+
+
 def cpu_sample(w, seconds, reps=1):
     """Times the FP64 oracle (L then L^T) on a bounded sample of the workload:
     a subset of shots and the first nt_s time steps, sized for ~`seconds` of
     work. Returns (G cell-updates/s, threads, description, seconds/rep)."""
     import oracle
     threads = oracle.num_threads()
-    ncell = w.padded_cells
+    if getattr(w.geom, "win_nx", None) is not None:
+        threads = 1   # the oracle models windowed shots one call (one thread) at a time
     nshot = min(w.geom.nshot, max(1, threads))
+    ncell = float(np.mean(shot_cells(w)[:nshot]))
     geom = w.geom.subset(list(range(nshot)))
     # calibrate the per-step cost from two short runs (removes the set-up time)
     ts = []
@@ -186,7 +202,8 @@ def cpu_sample(w, seconds, reps=1):
     t = min(times)
     cells = 2.0 * nshot * ncell * nt_s
     desc = (f"oracle L + L^T on {nshot} of {w.geom.nshot} shots x first {nt_s} of {w.nt} steps "
-            f"({cells:.3g} cell-updates), FP64, OpenMP over shots")
+            f"({cells:.3g} cell-updates), FP64, "
+            + ("one thread per windowed shot" if threads == 1 else "OpenMP over shots"))
     return cells / t / 1e9, threads, desc, times
 
 
@@ -225,6 +242,47 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def plain_compare(w, nshots, s_batched, bands, torch):
+    """Per-iteration time of the plain plan (one shot per launch, no graphs,
+    FP32 bands, background recomputed inside every L^T) timed on the first
+    `nshots` shots and scaled to all shots (the plain plan runs shots one
+    after another), against the batched plan's measured iteration; and the
+    relative L2 distance of the two plans' images after two CGNR iterations
+    on those shots (batched with the benchmark's band precision)."""
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
+    nshots = min(nshots, w.geom.nshot)
+    sub = dataclasses.replace(w, geom=w.geom.subset(list(range(nshots))))
+    hp = Lsrtm.from_workload(sub, plan=PLAN_PLAIN, band_precision=BAND_FP32)
+    hb = Lsrtm.from_workload(sub, plan=PLAN_BATCHED,
+                             band_precision=BAND_BF16 if bands == "bf16" else BAND_FP32)
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    d = hp.born(dm)
+    res = {}
+    for name, h in (("plain", hp), ("batched", hb)):
+        h.cg_begin(d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.cg_iterate(1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h.cg_iterate(1)
+        torch.cuda.synchronize()
+        res[name] = (min(t1 - t0, time.perf_counter() - t1), h.cg_result()[0])
+    frac = float(shot_cells(w)[:nshots].sum() / shot_cells(w).sum())
+    s_plain = res["plain"][0] / frac
+    xp, xb = res["plain"][1].double(), res["batched"][1].double()
+    out = {"s_per_iter_plain": s_plain, "s_per_iter_batched": s_batched,
+           "speedup": s_plain / s_batched,
+           "image_rel_l2_after_2_iters": float(torch.linalg.norm(xb - xp) / torch.linalg.norm(xp)),
+           "plain": "one shot per launch, no graph, FP32 bands, background recomputed in every L^T",
+           "batched_bands": bands,
+           "sample": f"plain timed on {nshots} of {w.geom.nshot} shots (fastest of 2 iterations), "
+                     f"scaled by padded cells"}
+    hp.close()
+    hb.close()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -237,15 +295,16 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
 
-    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, Lsrtm
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
 
     w = workload(args)
     K, W = args.steps, args.warmup
     ncell = w.padded_cells
     nshot = w.geom.nshot
-    cells_per_step = 2.0 * nshot * ncell * w.nt          # L + L^T per CG iteration
+    cells_per_step = 2.0 * float(shot_cells(w).sum()) * w.nt   # L + L^T per CG iteration
     h = Lsrtm.from_workload(w, band_precision=BAND_BF16 if args.bands == "bf16" else BAND_FP32,
-                            shots_per_batch=args.shots_per_batch)
+                            shots_per_batch=args.shots_per_batch,
+                            plan=PLAN_PLAIN if args.plan == "plain" else PLAN_BATCHED)
     dm_true = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
     d_obs = h.born(dm_true)                 # synthetic observed data (untimed setup)
     h.cg_begin(d_obs)                       # background bands cached here
@@ -274,6 +333,7 @@ def main():
         dist.barrier()
     t_local = ev0.elapsed_time(ev1) / 1e3
     launches = h.kernel_launches() - l0
+    workspace = h.workspace_bytes()
     tm = h.timings(reset=True)
     h.timing(False)
     clk = clocks.stop()
@@ -336,6 +396,10 @@ def main():
                "d2h_bytes_per_step": int(d_h.numel() * 4 + g_h.numel() * 4),
                "calls": "lsrtm_born + lsrtm_adjoint with pinned host buffers"}
 
+    plain = None
+    if args.plain_shots > 0 and args.plan == "batched":
+        plain = plain_compare(w, args.plain_shots, t_max / K, args.bands, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, threads, desc, _ = cpu_sample(w, args.cpu_seconds)
@@ -348,15 +412,18 @@ def main():
             "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": t_max / K * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "grid": [w.nz, w.nx], "padded_cells": ncell,
+            "config": {"workload": w.name, "grid": list(w.shape), "padded_cells": ncell,
+                       "padded_cells_per_step": float(shot_cells(w).sum()),
                        "nt": w.nt, "order": w.order, "shots_per_rank": nshot,
-                       "receivers_per_shot": int(w.geom.rec_ptr[1]), "bands": args.bands,
+                       "receivers_per_shot": float(np.mean(np.diff(w.geom.rec_ptr))),
+                       "bands": args.bands, "plan": args.plan,
                        "step": "one CGNR iteration (L + L^T + FP64 Krylov updates)",
                        "s_per_lsrtm_iter": t_max / K,
-                       "l2": "inputs larger than L2 (state 4.6 GB + bands 37.7 GB per rank)",
+                       "l2": f"inputs larger than L2 (workspace {workspace / 1e9:.1f} GB per rank)",
                        "parallelism": f"shots per rank, {world} rank(s), no data-path collective"},
             "roofline": roofline, "per_operator": per_op, "clocks": clk,
             "gpu_launches": int(launches), "e2e": e2e, "cpu_baseline": cpu,
+            "plain_vs_batched": plain,
         }
         print(json.dumps(line), flush=True)
     h.close()
