@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", type=int, default=2, help="preset number (default 2)")
     ap.add_argument("--shots-per-batch", type=int, default=0)
-    ap.add_argument("--bands", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--bands", choices=["fp32", "bf16", "fp16"], default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -249,12 +249,12 @@ def plain_compare(w, nshots, s_batched, bands, torch):
     after another), against the batched plan's measured iteration; and the
     relative L2 distance of the two plans' images after two CGNR iterations
     on those shots (batched with the benchmark's band precision)."""
-    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
     nshots = min(nshots, w.geom.nshot)
     sub = dataclasses.replace(w, geom=w.geom.subset(list(range(nshots))))
     hp = Lsrtm.from_workload(sub, plan=PLAN_PLAIN, band_precision=BAND_FP32)
     hb = Lsrtm.from_workload(sub, plan=PLAN_BATCHED,
-                             band_precision=BAND_BF16 if bands == "bf16" else BAND_FP32)
+                             band_precision={"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[bands])
     dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
     d = hp.born(dm)
     res = {}
@@ -295,14 +295,15 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
 
-    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
+    bands = {"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[args.bands]
 
     w = workload(args)
     K, W = args.steps, args.warmup
     ncell = w.padded_cells
     nshot = w.geom.nshot
     cells_per_step = 2.0 * float(shot_cells(w).sum()) * w.nt   # L + L^T per CG iteration
-    h = Lsrtm.from_workload(w, band_precision=BAND_BF16 if args.bands == "bf16" else BAND_FP32,
+    h = Lsrtm.from_workload(w, band_precision=bands,
                             shots_per_batch=args.shots_per_batch,
                             plan=PLAN_PLAIN if args.plan == "plain" else PLAN_BATCHED)
     dm_true = torch.tensor(w.dm, dtype=torch.float32, device="cuda")

@@ -49,8 +49,12 @@ typedef enum {
     LSRTM_ERR_STATE = 7       /* handle not usable for this call */
 } lsrtm_status;
 
-/* Band / checkpoint storage precision. */
-enum { LSRTM_BAND_FP32 = 0, LSRTM_BAND_BF16 = 1 };
+/* Storage precision of the saved boundary bands (App. A). The 16-bit formats
+ * keep one FP32 scale per band per step: values are stored as v / s with
+ * s = max|band| / 2^15, so FP16 keeps its 11-bit mantissa down to 2^-24 of
+ * each band's maximum and BF16 its 8-bit mantissa over the FP32 range. The
+ * plain plan always stores FP32. */
+enum { LSRTM_BAND_FP32 = 0, LSRTM_BAND_BF16 = 1, LSRTM_BAND_FP16 = 2 };
 /* Source-wavefield reconstruction for L^T (App. A: the background field must
  * be available in reverse time). */
 enum { LSRTM_RECON_BOUNDARY = 0,   /* boundary bands + reverse-time recomputation */
@@ -72,7 +76,7 @@ typedef struct {
     int npml;                /* CPML thickness in cells (>= fd_order/2) on every side */
     double f0;               /* dominant frequency [Hz]; sets the CPML alpha profile */
     double pml_vmax;         /* velocity for the CPML damping; <= 0: max of vp */
-    int band_precision;      /* LSRTM_BAND_FP32 or LSRTM_BAND_BF16 */
+    int band_precision;      /* LSRTM_BAND_FP32, LSRTM_BAND_BF16 or LSRTM_BAND_FP16 */
     size_t hbm_budget_bytes; /* workspace cap; 0 = no cap */
     int recon_mode;          /* LSRTM_RECON_* */
     int plan;                /* LSRTM_PLAN_* */

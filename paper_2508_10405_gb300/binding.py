@@ -20,7 +20,7 @@ SO_PATH = os.path.join(_HERE, "_lib", "liblsrtm.so")
 LSRTM_OK = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CFL", 3: "ERR_GEOMETRY", 4: "ERR_OOM",
           5: "ERR_NONFINITE", 6: "ERR_CUDA", 7: "ERR_STATE"}
-BAND_FP32, BAND_BF16 = 0, 1
+BAND_FP32, BAND_BF16, BAND_FP16 = 0, 1, 2
 RECON_BOUNDARY, RECON_CHECKPOINT, RECON_AUTO = 0, 1, 2
 PLAN_BATCHED, PLAN_PLAIN = 0, 1
 

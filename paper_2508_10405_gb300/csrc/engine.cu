@@ -348,14 +348,14 @@ int timing_kind(int graph_kind)
     return graph_kind == G_BORN ? 0 : (graph_kind == G_ADJ ? 2 : 1);
 }
 
-// Runs `body` (which enqueues the nt-step loop of one batch on h->work),
-// captured once into a CUDA graph per (kind, batch) and replayed afterwards.
-// Kernel launches one nt-step loop of this kind contains.
+// Kernel launches one nt-step loop of this kind contains (band-saving loops
+// with 16-bit bands pack the bands after every step).
 long long loop_launches(const lsrtm_handle *h, int kind)
 {
     const long long nt = h->g.nt;
-    if (h->g.ndim != 3) return nt;
-    return kind == G_ADJ ? 2 * nt - 1 : 2 * nt;
+    const long long pack = (kind == G_BG || kind == G_BG_HESS) && h->bands.fmt != BAND_F32 ? nt : 0;
+    if (h->g.ndim != 3) return nt + pack;
+    return (kind == G_ADJ ? 2 * nt - 1 : 2 * nt) + pack;
 }
 
 template <class F>
@@ -447,6 +447,8 @@ lsrtm_status zero_slots(lsrtm_handle *h, int bs)
     CU(cudaMemsetAsync(h->st[0], 0, sb, h->work));
     if (h->st[1]) CU(cudaMemsetAsync(h->st[1], 0, sb, h->work));
     if (h->psiv) CU(cudaMemsetAsync(h->psiv, 0, (size_t)bs * h->vstride * sizeof(float), h->work));
+    if (h->bands.stage)
+        CU(cudaMemsetAsync(h->bands.stage, 0, (size_t)bs * 2 * h->bands.nb * sizeof(float), h->work));
     return LSRTM_OK;
 }
 
@@ -470,13 +472,15 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                     a.n = n;
                     if (n + 1 < nt) {
                         CU(launch_fwd3d(a, bs, false, true, hess, 3, h->work));
-                        continue;
+                    } else {
+                        CU(launch_fwd3d(a, bs, false, true, hess, 1, h->work));
+                        for (int s = 0; s < bs; ++s)
+                            CU(cudaMemcpyAsync(h->final_state + (size_t)(s0 + s) * 4 * plane,
+                                               h->st[0] + s * h->sstride, plane * sizeof(float),
+                                               cudaMemcpyDeviceToDevice, h->work));
+                        CU(launch_fwd3d(a, bs, false, true, hess, 2, h->work));
                     }
-                    CU(launch_fwd3d(a, bs, false, true, hess, 1, h->work));
-                    for (int s = 0; s < bs; ++s)
-                        CU(cudaMemcpyAsync(h->final_state + (size_t)(s0 + s) * 4 * plane, h->st[0] + s * h->sstride,
-                                           plane * sizeof(float), cudaMemcpyDeviceToDevice, h->work));
-                    CU(launch_fwd3d(a, bs, false, true, hess, 2, h->work));
+                    if (h->bands.fmt != BAND_F32) CU(launch_band_pack(h->bands, bs, s0, n, h->work));
                 }
                 return LSRTM_OK;
             }));
@@ -493,6 +497,7 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                     a.in = h->st[n & 1];
                     a.out = h->st[(n + 1) & 1];
                     CU(launch_fwd2d(a, bs, false, true, hess, h->work));
+                    if (h->bands.fmt != BAND_F32) CU(launch_band_pack(h->bands, bs, s0, n, h->work));
                 }
                 return LSRTM_OK;
             }));
@@ -660,7 +665,8 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
     sb.shot0 = s0;
     sb.t0 = t0;
     const bool d3 = is3d(h);
-    return run_loop_n(h, G_SEG + 2 * j, 1, s0, bs, d3 ? 2 * c : c, c, [&]() -> lsrtm_status {
+    const bool pack = sb.fmt != BAND_F32;
+    return run_loop_n(h, G_SEG + 2 * j, 1, s0, bs, (d3 ? 2 * c : c) + (pack ? c : 0), c, [&]() -> lsrtm_status {
         if (d3) {
             CHECK(ck_copy(h, j, h->rec[0], 10 * plane, 10, 0, bs, false));
             Step3D a = step3_args(h, s0);
@@ -670,6 +676,7 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
             for (int n = t0; n < hi; ++n) {
                 a.n = n;
                 CU(launch_fwd3d(a, bs, false, true, false, 3, h->work));
+                if (pack) CU(launch_band_pack(sb, bs, s0, n, h->work));
             }
             return LSRTM_OK;
         }
@@ -685,6 +692,7 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
             a.in = h->rec[n & 1];
             a.out = h->rec[(n + 1) & 1];
             CU(launch_fwd2d(a, bs, false, true, false, h->work));
+            if (pack) CU(launch_band_pack(sb, bs, s0, n, h->work));
         }
         return LSRTM_OK;
     });
@@ -863,8 +871,9 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
     if (c->nz < 1 || c->nx < 1 || c->nt < 1) return fail(LSRTM_ERR_ARG, "empty grid or nt < 1");
     if (c->npml < c->fd_order / 2) return fail(LSRTM_ERR_ARG, "npml must be >= fd_order/2");
     if (!(c->dt > 0) || !(c->dx > 0) || !(c->dz > 0)) return fail(LSRTM_ERR_ARG, "non-positive spacing or dt");
-    if (c->band_precision != LSRTM_BAND_FP32 && c->band_precision != LSRTM_BAND_BF16)
-        return fail(LSRTM_ERR_ARG, "band_precision must be 0 (fp32) or 1 (bf16)");
+    if (c->band_precision != LSRTM_BAND_FP32 && c->band_precision != LSRTM_BAND_BF16 &&
+        c->band_precision != LSRTM_BAND_FP16)
+        return fail(LSRTM_ERR_ARG, "band_precision must be 0 (fp32), 1 (bf16) or 2 (fp16)");
     if (c->recon_mode != LSRTM_RECON_BOUNDARY && c->recon_mode != LSRTM_RECON_CHECKPOINT &&
         c->recon_mode != LSRTM_RECON_AUTO)
         return fail(LSRTM_ERR_ARG, "recon_mode must be 0 (boundary), 1 (checkpoint) or 2 (auto)");
@@ -1173,8 +1182,10 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     // bands of one K-step segment at a time are recomputed.
     h->bands.nb = d3 ? 2LL * g.M * ((long long)g.nz * g.ny + (long long)g.nz * g.nx + (long long)g.ny * g.nx)
                      : 2LL * g.M * (g.nz + g.nx);
-    h->bands.bf16 = (cfg->plan == LSRTM_PLAN_BATCHED && cfg->band_precision == LSRTM_BAND_BF16) ? 1 : 0;
-    const size_t esz = h->bands.bf16 ? 2 : 4;
+    h->bands.fmt = cfg->plan == LSRTM_PLAN_PLAIN ? BAND_F32
+                   : (cfg->band_precision == LSRTM_BAND_BF16 ? BAND_BF16S
+                                                              : (cfg->band_precision == LSRTM_BAND_FP16 ? BAND_F16S : BAND_F32));
+    const size_t esz = h->bands.fmt == BAND_F32 ? 4 : 2;
     const size_t fbytes = (size_t)g.plane * sizeof(float);
     h->fs_planes = d3 ? 4 : 3;
 
@@ -1185,6 +1196,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     h->vstride = d3 ? 0 : kPsivPlanes2D * g.plane;
     size_t per_slot = d3 ? ((size_t)h->sstride + g.plane) * sizeof(float)
                          : (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
+    if (h->bands.fmt != BAND_F32) per_slot += 2 * (size_t)h->bands.nb * sizeof(float);   // FP32 band stage
     int batch = cfg->plan == LSRTM_PLAN_PLAIN ? 1 : (cfg->shots_per_batch > 0 ? cfg->shots_per_batch : h->nshot);
     batch = std::min(batch, h->nshot);
     size_t cg_bytes = (5 * 2 * (size_t)h->nint + (size_t)nd) * sizeof(float);
@@ -1197,9 +1209,11 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         avail = (long long)(0.92 * (double)fr) - (long long)cg_bytes;
     }
     const size_t band_full = 2 * (size_t)h->nshot * g.nt * h->bands.nb * esz;
+    const size_t scale_full = h->bands.fmt != BAND_F32 ? 2 * (size_t)h->nshot * g.nt * sizeof(float) : 0;
     const size_t fs_full = (size_t)h->nshot * h->fs_planes * fbytes;
     bool ckpt = cfg->recon_mode == LSRTM_RECON_CHECKPOINT;
-    if (cfg->recon_mode == LSRTM_RECON_AUTO) ckpt = !h->win && (long long)(band_full + fs_full + per_slot) > avail;
+    if (cfg->recon_mode == LSRTM_RECON_AUTO)
+        ckpt = !h->win && (long long)(band_full + scale_full + fs_full + per_slot) > avail;
     if (ckpt && h->win)
         return fail(LSRTM_ERR_ARG, "checkpoint reconstruction does not support aperture windows");
     h->ckpt = ckpt;
@@ -1210,8 +1224,9 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         h->bands.shot0 = 0;
         h->bands.t0 = 0;
         h->bands.nsteps = g.nt;
+        if (h->bands.fmt != BAND_F32) CHECK(dalloc_t(h, &h->bands.scale, (size_t)h->nshot * g.nt * 2));
         CHECK(dalloc_t(h, &h->final_state, (size_t)h->nshot * h->fs_planes * g.plane));
-        avail -= (long long)(band_full + fs_full);
+        avail -= (long long)(band_full + scale_full + fs_full);
     } else {
         // checkpoint: the background planes of a forward state (2D: p vx vz psi_px
         // psi_pz + the two node CPML memories; 3D: p, v, psi_p, psi_v)
@@ -1227,7 +1242,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         // recomputation state: 2D 5 + 5 ping-pong planes and 2 CPML planes; 3D 10 in place
         size_t rec_slot = (d3 ? 10 : 12) * fbytes;
         size_t ck_slot = (size_t)h->ck_nseg * h->ck_planes * fbytes + (size_t)K * (size_t)seg_step +
-                         rec_slot + h->fs_planes * fbytes;
+                         rec_slot + h->fs_planes * fbytes +
+                         (h->bands.fmt != BAND_F32 ? 2 * (size_t)K * sizeof(float) : 0);
         per_slot += ck_slot;
     }
     if (avail < (long long)per_slot)
@@ -1245,6 +1261,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         h->segbands.p = h->band_mem;
         h->segbands.v = static_cast<char *>(h->band_mem) + segb;
         h->segbands.nsteps = h->ck_K;
+        if (h->segbands.fmt != BAND_F32) CHECK(dalloc_t(h, &h->segbands.scale, (size_t)batch * h->ck_K * 2));
         h->bands = h->segbands;
         h->bands.shot0 = 0;
         h->bands.t0 = 0;
@@ -1257,6 +1274,10 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
             CHECK(dalloc_t(h, &h->rec[1], (size_t)batch * 5 * g.plane));
             CHECK(dalloc_t(h, &h->rec_psiv, (size_t)batch * 2 * g.plane));
         }
+    }
+    if (h->bands.fmt != BAND_F32) {
+        CHECK(dalloc_t(h, &h->bands.stage, (size_t)batch * 2 * h->bands.nb));
+        h->segbands.stage = h->bands.stage;
     }
     CHECK(dalloc_t(h, &h->st[0], (size_t)batch * h->sstride));
     if (!d3) {

@@ -27,7 +27,10 @@ namespace lsrtm {
 namespace {
 
 constexpr int NTH = kThreads2D;
-constexpr int PD = 4;   // depth of the asynchronous row pipeline
+constexpr int PDF = 4;   // depth of the asynchronous row pipeline (forward)
+constexpr int PDA = 4;   // depth of the asynchronous row pipeline (adjoint)
+constexpr int kFwdMinBlocks = 2;   // resident CTAs per SM the register budget targets
+constexpr int kAdjMinBlocks = 2;
 
 // State layouts, as offsets in float planes within a shot slot.
 // Born: float2 pairs (background, scattered).
@@ -101,17 +104,6 @@ __device__ __forceinline__ long long pband_index(int iz, int ix, int M, int nz, 
     return -1;
 }
 
-__device__ __forceinline__ void band_put(const Bands &b, void *base, long long off, float v)
-{
-    if (b.bf16) reinterpret_cast<__nv_bfloat16 *>(base)[off] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float *>(base)[off] = v;
-}
-
-__device__ __forceinline__ float band_get(const Bands &b, const void *base, long long off)
-{
-    if (b.bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[off]);
-    return reinterpret_cast<const float *>(base)[off];
-}
 
 // ---- asynchronous copies (pred = false zero-fills the destination)
 template <class T>
@@ -128,8 +120,9 @@ __device__ __forceinline__ void cpa(T *dst, const T *src, bool pred)
 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
-// Waits until at most PD-1 of this thread's copy groups are pending.
-__device__ __forceinline__ void cp_wait_row() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PD - 1) : "memory"); }
+// Waits until at most PDN-1 of this thread's copy groups are pending.
+template <int PDN>
+__device__ __forceinline__ void cp_wait_row() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PDN - 1) : "memory"); }
 
 template <int M>
 struct Cols {
@@ -141,11 +134,11 @@ struct Cols {
 // Stage ring of the forward kernel: 8 fields of 8-byte slots per thread.
 constexpr int kFwdSlots = 8;
 constexpr size_t kFwdStageSlotBytes = (size_t)kFwdSlots * NTH * 8;
-constexpr size_t kFwdStageBytes = PD * kFwdStageSlotBytes;
+constexpr size_t kFwdStageBytes = PDF * kFwdStageSlotBytes;
 // Stage ring of the adjoint kernel: 5 float2 fields then 9 float fields.
 constexpr int kAdjF2 = 5, kAdjF1 = 9;
 constexpr size_t kAdjStageFloats = (size_t)(2 * kAdjF2 + kAdjF1) * NTH;
-constexpr size_t kAdjStageBytes = PD * kAdjStageFloats * sizeof(float);
+constexpr size_t kAdjStageBytes = PDA * kAdjStageFloats * sizeof(float);
 
 // ---------------------------------------------------------------------------
 // Forward step from n to n+1. BORN: the background and the scattered field as
@@ -240,7 +233,7 @@ __device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
 }
 
 template <int M, bool BORN, bool BANDS, bool HESS, bool WIN>
-__global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
+__global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
 {
     using C = Cols<M>;
     using T = typename FwdT<BORN>::T;
@@ -250,7 +243,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
     __shared__ R sB[NTH];
     __shared__ T sV[NTH];
     __shared__ float sH[HESS ? NTH : 1];
-    extern __shared__ __align__(16) char stages[];   // [PD][kFwdSlots][NTH] x 8 bytes
+    extern __shared__ __align__(16) char stages[];   // [PDF][kFwdSlots][NTH] x 8 bytes
 
     const GridDev &g = a.g;
     const int t = threadIdx.x;
@@ -313,7 +306,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
     }
 
 #pragma unroll
-    for (int j = 0; j < PD - 1; ++j) {
+    for (int j = 0; j < PDF - 1; ++j) {
         if (zstart + j < zc1)
             fwd_issue<M, BORN, WIN>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
                                outcol, pmlxh);
@@ -325,13 +318,13 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
         for (int u = 0; u < W; ++u) {
             const int z = zb + u;
             if (z >= zc1) break;
-            const int zi = z + PD - 1;
+            const int zi = z + PDF - 1;
             if (zi < zc1)
-                fwd_issue<M, BORN, WIN>(stages + ((zi - zstart) % PD) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
+                fwd_issue<M, BORN, WIN>(stages + ((zi - zstart) % PDF) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
                                    colok, vxok, outcol, pmlxh);
             cp_commit();
-            cp_wait_row();
-            const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PD) * kFwdStageSlotBytes);
+            cp_wait_row<PDF>();
+            const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PDF) * kFwdStageSlotBytes);
             const int k = z + M - 1;   // half row of vz computed in this iteration
             const int sl = (u + W - 1) % W;
             P[sl] = cur.p;
@@ -359,7 +352,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                     if (BANDS) {
                         int iz = k - z0;
                         if (ix >= 0 && ix < nx && in_xstrip(iz, M, g.nz))
-                            band_put(a.bands, a.bands.v, bandoff + band_zstrip(iz, ix, M, g.nz, nx), xof(vzn));
+                            band_put(a.bands, 1, slot, bandoff, band_zstrip(iz, ix, M, g.nz, nx), xof(vzn));
                     }
                 }
                 if (HESS) {
@@ -400,7 +393,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                     if (BANDS) {
                         int iz = z - z0;
                         if (iz >= 0 && iz < g.nz && in_xstrip(ix, M, nx))
-                            band_put(a.bands, a.bands.v, bandoff + band_xstrip(iz, ix, M, g.nz, nx), xof(vxn));
+                            band_put(a.bands, 1, slot, bandoff, band_xstrip(iz, ix, M, g.nz, nx), xof(vxn));
                     }
                 }
                 if (HESS) {
@@ -439,7 +432,7 @@ __global__ void __launch_bounds__(NTH, 2) k_fwd2d(const Step2D a)
                 out[oP * pT + cz] = pn;
                 if (BANDS) {
                     long long b = pband_index(z - z0, ix, M, g.nz, nx);
-                    if (b >= 0) band_put(a.bands, a.bands.p, bandoff + b, xof(p0));
+                    if (b >= 0) band_put(a.bands, 0, slot, bandoff, b, xof(p0));
                 }
                 if (HESS) {
                     int iz = z - z0;
@@ -557,7 +550,7 @@ __device__ __forceinline__ AdjRow adj_read(const float *st)
 }
 
 template <int M, bool WIN>
-__global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
+__global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
 {
     using C = Cols<M>;
     constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
@@ -566,7 +559,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     __shared__ float2 sVW[NTH];   // (vx^{n+1/2}, dt*bu_x*lvx - ah_x*lpsi_px), row z
     __shared__ float sVN[NTH];    // vx^{n-1/2}, row z
     __shared__ float sPi[NTH];    // Gx * lvx, row z
-    extern __shared__ __align__(16) float stagef[];   // [PD][kAdjStageFloats]
+    extern __shared__ __align__(16) float stagef[];   // [PDA][kAdjStageFloats]
 
     const GridDev &g = a.g;
     const int t = threadIdx.x;
@@ -600,7 +593,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     const int px = WIN ? shot * a.pml_xstride + x : x;   // x CPML profiles of this shot's window
     const float ahx = pmlxh ? a.pml.ah[2][px] : 0.f, bhx = pmlxh ? a.pml.bh[2][px] : 0.f;
     const float aix = pmlxn ? a.pml.ai[2][px] : 0.f, bix = pmlxn ? a.pml.bi[2][px] : 0.f;
-    const long long bandprev = band_base(a.bands, shot, n - 1);
+    const long long rowprev = band_row(a.bands, shot, n - 1);
     const int src = a.src_cell[shot];
     const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1] : 0.f;
     const float2 *imgs = a.img + slot * plane;   // image accumulators of this slot
@@ -643,7 +636,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
     }
 
 #pragma unroll
-    for (int j = 0; j < PD - 1; ++j) {
+    for (int j = 0; j < PDA - 1; ++j) {
         if (zstart + j < zc1)
             adj_issue<M, WIN>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
                          outcol, pmlxh, pmlxn, xint);
@@ -655,13 +648,13 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
         for (int u = 0; u < W; ++u) {
             const int z = zb + u;
             if (z >= zc1) break;
-            const int zi = z + PD - 1;
+            const int zi = z + PDA - 1;
             if (zi < zc1)
-                adj_issue<M, WIN>(stagef + ((zi - zstart) % PD) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
+                adj_issue<M, WIN>(stagef + ((zi - zstart) % PDA) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
                              colok, vxok, outcol, pmlxh, pmlxn, xint);
             cp_commit();
-            cp_wait_row();
-            const AdjRow cur = adj_read(stagef + ((z - zstart) % PD) * kAdjStageFloats);
+            cp_wait_row<PDA>();
+            const AdjRow cur = adj_read(stagef + ((z - zstart) % PDA) * kAdjStageFloats);
             const int k = z + M - 1;
             const int sl = (u + W - 1) % W;
             PU[sl] = pu_node(z + W - 1, cur.pl, cur.kdr, cur.lpvzr);
@@ -688,7 +681,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                     const int iz = k - z0;
                     if (iz >= 0 && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
                     else if (in_xstrip(iz, M, g.nz))
-                        vn = band_get(a.bands, a.bands.v, bandprev + band_zstrip(iz, ix, M, g.nz, nx));
+                        vn = band_get(a.bands, 1, rowprev, band_zstrip(iz, ix, M, g.nz, nx));
                 }
                 if (own) out2[(A_VZ / 2) * p2 + ck] = make_float2(vn, lv);
             }
@@ -728,7 +721,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                     if (iz >= 0 && iz < g.nz) {
                         if (xint) vxn = cur.v2x.x + dtbu * D.x;
                         else if (in_xstrip(ix, M, nx))
-                            vxn = band_get(a.bands, a.bands.v, bandprev + band_xstrip(iz, ix, M, g.nz, nx));
+                            vxn = band_get(a.bands, 1, rowprev, band_xstrip(iz, ix, M, g.nz, nx));
                     }
                 }
                 if (outcol) out2[(A_VX / 2) * p2 + cz] = make_float2(vxn, lv);
@@ -766,7 +759,7 @@ __global__ void __launch_bounds__(NTH, 2) k_adj2d(const Step2D a)
                         if (cz + x == src) pn -= wsrc;
                     } else {
                         long long b = pband_index(iz, ix, M, g.nz, nx);
-                        if (b >= 0) pn = band_get(a.bands, a.bands.p, bandprev + b);
+                        if (b >= 0) pn = band_get(a.bands, 0, rowprev, b);
                     }
                 }
                 out2[(A_PL / 2) * p2 + cz] = make_float2(pn, lp1 + E.y);

@@ -121,17 +121,6 @@ __device__ __forceinline__ long long pband3(const GridDev &g, int iz, int iy, in
     return -1;
 }
 
-__device__ __forceinline__ void band_put(const Bands &b, void *base, long long off, float v)
-{
-    if (b.bf16) reinterpret_cast<__nv_bfloat16 *>(base)[off] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float *>(base)[off] = v;
-}
-
-__device__ __forceinline__ float band_get(const Bands &b, const void *base, long long off)
-{
-    if (b.bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[off]);
-    return reinterpret_cast<const float *>(base)[off];
-}
 
 __device__ __forceinline__ bool pml_half(const GridDev &g, int d, int i)
 {
@@ -192,7 +181,7 @@ __global__ void __launch_bounds__(256) k3_v(const Step3D a)
         V[cc] = vn;
         if (BANDS) {
             long long b = face_band(g, d, c.z - g.z0, c.y - g.y0, c.x - g.x0);
-            if (b >= 0) band_put(a.bands, a.bands.v, bandoff + b, xof(vn));
+            if (b >= 0) band_put(a.bands, 1, c.slot, bandoff, b, xof(vn));
         }
         if (HESS) {
             float q = bu * xof(G);
@@ -252,7 +241,7 @@ __global__ void __launch_bounds__(256) k3_p(const Step3D a)
     const int iz = c.z - g.z0, iy = c.y - g.y0, ix = c.x - g.x0;
     if (BANDS) {
         long long b = pband3(g, iz, iy, ix);
-        if (b >= 0) band_put(a.bands, a.bands.p, band_base(a.bands, shot, a.n) + b, xof(p0));
+        if (b >= 0) band_put(a.bands, 0, c.slot, band_base(a.bands, shot, a.n), b, xof(p0));
     }
     if (HESS) {
         if (iz >= 0 && iz < g.nz && iy >= 0 && iy < g.ny && ix >= 0 && ix < g.nx) {
@@ -344,7 +333,7 @@ __global__ void __launch_bounds__(256) k3_a(const Step3D a)
     const int shot = a.shot0 + c.slot;
     const float dt = g.dt;
     const bool recon = a.n > 0;
-    const long long bandprev = band_base(a.bands, shot, a.n - 1);
+    const long long rowprev = band_row(a.bands, shot, a.n - 1);
     const float b0 = a.binv[cc];
     const int iz = c.z - g.z0, iy = c.y - g.y0, ix = c.x - g.x0;
     for (int d = 0; d < 3; ++d) {
@@ -379,7 +368,7 @@ __global__ void __launch_bounds__(256) k3_a(const Step3D a)
             if (inner_h) vn = v.x + dtbu * D.x;
             else {
                 long long b = face_band(g, d, iz, iy, ix);
-                if (b >= 0) vn = band_get(a.bands, a.bands.v, bandprev + b);
+                if (b >= 0) vn = band_get(a.bands, 1, rowprev, b);
             }
         }
         V[cc] = make_float2(vn, lv);
@@ -440,7 +429,7 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
             pn -= a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1];
     } else {
         long long b = pband3(g, c.z - g.z0, c.y - g.y0, c.x - g.x0);
-        if (b >= 0) pn = band_get(a.bands, a.bands.p, band_base(a.bands, shot, n - 1) + b);
+        if (b >= 0) pn = band_get(a.bands, 0, band_row(a.bands, shot, n - 1), b);
     }
     const float lpn = lp3 + residual_at(a, shot, cc, n - 1);
     if (in) st[A3_IMK * plane + cc] += E.x * lpn;

@@ -114,6 +114,39 @@ __global__ void k_image_acc(GridDev gm, GridDev g, const float2 *img, int batch,
     }
 }
 
+// One CTA per (field, slot): scale = max |band| / 2^15 of the step's FP32
+// stage, then the scaled values in the 16-bit format.
+__global__ void k_band_pack(Bands b, int shot0, int n)
+{
+    __shared__ float red[32];
+    const int field = blockIdx.x, slot = blockIdx.y;
+    const float *src = b.stage + ((long long)slot * 2 + field) * b.nb;
+    float m = 0.f;
+    for (long long i = threadIdx.x; i < b.nb; i += blockDim.x) m = fmaxf(m, fabsf(src[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const float sc = red[0] > 0.f ? red[0] * (1.0f / 32768.0f) : 1.0f;
+    const float inv = 1.0f / sc;
+    const long long row = band_row(b, shot0 + slot, n);
+    if (threadIdx.x == 0) b.scale[row * 2 + field] = sc;
+    void *dst = field ? b.v : b.p;
+    const long long o = row * b.nb;
+    if (b.fmt == BAND_BF16S) {
+        __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(dst) + o;
+        for (long long i = threadIdx.x; i < b.nb; i += blockDim.x) d[i] = __float2bfloat16_rn(src[i] * inv);
+    } else {
+        __half *d = reinterpret_cast<__half *>(dst) + o;
+        for (long long i = threadIdx.x; i < b.nb; i += blockDim.x) d[i] = __float2half_rn(src[i] * inv);
+    }
+}
+
 // g_kappa = -dt kappa sum_n Q lp, g_rho = (dt / 2) / rho * sum_n (products at
 // the adjacent half nodes); g_Vp = g_kappa - g_rho, g_Ip = g_kappa + g_rho.
 __global__ void k_image_fin(GridDev g, const double2 *acc, const float *kdt, const float *binv,
@@ -363,6 +396,12 @@ cudaError_t launch_image_accumulate(const GridDev &gm, const GridDev &g, const f
 {
     long long n = (long long)gm.nz * gm.ny * gm.nx;
     k_image_acc<<<grid_for(n), NT, 0, s>>>(gm, g, img, batch, shot0, win_x0, win_nx, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_pack(const Bands &b, int batch, int shot0, int n, cudaStream_t s)
+{
+    k_band_pack<<<dim3(2, batch), 512, 0, s>>>(b, shot0, n);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace lsrtm {
@@ -38,18 +39,53 @@ struct Pml {
 //   3D: [x-faces 2*M*nz*ny][y-faces 2*M*nz*nx][z-faces 2*M*ny*nx]
 // The buffers hold steps [t0, t0 + nsteps) of shots [shot0, ...): the band of
 // shot s at step n starts at ((s - shot0) * nsteps + (n - t0)) * NB.
+//
+// Storage: FP32, or 16-bit values with one FP32 scale per band per step
+// (BF16 or FP16). With a 16-bit format the time-step kernels write the step's
+// bands in FP32 into a per-slot stage; k_band_pack then takes the largest
+// magnitude of each band, stores scale = max / 2^15 and the values divided by
+// it (so FP16 keeps its full mantissa over 2^15 .. 2^-24 of the band's
+// maximum), and the reverse pass multiplies back.
+enum BandFmt { BAND_F32 = 0, BAND_BF16S = 1, BAND_F16S = 2 };
+
 struct Bands {
     void *p;              // [shots][nsteps][NB]
     void *v;              // [shots][nsteps][NB]
     long long nb;         // NB
-    int bf16;             // element type: 0 float, 1 bf16
+    int fmt;              // BandFmt
     int shot0, t0, nsteps;
+    float *scale;         // [shots][nsteps][2] (p, v) scales (16-bit formats)
+    float *stage;         // [batch][2][NB] FP32 bands of the current step (16-bit formats)
 };
 
-__host__ __device__ inline long long band_base(const Bands &b, int shot, int n)
+// Band row (shot, step) within the buffers.
+__host__ __device__ inline long long band_row(const Bands &b, int shot, int n)
 {
-    return ((long long)(shot - b.shot0) * b.nsteps + (n - b.t0)) * b.nb;
+    return (long long)(shot - b.shot0) * b.nsteps + (n - b.t0);
 }
+
+__host__ __device__ inline long long band_base(const Bands &b, int shot, int n) { return band_row(b, shot, n) * b.nb; }
+
+#ifdef __CUDACC__
+// Saves value v at slot idx of field (0: p band, 1: normal-v band) of the band
+// starting at base = band_base(shot, n) of batch slot `slot`.
+__device__ __forceinline__ void band_put(const Bands &b, int field, int slot, long long base, long long idx, float v)
+{
+    if (b.fmt == BAND_F32) reinterpret_cast<float *>(field ? b.v : b.p)[base + idx] = v;
+    else b.stage[((long long)slot * 2 + field) * b.nb + idx] = v;
+}
+
+// Value at slot idx of field of the band in row `row` (band_row(shot, n)).
+__device__ __forceinline__ float band_get(const Bands &b, int field, long long row, long long idx)
+{
+    const long long o = row * b.nb + idx;
+    const void *base = field ? b.v : b.p;
+    if (b.fmt == BAND_F32) return reinterpret_cast<const float *>(base)[o];
+    const float sc = b.scale[row * 2 + field];
+    if (b.fmt == BAND_BF16S) return sc * __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[o]);
+    return sc * __half2float(reinterpret_cast<const __half *>(base)[o]);
+}
+#endif
 
 // Receivers grouped by (shot, tile): CSR over shot*ntiles + tile.
 struct TileRecs {
@@ -159,6 +195,9 @@ cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, 
                           float *filt, float *out, int *flag, cudaStream_t st);
 
 // Utility kernels (kernels_util.cu).
+// 16-bit band formats: per slot and field, scale = max|stage| / 2^15 and the
+// scaled values into the band store at row band_row(shot0 + slot, n).
+cudaError_t launch_band_pack(const Bands &b, int batch, int shot0, int n, cudaStream_t s);
 cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
                               float *binv, cudaStream_t s);
 cudaError_t launch_pert_prep(const GridDev &g, const float *dm, const float *kdt,

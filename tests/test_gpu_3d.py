@@ -1,7 +1,7 @@
 """3D operators through the C ABI against the FP64 oracle.
 
 Small grids (both orders, several shots, ragged extents) for Born, migration,
-the FP32 dot tests, the pseudo-Hessian, PSF, CGNR and BF16 bands; and the 3D
+the FP32 dot tests, the pseudo-Hessian, PSF, CGNR and 16-bit bands; and the 3D
 dipping-layer workload at its full grid size (296 x 296 x 168 padded cells,
 order 8, nt = 3000) on two of its shots with BF16 bands: Born records over the
 first steps against the oracle, and the FP32 dot test over the whole time
@@ -87,17 +87,19 @@ def test_3d_pseudo_hessian_psf_and_cg():
     assert rel(cpu(x), xr) < 1e-3
 
 
-def test_3d_bf16_bands():
-    from paper_2508_10405_gb300 import BAND_BF16
+@pytest.mark.parametrize("fmt,tol", [("bf16", 1e-2), ("fp16", 1e-3)])
+def test_3d_16bit_bands(fmt, tol):
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16
     w = li.small_case(**CASES3["o4"])
     rng = np.random.default_rng(3)
     dres = rng.standard_normal((w.geom.nrec_total, w.nt))
     dt = torch.tensor(dres, dtype=torch.float32, device="cuda")
     g32 = cpu(handle(w).adjoint(dt))
-    g16 = cpu(handle(w, band_precision=BAND_BF16).adjoint(dt))
+    g16 = cpu(handle(w, band_precision=BAND_BF16 if fmt == "bf16" else BAND_FP16).adjoint(dt))
     ref = oracle.adjoint(w, dres)
-    print(f"3D BF16 bands: {rel(g16, ref):.3e} vs oracle, {rel(g16, g32):.3e} vs FP32 bands")
-    assert rel(g16, ref) < 1e-2
+    print(f"3D {fmt} bands: {rel(g16, ref):.3e} vs oracle, {rel(g16, g32):.3e} vs FP32 bands")
+    assert rel(g16, ref) < tol
+    assert rel(g16, g32) < tol
 
 
 def test_3d_full_size_two_shots():

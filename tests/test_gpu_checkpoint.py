@@ -153,3 +153,19 @@ def test_checkpoint_autograd_workload_under_cap():
     print(f"checkpoint (batches of {info['batch']}) vs boundary (one batch): {e:.3e}")
     assert e < 1e-6
     hc.close()
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_checkpoint_with_16bit_bands_equals_boundary(fmt):
+    """The recomputed segment bands are packed with the same per-step scales
+    as the boundary mode's, so the 16-bit images agree bit for bit too."""
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, RECON_BOUNDARY, RECON_CHECKPOINT
+    bp = BAND_BF16 if fmt == "bf16" else BAND_FP16
+    for name in ("2d_o8", "3d_o4"):
+        w = li.small_case(**CASES[name])
+        rng = np.random.default_rng(13)
+        d = torch.tensor(rng.standard_normal((w.geom.nrec_total, w.nt)), dtype=torch.float32, device="cuda")
+        gb = handle(w, recon_mode=RECON_BOUNDARY, band_precision=bp).adjoint(d)
+        gc = handle(w, recon_mode=RECON_CHECKPOINT, band_precision=bp, checkpoint_interval=9).adjoint(d)
+        print(f"{name} {fmt}: checkpoint vs boundary {rel(cpu(gc), cpu(gb)):.3e}, bitwise {torch.equal(gc, gb)}")
+        assert rel(cpu(gc), cpu(gb)) < 1e-6
