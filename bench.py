@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps")
     ap.add_argument("--plan", choices=["batched", "plain"], default="batched",
                     help="execution plan of the timed handle")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default z-chunking instead of timing the candidates")
     ap.add_argument("--plain-shots", type=int, default=4,
                     help="shots on which the plain per-shot FP32 plan is timed for the "
                          "per-iteration comparison (0: skip)")
@@ -306,6 +308,7 @@ def main():
     h = Lsrtm.from_workload(w, band_precision=bands,
                             shots_per_batch=args.shots_per_batch,
                             plan=PLAN_PLAIN if args.plan == "plain" else PLAN_BATCHED)
+    tune = None if args.no_autotune else h.autotune()   # untimed setup
     dm_true = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
     d_obs = h.born(dm_true)                 # synthetic observed data (untimed setup)
     h.cg_begin(d_obs)                       # background bands cached here
@@ -418,6 +421,7 @@ def main():
                        "nt": w.nt, "order": w.order, "shots_per_rank": nshot,
                        "receivers_per_shot": float(np.mean(np.diff(w.geom.rec_ptr))),
                        "bands": args.bands, "plan": args.plan,
+                       "autotune": tune,
                        "step": "one CGNR iteration (L + L^T + FP64 Krylov updates)",
                        "s_per_lsrtm_iter": t_max / K,
                        "l2": f"inputs larger than L2 (workspace {workspace / 1e9:.1f} GB per rank)",

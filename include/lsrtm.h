@@ -241,6 +241,22 @@ lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_re
 /* Bytes of device workspace the handle holds. */
 size_t lsrtm_workspace_bytes(const lsrtm_handle *h);
 
+/* Autotuner of the 2D time-step kernels (no counterpart in the paper). A CTA
+ * of the 2D kernels owns a fixed number of x-columns and marches down a
+ * chunk of tzc padded rows; more chunks give more CTAs per shot but repeat
+ * 2M warm-up rows per chunk. The tuner times `steps` Born and migration steps
+ * (0: 16) on the first batch for every split of the padded depth into 1..12
+ * chunks of at least 2M + 8 rows (and the current one), keeps the fastest
+ * and rebuilds the receiver tiling; results do not depend on the choice
+ * (every cell is computed the same way). Captured graphs and the cached
+ * background are dropped. Outputs (each may be NULL):
+ *   *tzc      chosen rows per chunk (0 for 3D handles, which have none)
+ *   ms        [2*ncand] pairs (tzc, ms per Born + migration step); room for
+ *             at least 2*13 doubles
+ *   *ncand    number of candidates timed
+ * Synchronous; it uses the handle's slots as scratch. */
+lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc, double *ms, int *ncand);
+
 /* How the handle reconstructs the background in reverse time (chosen at
  * creation from recon_mode and the memory available):
  *   *mode     LSRTM_RECON_BOUNDARY or LSRTM_RECON_CHECKPOINT (never AUTO)

@@ -29,7 +29,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
-           "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur"]
+           "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune"]
 
 
 class LsrtmError(RuntimeError):
@@ -98,6 +98,7 @@ def load_library(path: str | None = None):
     L.lsrtm_born_static.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp, vp, vp]
     ip = ctypes.POINTER(ctypes.c_int)
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
+    L.lsrtm_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double), ip]
     L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
     L.lsrtm_workspace_bytes.argtypes = [vp]
     L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
@@ -219,6 +220,15 @@ class Lsrtm:
 
     def kernel_launches(self) -> int:
         return int(self._lib.lsrtm_kernel_launches(self._h))
+
+    def autotune(self, steps=16) -> dict:
+        """Times the 2D z-chunk candidates and keeps the fastest;
+        {"tzc": chosen rows per chunk, "ms_per_step": {tzc: ms}}."""
+        self._sync_stream()
+        t, n = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 32)()
+        _check(self._lib.lsrtm_autotune(self._h, int(steps), ctypes.byref(t), ms, ctypes.byref(n)))
+        return {"tzc": t.value, "ms_per_step": {int(ms[2 * i]): ms[2 * i + 1] for i in range(n.value)}}
 
     def reconstruction(self) -> dict:
         """{"mode": RECON_BOUNDARY | RECON_CHECKPOINT, "interval": K, "batch": shots per batch}."""

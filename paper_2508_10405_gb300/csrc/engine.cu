@@ -81,6 +81,8 @@ struct lsrtm_handle {
     float *wav = nullptr;
     int *src_cell = nullptr;
     int *trec_ptr = nullptr;
+    size_t trec_ptr_cap = 0;
+    std::vector<int2> rec_cells_h;   // 2D: per shot (rec_ptr ranges) the receiver cells and rows
     int2 *trec = nullptr;
     TileRecs trv{};
     float src_scale = 0.f;
@@ -884,6 +886,44 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
     return LSRTM_OK;
 }
 
+// Receivers of every 2D shot grouped by the CTA tile (txo columns x tzc rows)
+// that records them: CSR over shot * ntiles + tile, cells sorted within a tile.
+lsrtm_status build_tiles(lsrtm_handle *h)
+{
+    const GridDev &g = h->g;
+    int ntx = (g.Nx + h->txo - 1) / h->txo, ntz = (g.Nz + h->tzc - 1) / h->tzc;
+    int ntiles = ntx * ntz;
+    std::vector<std::vector<int2>> lists((size_t)h->nshot * ntiles);
+    for (int s = 0; s < h->nshot; ++s)
+        for (int r = h->rec_ptr[s]; r < h->rec_ptr[s + 1]; ++r) {
+            int2 e = h->rec_cells_h[r];
+            int z = (int)(e.x / g.rowz), x = (int)(e.x % g.pitch);
+            int t = (z / h->tzc) * ntx + x / h->txo;
+            lists[(size_t)s * ntiles + t].push_back(e);
+        }
+    std::vector<int> ptr(lists.size() + 1, 0);
+    std::vector<int2> flat;
+    flat.reserve(h->nrec_total);
+    for (size_t i = 0; i < lists.size(); ++i) {
+        auto &L = lists[i];
+        std::stable_sort(L.begin(), L.end(), [](int2 a, int2 b) { return a.x < b.x; });
+        flat.insert(flat.end(), L.begin(), L.end());
+        ptr[i + 1] = (int)flat.size();
+    }
+    if (ptr.size() > h->trec_ptr_cap) {
+        CHECK(dalloc_t(h, &h->trec_ptr, ptr.size()));
+        h->trec_ptr_cap = ptr.size();
+    }
+    CU(cudaMemcpyAsync(h->trec_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
+    if (!flat.empty())
+        CU(cudaMemcpyAsync(h->trec, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice, h->work));
+    CU(cudaStreamSynchronize(h->work));
+    h->trv.ptr = h->trec_ptr;
+    h->trv.rec = h->trec;
+    h->trv.ntiles = ntiles;
+    return LSRTM_OK;
+}
+
 lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
 {
     const GridDev &g = h->g;
@@ -953,40 +993,19 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         CU(cudaStreamSynchronize(h->work));
         return LSRTM_OK;
     }
-    int ntx = (g.Nx + h->txo - 1) / h->txo, ntz = (g.Nz + h->tzc - 1) / h->tzc;
-    int ntiles = ntx * ntz;
-    std::vector<std::vector<int2>> lists((size_t)h->nshot * ntiles);
+    h->rec_cells_h.resize(h->nrec_total);
     for (int s = 0; s < h->nshot; ++s)
         for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
             long long k = geo->rec_idx[r];
             if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "receiver outside the interior grid");
             long long cell = pad_cell(k, s);
             if (cell < 0) return fail(LSRTM_ERR_GEOMETRY, "receiver outside its shot's aperture window");
-            int z = (int)(cell / g.rowz), x = (int)(cell % g.pitch);
-            int t = (z / h->tzc) * ntx + x / h->txo;
-            lists[(size_t)s * ntiles + t].push_back(make_int2((int)cell, r));
+            h->rec_cells_h[r] = make_int2((int)cell, r);
         }
-    std::vector<int> ptr(lists.size() + 1, 0);
-    std::vector<int2> flat;
-    flat.reserve(h->nrec_total);
-    for (size_t i = 0; i < lists.size(); ++i) {
-        auto &L = lists[i];
-        std::stable_sort(L.begin(), L.end(), [](int2 a, int2 b) { return a.x < b.x; });
-        flat.insert(flat.end(), L.begin(), L.end());
-        ptr[i + 1] = (int)flat.size();
-    }
     CHECK(dalloc_t(h, &h->src_cell, src.size()));
-    CHECK(dalloc_t(h, &h->trec_ptr, ptr.size()));
-    CHECK(dalloc_t(h, &h->trec, std::max<size_t>(flat.size(), 1)));
     CU(cudaMemcpyAsync(h->src_cell, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
-    CU(cudaMemcpyAsync(h->trec_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, h->work));
-    if (!flat.empty())
-        CU(cudaMemcpyAsync(h->trec, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice, h->work));
-    CU(cudaStreamSynchronize(h->work));
-    h->trv.ptr = h->trec_ptr;
-    h->trv.rec = h->trec;
-    h->trv.ntiles = ntiles;
-    return LSRTM_OK;
+    CHECK(dalloc_t(h, &h->trec, std::max<size_t>(h->rec_cells_h.size(), 1)));
+    return build_tiles(h);
 }
 
 // Aperture windows: validates them, keeps host and device copies and turns
@@ -1617,6 +1636,88 @@ lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_re
     if (flag) return fail(LSRTM_ERR_NONFINITE, "deblurring normal equations not positive definite (eps too small "
                                               "or non-finite images); those filters are set to zero");
     return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms_out, int *ncand_out)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    if (h->g.ndim != 2) {   // the 3D kernels have no z-chunk to choose
+        if (tzc_out) *tzc_out = 0;
+        if (ncand_out) *ncand_out = 0;
+        return LSRTM_OK;
+    }
+    CHECK(begin_call(h));
+    const GridDev &g = h->g;
+    // candidates: the padded depth split into 1..12 chunks of at least 2M + 8 rows
+    std::vector<int> cand;
+    for (int nchunk = 1; nchunk <= 12; ++nchunk) {
+        int t = (g.Nz + nchunk - 1) / nchunk;
+        if (t < 2 * g.M + 8) break;
+        if (cand.empty() || cand.back() != t) cand.push_back(t);
+    }
+    if (std::find(cand.begin(), cand.end(), h->tzc) == cand.end()) cand.push_back(h->tzc);
+    int maxsteps = g.nt - 1;
+    if (h->ckpt) maxsteps = std::min(maxsteps, h->ck_K);
+    steps = std::max(1, std::min(steps > 0 ? steps : 16, maxsteps));
+    const int bs = batch_size(h, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_tzc = h->tzc;
+    std::vector<double> times;
+    lsrtm_status st = LSRTM_OK;
+    for (int c : cand) {
+        h->tzc = c;
+        if ((st = build_tiles(h)) != LSRTM_OK) break;
+        if ((st = zero_slots(h, bs)) != LSRTM_OK) break;
+        if ((st = gather_model(h, 0, bs, true)) != LSRTM_OK) break;
+        Step2D a = step_args(h, 0);
+        double ms = 0.0;
+        for (int rep = 0; rep < 2 && st == LSRTM_OK; ++rep) {   // first pass warms up
+            cudaEventRecord(e0, h->work);
+            for (int i = 0; i < steps; ++i) {
+                a.n = i;
+                a.in = h->st[i & 1];
+                a.out = h->st[(i + 1) & 1];
+                launch_fwd2d(a, bs, true, false, false, h->work);
+                a.n = steps - i;
+                launch_adj2d(a, bs, h->work);
+            }
+            cudaEventRecord(e1, h->work);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) st = fail(LSRTM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            ms = f / steps;
+        }
+        h->launches += 4LL * steps;
+        times.push_back(ms);
+        if (st != LSRTM_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_tzc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tzc = best_tzc;
+    lsrtm_status s2 = build_tiles(h);
+    if (st == LSRTM_OK) st = s2;
+    // graphs captured with the previous chunking are stale
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    h->bg_cached = false;
+    if (st != LSRTM_OK) return st;
+    if (tzc_out) *tzc_out = best_tzc;
+    if (ncand_out) *ncand_out = (int)cand.size();
+    if (ms_out)
+        for (size_t i = 0; i < times.size(); ++i) {
+            ms_out[2 * i] = cand[i];
+            ms_out[2 * i + 1] = times[i];
+        }
+    return end_call(h, true);
 }
 
 lsrtm_status lsrtm_reconstruction(const lsrtm_handle *h, int *mode, int *interval, int *batch)
