@@ -31,6 +31,11 @@ constexpr int PDF = 4;   // depth of the asynchronous row pipeline (forward)
 constexpr int PDA = 4;   // depth of the asynchronous row pipeline (adjoint)
 constexpr int kFwdMinBlocks = 2;   // resident CTAs per SM the register budget targets
 constexpr int kAdjMinBlocks = 2;
+// The z-marches are unrolled by 2M / k*GroupDiv rows and shift their register
+// rings after every group: a full 2M-row unroll made the migration loop body
+// large enough to miss in the instruction cache.
+constexpr int kAdjGroupDiv = 4;
+constexpr int kFwdGroupDiv = 2;
 
 // State layouts, as offsets in float planes within a shot slot.
 // Born: float2 pairs (background, scattered).
@@ -281,10 +286,13 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
     constexpr int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
     constexpr int oPVX = BORN ? B_PVX / 2 : G_PVX, oPVZ = BORN ? B_PVZ / 2 : G_PVZ;
 
-    T P[W], VZ[W];
-    float HZ[HESS ? W : 1];
+    // z rings, shifted by U entries after every group of U rows (entry u + m
+    // holds row z + m of P, or the half-row value written m - W + 1 rows earlier)
+    constexpr int U = W / kFwdGroupDiv > 0 ? W / kFwdGroupDiv : 1, RL = W + U - 1;
+    T P[RL], VZ[RL];
+    float HZ[HESS ? RL : 1];
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
+    for (int j = 0; j < RL; ++j) {
         P[j] = zero_<T>();
         VZ[j] = zero_<T>();
         if (HESS) HZ[j] = 0.f;
@@ -313,9 +321,9 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
         cp_commit();
     }
 
-    for (int zb = zstart; zb < zc1; zb += W) {
+    for (int zb = zstart; zb < zc1; zb += U) {
 #pragma unroll
-        for (int u = 0; u < W; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int z = zb + u;
             if (z >= zc1) break;
             const int zi = z + PDF - 1;
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             cp_wait_row<PDF>();
             const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PDF) * kFwdStageSlotBytes);
             const int k = z + M - 1;   // half row of vz computed in this iteration
-            const int sl = (u + W - 1) % W;
+            const int sl = u + W - 1;
             P[sl] = cur.p;
             // ---- vz at half row k (column-local)
             const float buz = 0.5f * (xof(br_old) + xof(cur.br1));
@@ -337,8 +345,8 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             if (colok && k >= 0 && k < g.Nz) {
                 const long long ck = (long long)k * pitch;
                 const bool own = outcol && k >= zc0 && k < zc1;
-                T G = stencil<M, T>(g.cz, [&](int l) { return P[(u + M - 1 + l) % W]; },
-                                    [&](int l) { return P[(u + M - l) % W]; });
+                T G = stencil<M, T>(g.cz, [&](int l) { return P[u + M - 1 + l]; },
+                                    [&](int l) { return P[u + M - l]; });
                 if ((k <= z0 - 2) || (k >= z1)) {
                     T ps = fma_(a.pml.bh[0][k], cur.psz, mul_(a.pml.ah[0][k], G));
                     if (own) out[oPPZ * pT + ck] = ps;
@@ -408,8 +416,8 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             // ---- row z: pressure on the output columns
             if (outcol) {
                 T qx = stencil<M, T>(g.cx, [&](int l) { return sV[t + l - 1]; }, [&](int l) { return sV[t - l]; });
-                T qz = stencil<M, T>(g.cz, [&](int l) { return VZ[(u + M + l - 1) % W]; },
-                                     [&](int l) { return VZ[(u + M - l) % W]; });
+                T qz = stencil<M, T>(g.cz, [&](int l) { return VZ[u + M + l - 1]; },
+                                     [&](int l) { return VZ[u + M - l]; });
                 if (pmlxn) {
                     T ps = fma_(bix, psiv[oPVX * pT + cz], mul_(aix, qx));
                     psiv[oPVX * pT + cz] = ps;
@@ -438,13 +446,18 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
                     int iz = z - z0;
                     if (iz >= 0 && iz < g.nz && ix >= 0 && ix < nx) {
                         float bx0 = xof(cur.brz);
-                        float hr = 0.5f * ((sH[t] + sH[t - 1]) + (HZ[(u + M) % W] + HZ[(u + M - 1) % W])) /
-                                   (bx0 * bx0);
+                        float hr = 0.5f * ((sH[t] + sH[t - 1]) + (HZ[u + M] + HZ[u + M - 1])) / (bx0 * bx0);
                         float kq = kd * xof(Q) / dt;
                         a.hess[slot * plane + cz + xc] += dt * (hr + kq * kq);
                     }
                 }
             }
+        }
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            P[j] = P[j + U];
+            VZ[j] = VZ[j + U];
+            if (HESS) HZ[j] = HZ[j + U];
         }
     }
 
@@ -599,11 +612,14 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
     const float2 *imgs = a.img + slot * plane;   // image accumulators of this slot
     float2 *img = a.img + slot * plane + xc;
 
-    // z rings: node rows (slot (r - zstart) % W), half rows (slot (k - zstart + M) % W)
-    float2 PU[W], VW[W];
-    float VN[W], PIZ[W];
+    // z rings, shifted by U entries after every group of U rows: at row u of a
+    // group, entry u + m holds node row z + m (PU) or the half-row value
+    // written m - W + 1 rows earlier (VW, VN, PIZ), m = 0 .. W - 1
+    constexpr int U = W / kAdjGroupDiv > 0 ? W / kAdjGroupDiv : 1, RL = W + U - 1;
+    float2 PU[RL], VW[RL];
+    float VN[RL], PIZ[RL];
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
+    for (int j = 0; j < RL; ++j) {
         PU[j] = make_float2(0.f, 0.f);
         VW[j] = make_float2(0.f, 0.f);
         VN[j] = 0.f;
@@ -643,9 +659,9 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
         cp_commit();
     }
 
-    for (int zb = zstart; zb < zc1; zb += W) {
+    for (int zb = zstart; zb < zc1; zb += U) {
 #pragma unroll
-        for (int u = 0; u < W; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int z = zb + u;
             if (z >= zc1) break;
             const int zi = z + PDA - 1;
@@ -656,7 +672,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
             cp_wait_row<PDA>();
             const AdjRow cur = adj_read(stagef + ((z - zstart) % PDA) * kAdjStageFloats);
             const int k = z + M - 1;
-            const int sl = (u + W - 1) % W;
+            const int sl = u + W - 1;
             PU[sl] = pu_node(z + W - 1, cur.pl, cur.kdr, cur.lpvzr);
             const float buz = 0.5f * (bz_old + cur.bz);
             bz_old = cur.bz;
@@ -666,8 +682,8 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 const long long ck = (long long)k * pitch;
                 const bool own = outcol && k >= zc0 && k < zc1;
                 // (Gz, du/dz)
-                const float2 D = stencil<M, float2>(g.cz, [&](int l) { return PU[(u + M - 1 + l) % W]; },
-                                                    [&](int l) { return PU[(u + M - l) % W]; });
+                const float2 D = stencil<M, float2>(g.cz, [&](int l) { return PU[u + M - 1 + l]; },
+                                                    [&](int l) { return PU[u + M - l]; });
                 const float lv = cur.v2z.y + D.y;
                 const float dtbu = dt * buz;
                 wz = dtbu * lv;
@@ -736,20 +752,20 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 // (Q_n, D- w) along x and z
                 const float2 Ex = stencil<M, float2>(g.cx, [&](int l) { return sVW[t + l - 1]; },
                                                      [&](int l) { return sVW[t - l]; });
-                const float2 Ez = stencil<M, float2>(g.cz, [&](int l) { return VW[(u + M + l - 1) % W]; },
-                                                     [&](int l) { return VW[(u + M - l) % W]; });
+                const float2 Ez = stencil<M, float2>(g.cz, [&](int l) { return VW[u + M + l - 1]; },
+                                                     [&](int l) { return VW[u + M - l]; });
                 const float2 E = add_(Ex, Ez);
                 float qn = 0.f;
                 if (recon)
                     qn = stencil<M, float>(g.cx, [&](int l) { return sVN[t + l - 1]; }, [&](int l) { return sVN[t - l]; }) +
-                         stencil<M, float>(g.cz, [&](int l) { return VN[(u + M + l - 1) % W]; },
-                                           [&](int l) { return VN[(u + M - l) % W]; });
+                         stencil<M, float>(g.cz, [&](int l) { return VN[u + M + l - 1]; },
+                                           [&](int l) { return VN[u + M - l]; });
                 const int iz = z - z0;
                 const bool inner = xint && iz >= 0 && iz < g.nz;
                 if (inner) {
                     float2 acc = cur.img;
                     acc.x += E.x * lp1;
-                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[(u + M) % W] + PIZ[(u + M - 1) % W]);
+                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[u + M] + PIZ[u + M - 1]);
                     img[cz] = acc;
                 }
                 float pn = 0.f;
@@ -766,6 +782,13 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 if (pmlxn) outf[A_LPVX * plane + cz] = bix * (cur.lpsvx - kl);
                 if ((z <= z0 - 1) || (z >= z1)) outf[A_LPVZ * plane + cz] = a.pml.bi[0][z] * (cur.lpsvz - kl);
             }
+        }
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            PU[j] = PU[j + U];
+            VW[j] = VW[j + U];
+            VN[j] = VN[j + U];
+            PIZ[j] = PIZ[j + U];
         }
     }
 
