@@ -28,9 +28,9 @@ namespace {
 
 constexpr int NTH = kThreads2D;
 constexpr int PDF = 4;   // depth of the asynchronous row pipeline (forward)
-constexpr int PDA = 4;   // depth of the asynchronous row pipeline (adjoint)
+constexpr int PDA = 3;   // depth of the asynchronous row pipeline (adjoint; 3 CTAs per SM fit)
 constexpr int kFwdMinBlocks = 2;   // resident CTAs per SM the register budget targets
-constexpr int kAdjMinBlocks = 2;
+constexpr int kAdjMinBlocks = 3;
 // The z-marches are unrolled by 2M / k*GroupDiv rows and shift their register
 // rings after every group: a full 2M-row unroll made the migration loop body
 // large enough to miss in the instruction cache.
