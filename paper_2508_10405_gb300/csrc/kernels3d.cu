@@ -11,7 +11,11 @@
 //            and the kappa image of step n-1).
 // Stencil neighbours come through L1/L2. As in 2D, a background field and its
 // partner (scattered or adjoint) are float2 pairs, so the stencils run as
-// packed FFMA2.
+// packed FFMA2. The adjoint fields are kept pre-scaled by the coefficient
+// their neighbours' stencils apply: the node pair holds (p, mu) with
+// mu = dt kappa lambda_p and the half-node pairs (v_d, w_d) with
+// w_d = dt b_d lambda_v,d, so a stencil tap is one pair load; each stage
+// recovers its own lambda with one division.
 #include <algorithm>
 #include <type_traits>
 
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(256) k3_adj_init(const Step3D a)
     float2 *S = reinterpret_cast<float2 *>(st);
     const int shot = a.shot0 + c.slot;
     const float lp1 = residual_at(a, shot, cc, g.nt - 1);
-    S[(A3_PL / 2) * plane + cc].y = lp1;
+    S[(A3_PL / 2) * plane + cc].y = a.kdt[cc] * lp1;   // mu
     if (interior(g, c)) {
         float Q = 0.f;
         for (int d = 0; d < 3; ++d) {
@@ -343,20 +347,19 @@ __global__ void __launch_bounds__(256) k3_a(const Step3D a)
         // (p^n, kdt*lp - ai_d (lpsi_vd - kdt*lp)) at a node along d
         auto pu = [&](int j, long long cj) -> float2 {
             if (j < 0 || j >= N) return make_float2(0.f, 0.f);
-            const float2 pl = PL[cj];
-            const float kl = a.kdt[cj] * pl.y;
-            float u = kl;
-            if (pml_node(g, d, j)) u -= a.pml.ai[d][j] * (lpv[cj] - kl);
+            const float2 pl = PL[cj];   // (p, mu)
+            float u = pl.y;
+            if (pml_node(g, d, j)) u -= a.pml.ai[d][j] * (lpv[cj] - pl.y);
             return make_float2(pl.x, u);
         };
         const float2 D = diff<M, float2>(cdir(g, d), [&](int l) {
             return sub_(pu(i + l, cc + l * sd), pu(i + 1 - l, cc + (1 - l) * sd));
         });   // (G_d, du/dd)
         float2 *V = S + ((A3_V + 2 * d) / 2) * plane;
-        const float2 v = V[cc];
-        const float lv = v.y + D.y;
+        const float2 v = V[cc];   // (v, w)
         const float b1 = (i + 1 < N) ? a.binv[cc + sd] : b0;
         const float dtbu = dt * 0.5f * (b0 + b1);
+        const float lv = v.y / dtbu + D.y;
         if (pml_half(g, d, i)) {
             float *lpp = st + (A3_LPP + d) * plane;
             lpp[cc] = a.pml.bh[d][i] * lpp[cc] - dtbu * lv;
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(256) k3_a(const Step3D a)
                 if (b >= 0) vn = band_get(a.bands, 1, rowprev, b);
             }
         }
-        V[cc] = make_float2(vn, lv);
+        V[cc] = make_float2(vn, dtbu * lv);
     }
 }
 
@@ -391,11 +394,11 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
     float *st = a.st + c.slot * a.sstride;
     float2 *S = reinterpret_cast<float2 *>(st);
     const int shot = a.shot0 + c.slot;
-    const float dt = g.dt;
     const int n = a.n;
     float2 *PL = S + (A3_PL / 2) * plane;
-    const float2 pl = PL[cc];
+    const float2 pl = PL[cc];   // (p, mu)
     const float kd = a.kdt[cc];
+    const float lp = pl.y / kd;
     float2 E = make_float2(0.f, 0.f);   // (D- . v^{n-1/2}, D- . w)
     for (int d = 0; d < 3; ++d) {
         const int i = coord(c, d), N = extent(g, d);
@@ -405,10 +408,8 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
         // (v^{n-1/2}, dt bu lambda_v - ah lambda_psi_p) at a half node along d
         auto vw = [&](int j, long long cj) -> float2 {
             if (j < 0 || j >= N) return make_float2(0.f, 0.f);
-            const float2 v = V[cj];
-            const float bj = a.binv[cj];
-            const float bj1 = (j + 1 < N) ? a.binv[cj + sd] : bj;
-            float w = dt * 0.5f * (bj + bj1) * v.y;
+            const float2 v = V[cj];   // (v, w)
+            float w = v.y;
             if (pml_half(g, d, j)) w -= a.pml.ah[d][j] * lpp[cj];
             return make_float2(v.x, w);
         };
@@ -417,10 +418,10 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
                  }));
         if (pml_node(g, d, i)) {
             float *lpv = st + (A3_LPV + d) * plane;
-            lpv[cc] = a.pml.bi[d][i] * (lpv[cc] - kd * pl.y);
+            lpv[cc] = a.pml.bi[d][i] * (lpv[cc] - pl.y);
         }
     }
-    const float lp3 = pl.y + E.y;
+    const float lp3 = lp + E.y;
     const bool in = interior(g, c);
     float pn = 0.f;
     if (in) {
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(256) k3_b(const Step3D a)
     }
     const float lpn = lp3 + residual_at(a, shot, cc, n - 1);
     if (in) st[A3_IMK * plane + cc] += E.x * lpn;
-    PL[cc] = make_float2(pn, lpn);
+    PL[cc] = make_float2(pn, kd * lpn);
 }
 
 // lambda_psi_p memories hold S2^T values before the b_h scaling of S1^T; the
