@@ -125,6 +125,17 @@ __device__ __forceinline__ void cpa(T *dst, const T *src, bool pred)
 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
+// Copy only where the field is used (the forward kernel's CPML memories): the
+// stage slot keeps stale data elsewhere, which no consumer reads (every
+// consumer tests the same condition), and warps outside the strips issue
+// nothing. (In the migration kernel the extra branches cost more registers
+// than the skipped copies save.)
+template <class T>
+__device__ __forceinline__ void cpa_if(T *dst, const T *src, bool pred)
+{
+    if (pred) cpa(dst, src, true);
+}
+
 // Waits until at most PDN-1 of this thread's copy groups are pending.
 template <int PDN>
 __device__ __forceinline__ void cp_wait_row() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PDN - 1) : "memory"); }
@@ -209,9 +220,9 @@ __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float
     constexpr size_t F = (size_t)NTH * 8;   // bytes between field rows of a stage
     cpa(reinterpret_cast<T *>(sl + 0 * F), fin + oP * pT + cr, okr);
     cpa(reinterpret_cast<T *>(sl + 1 * F), fin + oVZ * pT + ck, okk);
-    cpa(reinterpret_cast<T *>(sl + 2 * F), fin + oPPZ * pT + ck, pz);
+    cpa_if(reinterpret_cast<T *>(sl + 2 * F), fin + oPPZ * pT + ck, pz);
     cpa(reinterpret_cast<T *>(sl + 3 * F), fin + oVX * pT + cz, okv);
-    cpa(reinterpret_cast<T *>(sl + 4 * F), fin + oPPX * pT + cz, okv && pmlxh);
+    cpa_if(reinterpret_cast<T *>(sl + 4 * F), fin + oPPX * pT + cz, okv && pmlxh);
     cpa(reinterpret_cast<R *>(sl + 5 * F), br + ck1, okk1);
     cpa(reinterpret_cast<R *>(sl + 6 * F), br + cz, okz);
     cpa(reinterpret_cast<K *>(sl + 7 * F), kk + cz, oko);
