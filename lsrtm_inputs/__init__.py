@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "Geometry", "preset", "PRESETS", "ricker", "gardner_rho",
-    "gaussian_blobs", "small_case", "image_pair",
+    "gaussian_blobs", "small_case", "image_pair", "psf_images",
 ]
 
 
@@ -417,3 +417,41 @@ def image_pair(nz: int = 300, nx: int = 2000, seed: int = 5, nrefl: int = 40,
         remig[q] = ((1.0 - depth) * b1 + depth * b3) * (1.0 - 0.5 * depth)
         remig[q] += noise * np.abs(remig[q]).max() * rng.standard_normal((nz, nx))
     return m, remig
+
+
+def psf_images(nz: int = 300, nx: int = 2000, spacing: int = 20, seed: int = 9,
+               cross: float = 0.3) -> tuple[np.ndarray, np.ndarray]:
+    """Synthetic PSF images shaped like the response of a spike comb (nodes at
+    spacing//2 + k*spacing along both axes) for the two comb parameters.
+
+    Returns (psf_vp, psf_ip), each [2, nz, nx]: around every node, plane q of
+    the comb-in-parameter-j image holds a tilted, band-limited blob (a
+    Mexican hat across a dipping axis times a Gaussian along it) whose width
+    grows and amplitude falls with depth, with seeded per-node jitter of
+    amplitude, width and tilt; off-diagonal planes (q != j) carry `cross`
+    times an odd-symmetric blob. Values decay to ~1e-3 within spacing/2 of the
+    node."""
+    rng = np.random.default_rng(seed)
+    zk = np.arange(spacing // 2, nz, spacing)
+    xk = np.arange(spacing // 2, nx, spacing)
+    out = [np.zeros((2, nz, nx)), np.zeros((2, nz, nx))]
+    r = max(1, spacing // 2)
+    dz, dx = np.meshgrid(np.arange(-r, r + 1, dtype=np.float64),
+                         np.arange(-r, r + 1, dtype=np.float64), indexing="ij")
+    for z in zk:
+        depth = z / max(nz - 1, 1)
+        for x in xk:
+            for j in range(2):
+                for q in range(2):
+                    sig = (0.08 + 0.08 * depth) * spacing * rng.uniform(0.85, 1.15)
+                    tilt = rng.uniform(-0.4, 0.4)
+                    amp = (1.0 - 0.6 * depth) * rng.uniform(0.8, 1.2)
+                    u = (dz * math.cos(tilt) + dx * math.sin(tilt)) / sig
+                    v = (-dz * math.sin(tilt) + dx * math.cos(tilt)) / (2.0 * sig)
+                    blob = (1.0 - u * u) * np.exp(-0.5 * (u * u + v * v))
+                    if q != j:
+                        blob = cross * u * np.exp(-0.5 * (u * u + v * v))
+                    z0, z1 = max(0, z - r), min(nz, z + r + 1)
+                    x0, x1 = max(0, x - r), min(nx, x + r + 1)
+                    out[j][q, z0:z1, x0:x1] += amp * blob[z0 - z + r:z1 - z + r, x0 - x + r:x1 - x + r]
+    return out[0], out[1]
