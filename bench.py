@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--plain-shots", type=int, default=4,
                     help="shots on which the plain per-shot FP32 plan is timed for the "
                          "per-iteration comparison (0: skip)")
+    ap.add_argument("--psf-cg", action="store_true",
+                    help="time the image-domain CGNR with the interpolated PSF Hessian (App. D) "
+                         "on the marine-line image instead of the data-domain iteration")
+    ap.add_argument("--psf-iters", type=int, default=100, help="CGNR iterations per --psf-cg step")
     return ap.parse_args()
 
 
@@ -219,8 +223,173 @@ def workload(args):
     return w
 
 
+# Image-domain CGNR with the interpolated PSF Hessian (App. D): the marine-line
+# image (300 x 2000, comb spacing 20 as in the deblurring experiment), 19 x 19
+# node windows, both parameters (2 x 2 blocks).
+PSF_CG = {"nz": 300, "nx": 2000, "spacing": 20, "half": 9, "mask": 3}
+# FP32 peak of the CUDA cores: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def psf_cg_inputs(nz=None, nx=None):
+    c = PSF_CG
+    nz, nx = nz or c["nz"], nx or c["nx"]
+    pv, pi = li.psf_images(nz, nx, c["spacing"], seed=9)
+    m_rtm, _ = li.image_pair(nz, nx, seed=5)
+    return pv, pi, m_rtm
+
+
+def psf_apply_flops(nz, nx, half, mask):
+    """Algorithmic FP32 flops of one application of H (or H^T): per pixel, window
+    offset and parameter block, the interpolated entry (4 multiply-adds over
+    the corners) and its product with the input (1 multiply-add)."""
+    nblocks = 4 if mask == 3 else 1
+    return float(nz) * nx * (2 * half + 1) ** 2 * nblocks * 10.0
+
+
+def psf_cpu_sample(seconds, niter_full):
+    """The FP64 oracle's CGNR on a crop of the image (origin on the node grid),
+    as many iterations as fit in about `seconds`; scaled to full-image
+    iterations/s by the pixel ratio (the cost is linear in the pixels)."""
+    from oracle import psf_hessian as ph
+    c = PSF_CG
+    zc, xc = 60, 400
+    pv, pi, m = psf_cg_inputs()
+    pv, pi, m = pv[:, :zc, :xc], pi[:, :zc, :xc], m[:, :zc, :xc]
+    bl = ph.block_patches(pv, pi, c["spacing"], c["half"], c["mask"])
+    t0 = time.perf_counter()
+    ph.cgnr(bl, c["spacing"], c["half"], m, 1, c["mask"])
+    per = max(time.perf_counter() - t0, 1e-3)
+    n = int(max(1, min(niter_full, seconds / per)))
+    t0 = time.perf_counter()
+    ph.cgnr(bl, c["spacing"], c["half"], m, n, c["mask"])
+    t = time.perf_counter() - t0
+    ratio = (zc * xc) / float(c["nz"] * c["nx"])
+    desc = (f"oracle CGNR, {n} iterations on a {zc} x {xc} crop of the {c['nz']} x {c['nx']} image "
+            f"(FP64 numpy, one thread), scaled by the pixel ratio {ratio:.3f}")
+    return n / t * ratio, 1, desc, t
+
+
+def psf_cg_bench(args, rank, world, local):
+    import torch
+    from paper_2508_10405_gb300 import Lsrtm, binding
+    c = PSF_CG
+    nz, nx, s, half, mask = c["nz"], c["nx"], c["spacing"], c["half"], c["mask"]
+    niter, K, W = args.psf_iters, args.steps, args.warmup
+    wk = li.small_case(nz=nz, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+    h = Lsrtm.from_workload(wk)
+    pv, pi, m = psf_cg_inputs()
+    pv_d, pi_d, m_d = (torch.tensor(a, dtype=torch.float32, device="cuda") for a in (pv, pi, m))
+    for _ in range(W):
+        h.psf_cg(m_d, pv_d, pi_d, niter, s, half, mask)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = h.kernel_launches()
+    t_steps = []
+    for _ in range(K):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dm, mis = h.psf_cg(m_d, pv_d, pi_d, niter, s, half, mask)
+        e1.record()
+        torch.cuda.synchronize()
+        t_steps.append(e0.elapsed_time(e1) / 1e3)
+    launches = h.kernel_launches() - l0
+    # the application kernel alone: H and H^T calls back to back (each call
+    # also builds the node windows, a few microseconds)
+    reps = 40
+    y = torch.empty_like(m_d)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(reps):
+        h.psf_hessian(m_d, pv_d, pi_d, s, half, r % 2 == 1, mask, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    apply_s = e0.elapsed_time(e1) / 1e3 / reps
+    flops = psf_apply_flops(nz, nx, half, mask)
+    achieved = flops / apply_s / 1e12
+    t_step = float(np.sum(t_steps)) / K
+    value = niter * world / t_step
+    # end to end through the C ABI with pinned host buffers
+    hb = [torch.tensor(a, dtype=torch.float32).pin_memory() for a in (pv, pi, m)]
+    dm_h = torch.empty(m.shape, dtype=torch.float32).pin_memory()
+    misb = (binding.ctypes.c_double * (niter + 1))()
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(K, 1)):
+        t0 = time.perf_counter()
+        rc = h._lib.lsrtm_psf_cg(h._h, binding._ptr(hb[0]), binding._ptr(hb[1]), s, half, mask,
+                                 binding._ptr(hb[2]), binding._ptr(dm_h), niter, misb)
+        te.append(time.perf_counter() - t0)
+        assert rc == 0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, threads, desc, _ = psf_cpu_sample(args.cpu_seconds, niter)
+        cpu = {"value": val, "unit": "iter/s", "cores": threads, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": "PSF-Hessian CGNR iterations/s", "value": value, "unit": "iter/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"marine-line image {nz} x {nx}, comb spacing {s}, "
+                                   f"{2 * half + 1} x {2 * half + 1} node windows, two parameters",
+                       "niter": niter, "step": f"one image-domain CGNR solve of {niter} iterations "
+                                               "(node windows built, 2 niter + 1 applications of H or H^T, "
+                                               "FP64 Krylov scalars)",
+                       "final_misfit": float(mis[-1]),
+                       "l2": "L2 flushed (256 MB write) before every timed step; the solve's working "
+                             "set (about 40 MB) is L2-resident within a step"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_psfh_apply<3>", "flops_per_launch": flops,
+                         "avg_launch_ms": apply_s * 1e3,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no tensor cores)"},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": niter / float(np.mean(te)), "unit": "iter/s",
+                    "h2d_bytes_per_step": int(sum(a.numel() * 4 for a in hb)),
+                    "d2h_bytes_per_step": int(dm_h.numel() * 4 + 8 * (niter + 1)),
+                    "calls": "lsrtm_psf_cg with pinned host buffers"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
+def psf_reference_arm(args):
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        psf_cpu_sample(min(args.cpu_seconds, 5.0) / 4, args.psf_iters)
+    vals, descs, ts = [], [], []
+    for _ in range(K):
+        v, threads, desc, t = psf_cpu_sample(min(args.cpu_seconds, 30.0), args.psf_iters)
+        vals.append(v)
+        descs.append(desc)
+        ts.append(t)
+    val = float(np.mean(vals))
+    c = PSF_CG
+    line = {
+        "impl": "reference", "metric": "PSF-Hessian CGNR iterations/s", "value": val, "unit": "iter/s",
+        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": args.psf_iters / val * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"marine-line image {c['nz']} x {c['nx']}, comb spacing {c['spacing']}, "
+                               f"{2 * c['half'] + 1} x {2 * c['half'] + 1} node windows, two parameters",
+                   "niter": args.psf_iters, "sample": descs[-1]},
+        "cpu_baseline": {"value": val, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": descs[-1]},
+        "e2e": {"value": val, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
+        return
+    if args.psf_cg:
+        psf_reference_arm(args)
         return
     w = workload(args)
     K, W = args.steps, args.warmup
@@ -294,6 +463,9 @@ def main():
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
+    if args.psf_cg:
+        psf_cg_bench(args, rank, world, local)
+        return
     if world > 1:
         dist.init_process_group("nccl")
 

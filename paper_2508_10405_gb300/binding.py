@@ -29,7 +29,8 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_cg_solve", "lsrtm_cg_begin", "lsrtm_cg_iterate", "lsrtm_cg_result",
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
-           "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune"]
+           "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune",
+           "lsrtm_psf_hessian", "lsrtm_psf_cg"]
 
 
 class LsrtmError(RuntimeError):
@@ -100,6 +101,9 @@ def load_library(path: str | None = None):
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
     L.lsrtm_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double), ip]
     L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+    L.lsrtm_psf_hessian.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.lsrtm_psf_cg.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double)]
     L.lsrtm_workspace_bytes.argtypes = [vp]
     L.lsrtm_workspace_bytes.restype = ctypes.c_size_t
     L.lsrtm_kernel_launches.argtypes = [vp]
@@ -284,6 +288,35 @@ class Lsrtm:
         _check(self._lib.lsrtm_deblur(self._h, _ptr(a), _ptr(b), int(spacing), int(flen), float(eps),
                                       _ptr(out), None if filt is None else _ptr(filt)))
         return (out, filt) if return_filters else out
+
+    def psf_hessian(self, x, psf_vp, psf_ip, spacing=20, half=-1, transpose=False, param_mask=3, out=None):
+        """y = P H P x (or P H^T P x) with the PSF Hessian interpolated on the
+        fly from the PSF images of the combs in Vp and Ip (App. D); half < 0
+        selects (spacing - 1) // 2. The PSF of a parameter outside param_mask
+        may be None."""
+        self._sync_stream()
+        x = _f32(x)
+        pv = None if psf_vp is None else _f32(psf_vp)
+        pi = None if psf_ip is None else _f32(psf_ip)
+        out = self._empty((2,) + self.shape) if out is None else out
+        _check(self._lib.lsrtm_psf_hessian(self._h, None if pv is None else _ptr(pv),
+                                           None if pi is None else _ptr(pi), int(spacing), int(half),
+                                           int(param_mask), int(bool(transpose)), _ptr(x), _ptr(out)))
+        return out
+
+    def psf_cg(self, m_rtm, psf_vp, psf_ip, niter, spacing=20, half=-1, param_mask=3):
+        """Image-domain CGNR on H^H H dm = H^H P m_rtm with the interpolated
+        PSF Hessian (App. D); returns (dm, misfit history of length niter+1)."""
+        self._sync_stream()
+        m = _f32(m_rtm)
+        pv = None if psf_vp is None else _f32(psf_vp)
+        pi = None if psf_ip is None else _f32(psf_ip)
+        out = self._empty((2,) + self.shape)
+        mis = (ctypes.c_double * (niter + 1))()
+        _check(self._lib.lsrtm_psf_cg(self._h, None if pv is None else _ptr(pv), None if pi is None else _ptr(pi),
+                                      int(spacing), int(half), int(param_mask), _ptr(m), _ptr(out), int(niter),
+                                      mis))
+        return out, np.array(list(mis))
 
     def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3):
         """CGNR / PCGNR; returns (dm, misfit history of length niter+1)."""

@@ -122,6 +122,13 @@ struct lsrtm_handle {
     float *db_filt = nullptr;    // deblurring filters, grown on demand
     size_t db_cap = 0;
     float *db_out = nullptr;     // [2][nint]
+    // interpolated PSF Hessian (App. D)
+    float4 *ph_pt = nullptr;     // node windows, grown on demand
+    size_t ph_cap = 0;
+    float *ph_vec = nullptr;     // [8][2 nint]: x, r, s, p, q, staged input, staged PSFs (Vp, Ip)
+    double *ph_scal = nullptr;   // [0] gamma [1] gamma_new [2] <q,q> [3] <d,d>
+    double *ph_mis = nullptr;    // per-iteration <r,r>
+    int ph_mis_cap = 0;
     // Krylov
     float *cg_x = nullptr, *cg_s = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_minv = nullptr;
     float *cg_r = nullptr;
@@ -1609,7 +1616,7 @@ lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_re
     if (flen < 1 || flen > 11 || flen % 2 == 0) return fail(LSRTM_ERR_ARG, "flen must be odd and in [1, 11]");
     if (spacing < 2 || spacing > 48) return fail(LSRTM_ERR_ARG, "spacing must be in [2, 48]");
     if (!(eps >= 0.0)) return fail(LSRTM_ERR_ARG, "eps must be >= 0");
-    const int nz = h->g.nz, nx = h->g.nx;
+    const int nz = h->gm.nz, nx = h->gm.nx;   // the model grid (the slot grid is the widest window)
     if (nz <= spacing / 2 || nx <= spacing / 2)
         return fail(LSRTM_ERR_ARG, "image smaller than half the node spacing: no deblurring node");
     const int nkz = deblur_nodes(nz, spacing), nkx = deblur_nodes(nx, spacing);
@@ -1636,6 +1643,124 @@ lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_re
     if (flag) return fail(LSRTM_ERR_NONFINITE, "deblurring normal equations not positive definite (eps too small "
                                               "or non-finite images); those filters are set to zero");
     return LSRTM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validates the PSF Hessian arguments, stages the PSF images and builds the
+// node windows; the caller has called begin_call.
+lsrtm_status psfh_setup(lsrtm_handle *h, const float *psf_vp, const float *psf_ip, int spacing, int half,
+                        int param_mask, PsfHessDev *a)
+{
+    if (h->g.ndim != 2) return fail(LSRTM_ERR_ARG, "the PSF Hessian supports 2D images only");
+    if (param_mask < 1 || param_mask > 3) return fail(LSRTM_ERR_ARG, "param_mask must be 1, 2 or 3");
+    if (spacing < 2 || spacing > 64) return fail(LSRTM_ERR_ARG, "spacing must be in [2, 64]");
+    if (half < 0) half = (spacing - 1) / 2;
+    if (half > kPsfHessMaxHalf) return fail(LSRTM_ERR_ARG, "half must be <= 15");
+    if ((param_mask & 1) && !psf_vp) return fail(LSRTM_ERR_ARG, "param_mask includes Vp but psf_vp is NULL");
+    if ((param_mask & 2) && !psf_ip) return fail(LSRTM_ERR_ARG, "param_mask includes Ip but psf_ip is NULL");
+    const int nz = h->gm.nz, nx = h->gm.nx;
+    if (nz <= spacing / 2 || nx <= spacing / 2)
+        return fail(LSRTM_ERR_ARG, "image smaller than half the node spacing: no comb node");
+    const int nkz = deblur_nodes(nz, spacing), nkx = deblur_nodes(nx, spacing);
+    const long long L = 2 * half + 1;
+    const long long npt = (long long)nkz * nkx * L * L;
+    if (npt >= (1LL << 31)) return fail(LSRTM_ERR_ARG, "too many node windows for this spacing and half");
+    const size_t m = 2 * (size_t)h->nint;
+    if (!h->ph_vec) CHECK(dalloc_t(h, &h->ph_vec, 8 * m));
+    if (!h->ph_scal) CHECK(dalloc_t(h, &h->ph_scal, 8));
+    if ((size_t)npt > h->ph_cap) {
+        CHECK(dalloc_t(h, &h->ph_pt, (size_t)npt));
+        h->ph_cap = (size_t)npt;
+    }
+    const float *pv = nullptr, *pi = nullptr;
+    if (param_mask & 1) CHECK(stage_in(h, psf_vp, h->ph_vec + 6 * m, m, &pv));
+    if (param_mask & 2) CHECK(stage_in(h, psf_ip, h->ph_vec + 7 * m, m, &pi));
+    CU(launch_psfh_patches(pv, pi, nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt, h->work));
+    h->launches++;
+    *a = PsfHessDev{nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt};
+    return LSRTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsrtm_status lsrtm_psf_hessian(lsrtm_handle *h, const float *psf_vp, const float *psf_ip, int spacing, int half,
+                               int param_mask, int transpose, const float *x, float *y)
+{
+    if (!h || !x || !y) return fail(LSRTM_ERR_ARG, "null argument");
+    if ((const void *)x == (const void *)y) return fail(LSRTM_ERR_ARG, "x and y must not overlap");
+    CHECK(begin_call(h));
+    PsfHessDev a;
+    CHECK(psfh_setup(h, psf_vp, psf_ip, spacing, half, param_mask, &a));
+    const size_t m = 2 * (size_t)h->nint;
+    const float *xd;
+    CHECK(stage_in(h, x, h->ph_vec + 5 * m, m, &xd));
+    const bool odev = is_device_ptr(y);
+    float *od = odev ? y : h->ph_vec + 4 * m;
+    CU(launch_psfh_apply(a, transpose != 0, xd, od, h->work));
+    h->launches++;
+    if (!odev) CHECK(copy_out(h, y, od, m));
+    return end_call(h, !odev);
+}
+
+// CGNR (CGLS form) on H^H H dm = H^H P m_rtm from dm = 0, FP64 device scalars:
+//   r = P m_rtm, s = H^T r, p = s, gamma = <s, s>; per iteration
+//   q = H p, alpha = gamma / <q, q>, dm += alpha p, r -= alpha q,
+//   s = H^T r, gamma' = <s, s>, p = s + (gamma'/gamma) p.
+lsrtm_status lsrtm_psf_cg(lsrtm_handle *h, const float *psf_vp, const float *psf_ip, int spacing, int half,
+                          int param_mask, const float *m_rtm, float *dm, int niter, double *misfit)
+{
+    if (!h || !m_rtm || !dm) return fail(LSRTM_ERR_ARG, "null argument");
+    if (niter < 0) return fail(LSRTM_ERR_ARG, "niter < 0");
+    CHECK(begin_call(h));
+    PsfHessDev a;
+    CHECK(psfh_setup(h, psf_vp, psf_ip, spacing, half, param_mask, &a));
+    const long long m = 2 * h->nint;
+    float *v = h->ph_vec;
+    float *X = v, *R = v + m, *S = v + 2 * m, *Pp = v + 3 * m, *Q = v + 4 * m;
+    const float *md;
+    CHECK(stage_in(h, m_rtm, v + 5 * m, m, &md));
+    if (h->ph_mis_cap < niter + 1) {
+        const int cap = std::max(niter + 1, 64);
+        CHECK(dalloc_t(h, &h->ph_mis, cap));
+        h->ph_mis_cap = cap;
+    }
+    cudaStream_t s = h->work;
+    double *gamma = h->ph_scal, *gnew = h->ph_scal + 1, *qq = h->ph_scal + 2, *dd = h->ph_scal + 3;
+    CU(cudaMemsetAsync(X, 0, m * sizeof(float), s));
+    CU(launch_scale_copy(R, md, m, s));
+    CU(launch_mul_mask(R, nullptr, param_mask, h->nint, s));
+    CU(launch_dot(R, R, m, dd, h->dotwork, s));
+    CU(launch_psfh_apply(a, true, R, S, s));
+    CU(launch_scale_copy(Pp, S, m, s));
+    CU(launch_dot(S, S, m, gamma, h->dotwork, s));
+    CU(cudaMemcpyAsync(h->ph_mis, dd, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    h->launches += 6;
+    for (int k = 0; k < niter; ++k) {
+        CU(launch_psfh_apply(a, false, Pp, Q, s));
+        CU(launch_dot(Q, Q, m, qq, h->dotwork, s));
+        CU(launch_axpy_ratio(X, Pp, gamma, qq, 1.0f, m, s));
+        CU(launch_axpy_ratio(R, Q, gamma, qq, -1.0f, m, s));
+        CU(launch_psfh_apply(a, true, R, S, s));
+        CU(launch_dot(S, S, m, gnew, h->dotwork, s));
+        CU(launch_xpby_ratio(Pp, S, gnew, gamma, m, s));
+        CU(cudaMemcpyAsync(gamma, gnew, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CU(launch_dot(R, R, m, h->ph_mis + k + 1, h->dotwork, s));
+        h->launches += 8;
+    }
+    CHECK(copy_out(h, dm, X, m));
+    std::vector<double> m2(niter + 1);
+    double d2 = 0.0;
+    CU(cudaMemcpyAsync(m2.data(), h->ph_mis, (niter + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&d2, dd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CHECK(end_call(h, true));
+    if (misfit)
+        for (int k = 0; k <= niter; ++k) misfit[k] = d2 > 0 ? std::sqrt(m2[k] / d2) : 0.0;
+    return check_finite(h, X, m, "PSF-Hessian CG solution");
 }
 
 lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms_out, int *ncand_out)

@@ -194,6 +194,20 @@ size_t deblur_solve_smem(int nz, int nx, int s, int flen);
 cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, int s, int flen, double eps,
                           float *filt, float *out, int *flag, cudaStream_t st);
 
+// Interpolated PSF Hessian (psfhess.cu, App. D): node windows of the PSF
+// images, packed per (node, offset) as float4 (blocks 00, 01, 10, 11: output
+// plane i, input plane j at component 2 i + j), and the on-the-fly
+// application of P H P or P H^T P to a [2][nz][nx] image (mask 1, 2 or 3).
+constexpr int kPsfHessMaxHalf = 15;
+struct PsfHessDev {
+    int nz, nx, s, half, nkz, nkx, mask;
+    const float4 *pt;   // [nkz][nkx][(2 half + 1)^2]
+};
+int psfh_max_half();
+cudaError_t launch_psfh_patches(const float *psf_vp, const float *psf_ip, int nz, int nx, int s, int half,
+                                int nkz, int nkx, int mask, float4 *pt, cudaStream_t st);
+cudaError_t launch_psfh_apply(const PsfHessDev &a, bool transpose, const float *in, float *out, cudaStream_t s);
+
 // Utility kernels (kernels_util.cu).
 // 16-bit band formats: per slot and field, scale = max|stage| / 2^15 and the
 // scaled values into the band store at row band_row(shot0 + slot, n).

@@ -133,3 +133,22 @@ def test_argument_errors():
         with pytest.raises(LsrtmError):
             h.deblur(a, a, **args)
     h.close()
+
+
+def test_windowed_handle_filters_the_model_sized_image():
+    """Handles with per-shot aperture windows run their wavefields on the
+    widest window's grid; the deblurring works on the model-sized image."""
+    import dataclasses
+    from paper_2508_10405_gb300 import Lsrtm
+    w = li.preset(5, nz=36, nx=110, nt=8, nshot=4, shot_dx=22, shot_x0=8, nrec_range=(6, 14), margin=9)
+    w = dataclasses.replace(w, npml=10)
+    assert np.all(w.geom.win_nx < w.nx)
+    m, r = li.image_pair(36, 110, seed=7, nrefl=6)
+    m = m.astype(np.float32).astype(np.float64)
+    r = r.astype(np.float32).astype(np.float64)
+    h = Lsrtm.from_workload(w)
+    out, F = _gpu(h, m, r, 10, 7, 1e-3)
+    ref, Fr = db.deblur(m, r, 10, 7, 1e-3)
+    assert out.shape == (2, 36, 110)
+    assert rel(F, Fr) < 1e-5 and rel(out, ref) < 1e-5
+    h.close()
