@@ -14,10 +14,15 @@
 //
 // k_psfh_patches: the node windows, packed per (node, offset) as one float4
 //   of the four blocks (00, 01, 10, 11), so one 16-byte load serves all four.
-// k_psfh_apply<MASK, TR>: one thread per output pixel, CTAs of 32 x 8 pixels.
-//   The input planes over the tile plus a half-wide halo and the corner
-//   tables of the halo's rows and columns sit in shared memory; the node
-//   windows are read through L1 (a warp's 32 pixels touch at most a few nodes).
+// k_psfh_apply<MASK, TR, R>: one thread per output column and R consecutive
+//   rows (R = the largest of 8, 4, 2, 1 not above s), CTAs of 32 columns x
+//   4 R rows. The input planes over the tile plus a half-wide halo and the
+//   corner tables of the halo's rows and columns sit in shared memory. Per
+//   window offset a thread reads the six node windows covering its rows
+//   (three node rows, two node columns; R <= s rows cross at most one node
+//   row) through L1, interpolates along x once and along z per row: one
+//   loaded value serves R pixels, which keeps the L1 return path (the limit
+//   of a one-pixel-per-thread form) below the FMA pipe.
 //   TR = false: y(r) = sum_a H(r, r - a) x(r - a), the columns gathered at r;
 //   TR = true:  y(c) = sum_a H(c + a, c) x(c + a), the transpose.
 #include <cuda_runtime.h>
@@ -30,7 +35,7 @@ namespace lsrtm {
 
 namespace {
 
-constexpr int kTX = 32, kTZ = 8, kThreads = kTX * kTZ;
+constexpr int kTX = 32;
 
 struct Corner {
     int k0, k1;
@@ -84,150 +89,219 @@ __global__ void k_psfh_patches(const float *psf_vp, const float *psf_ip, int nz,
     }
 }
 
-__device__ __forceinline__ float4 fma4(float w, float4 e, float4 acc)
+// Parameter-block values: a float4 of the four blocks (two parameters) or
+// the one block of a single-parameter mask.
+template <int MASK>
+struct Blk {
+    using T = float;
+};
+template <>
+struct Blk<3> {
+    using T = float4;
+};
+
+template <int BM>
+__device__ __forceinline__ float load_blk(const float4 *pt, int i, float)
 {
-    return make_float4(fmaf(w, e.x, acc.x), fmaf(w, e.y, acc.y), fmaf(w, e.z, acc.z), fmaf(w, e.w, acc.w));
+    return __ldg(reinterpret_cast<const float *>(pt) + 4 * i + BM);
+}
+template <int BM>
+__device__ __forceinline__ float4 load_blk(const float4 *pt, int i, float4)
+{
+    return __ldg(pt + i);
+}
+// p0 + w (p1 - p0)
+__device__ __forceinline__ float lerp_(float p0, float p1, float w) { return fmaf(w, p1 - p0, p0); }
+__device__ __forceinline__ float4 lerp_(float4 p0, float4 p1, float w)
+{
+    return make_float4(lerp_(p0.x, p1.x, w), lerp_(p0.y, p1.y, w), lerp_(p0.z, p1.z, w), lerp_(p0.w, p1.w, w));
+}
+// a q0 + b q1 + c q2
+__device__ __forceinline__ float mix3(float q0, float q1, float q2, float a, float b, float c)
+{
+    return fmaf(c, q2, fmaf(b, q1, a * q0));
+}
+__device__ __forceinline__ float4 mix3(float4 q0, float4 q1, float4 q2, float a, float b, float c)
+{
+    return make_float4(mix3(q0.x, q1.x, q2.x, a, b, c), mix3(q0.y, q1.y, q2.y, a, b, c),
+                       mix3(q0.z, q1.z, q2.z, a, b, c), mix3(q0.w, q1.w, q2.w, a, b, c));
 }
 
-// Block (i, j) of a packed float4: component 2 i + j.
-template <int B>
-__device__ __forceinline__ float comp(float4 e)
+// Weights of R consecutive rows (first corner row kf) on the node rows kf,
+// kf + 1, kf + 2: row r gets 1 - w on its k0 and w on its k1. R <= s keeps
+// every k0 in {kf, kf + 1} and every k1 in {kf, .., kf + 2}.
+template <int R>
+__device__ __forceinline__ void row_weights(const Corner *zc, int kf, float (&wa)[R], float (&wb)[R],
+                                            float (&wc)[R])
 {
-    return B == 0 ? e.x : B == 1 ? e.y : B == 2 ? e.z : e.w;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const Corner Z = zc[r];
+        const int s0 = Z.k0 - kf, s1 = Z.k1 - kf;
+        const float u = 1.f - Z.w, w = Z.w;
+        wa[r] = (s0 == 0 ? u : 0.f) + (s1 == 0 ? w : 0.f);
+        wb[r] = (s0 == 1 ? u : 0.f) + (s1 == 1 ? w : 0.f);
+        wc[r] = s1 == 2 ? w : 0.f;
+    }
 }
 
-template <int MASK, bool TR>
-__global__ void __launch_bounds__(kThreads) k_psfh_apply(const PsfHessDev a, const float *__restrict__ in,
-                                                          float *__restrict__ out)
+// One thread per column and R consecutive rows; CTAs of 32 columns x kRowThreads
+// thread rows (32 x kRowThreads R pixels). Per window offset a thread loads the
+// six node windows (three node rows x two node columns) that cover its R
+// rows, interpolates along x once, then along z per row, so a loaded value
+// serves R pixels.
+constexpr int kRowThreads = 4, kApplyThreads = kTX * kRowThreads;
+
+template <int MASK, bool TR, int R>
+__global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a, const float *__restrict__ in,
+                                                               float *__restrict__ out)
 {
+    using V = typename Blk<MASK>::T;
     constexpr int NP = MASK == 3 ? 2 : 1;
     constexpr int P0 = MASK == 2 ? 1 : 0;    // first plane in the mask
     constexpr int BM = MASK == 2 ? 3 : 0;    // the block of a single-parameter mask
+    constexpr int TZ = kRowThreads * R;      // rows of the CTA tile
     extern __shared__ __align__(16) float sm[];
     const int h = a.half, L = 2 * h + 1, LL = L * L;
-    const int TRW = kTZ + 2 * h, TCW = kTX + 2 * h;
+    const int TRW = TZ + 2 * h, TCW = kTX + 2 * h;
     float *tile = sm;                                                  // [NP][TRW][TCW]
     Corner *zc = reinterpret_cast<Corner *>(tile + NP * TRW * TCW);    // [TRW]
     Corner *xc = zc + TRW;                                             // [TCW]
-    const int t = threadIdx.x, tx = t % kTX, tz = t / kTX;
-    const int R0 = (int)blockIdx.y * kTZ, X0 = (int)blockIdx.x * kTX;
+    const int t = threadIdx.x, tx = t % kTX, ty = t / kTX;
+    const int Z0 = (int)blockIdx.y * TZ, X0 = (int)blockIdx.x * kTX;
     const long long plane = (long long)a.nz * a.nx;
 
-    for (int i = t; i < NP * TRW * TCW; i += kThreads) {
+    for (int i = t; i < NP * TRW * TCW; i += kApplyThreads) {
         const int q = i / (TRW * TCW), rem = i - q * TRW * TCW, r = rem / TCW, c = rem - r * TCW;
-        const int gz = R0 - h + r, gx = X0 - h + c;
+        const int gz = Z0 - h + r, gx = X0 - h + c;
         tile[i] = (gz >= 0 && gz < a.nz && gx >= 0 && gx < a.nx)
                       ? in[(P0 + q) * plane + (long long)gz * a.nx + gx]
                       : 0.f;
     }
-    for (int i = t; i < TRW + TCW; i += kThreads) {
-        if (i < TRW) zc[i] = corner_of(R0 - h + i, a.nz, a.s, a.nkz);
+    for (int i = t; i < TRW + TCW; i += kApplyThreads) {
+        if (i < TRW) zc[i] = corner_of(Z0 - h + i, a.nz, a.s, a.nkz);
         else xc[i - TRW] = corner_of(X0 - h + (i - TRW), a.nx, a.s, a.nkx);
     }
     __syncthreads();
-    const int rz = R0 + tz, rx = X0 + tx;
-    if (rz >= a.nz || rx >= a.nx) return;
+    const int rz0 = Z0 + ty * R, rx = X0 + tx;   // this thread: rows rz0 .. rz0 + R - 1, column rx
+    if (rz0 >= a.nz || rx >= a.nx) return;
 
     const float4 *pt = a.pt;
-    const float *pt1 = reinterpret_cast<const float *>(a.pt);
-    const int nkx = a.nkx;
-    float acc0 = 0.f, acc1 = 0.f;
+    const int nkx = a.nkx, nkz1 = a.nkz - 1;
     const float *t0 = tile, *t1 = tile + (NP - 1) * TRW * TCW;
+    const V zero = V{};
+    float acc0[R], acc1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc0[r] = acc1[r] = 0.f;
+    float wa[R], wb[R], wc[R];
 
     if (!TR) {
-        // y(r) = sum_a [sum_corners(c) w P(a)] x(c), c = r - a
+        // y(r) = sum_a [sum_corners(c) w P(a)] x(c), c = r - a: for offset
+        // row dz the thread's input rows c are rz0 - dz .. + R - 1
         for (int dz = -h; dz <= h; ++dz) {
-            const int cz = rz - dz;
-            if (cz < 0 || cz >= a.nz) continue;
-            const int row = tz + h - dz;
-            const Corner Z = zc[row];
-            const int z0 = Z.k0 * nkx, z1 = Z.k1 * nkx;
-            const float wz1 = Z.w, wz0 = 1.f - Z.w;
+            const int row0 = ty * R + h - dz;   // tile row of c = rz0 - dz
+            const int kf = zc[row0].k0;
+            row_weights<R>(zc + row0, kf, wa, wb, wc);
+            const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
             const int arow = (dz + h) * L + h;
             for (int dx = -h; dx <= h; ++dx) {
                 const int col = tx + h - dx;
                 const int xk0 = xc[col].k0, xk1 = xc[col].k1;
-                const float wx1 = xc[col].w, wx0 = 1.f - wx1;
+                const float wx = xc[col].w;
                 const int ai = arow + dx;
-                const int i00 = (z0 + xk0) * LL + ai, i01 = (z0 + xk1) * LL + ai;
-                const int i10 = (z1 + xk0) * LL + ai, i11 = (z1 + xk1) * LL + ai;
-                const float w00 = wz0 * wx0, w01 = wz0 * wx1, w10 = wz1 * wx0, w11 = wz1 * wx1;
-                const float x0 = t0[row * TCW + col];
-                if (MASK == 3) {
-                    const float x1 = t1[row * TCW + col];
-                    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-                    C = fma4(w00, __ldg(pt + i00), C);
-                    C = fma4(w01, __ldg(pt + i01), C);
-                    C = fma4(w10, __ldg(pt + i10), C);
-                    C = fma4(w11, __ldg(pt + i11), C);
-                    acc0 = fmaf(comp<0>(C), x0, fmaf(comp<1>(C), x1, acc0));
-                    acc1 = fmaf(comp<2>(C), x0, fmaf(comp<3>(C), x1, acc1));
-                } else {
-                    float C = w00 * __ldg(pt1 + 4 * i00 + BM);
-                    C = fmaf(w01, __ldg(pt1 + 4 * i01 + BM), C);
-                    C = fmaf(w10, __ldg(pt1 + 4 * i10 + BM), C);
-                    C = fmaf(w11, __ldg(pt1 + 4 * i11 + BM), C);
-                    acc0 = fmaf(C, x0, acc0);
+                const V q0 = lerp_(load_blk<BM>(pt, (n0 + xk0) * LL + ai, zero),
+                                   load_blk<BM>(pt, (n0 + xk1) * LL + ai, zero), wx);
+                const V q1 = lerp_(load_blk<BM>(pt, (n1 + xk0) * LL + ai, zero),
+                                   load_blk<BM>(pt, (n1 + xk1) * LL + ai, zero), wx);
+                const V q2 = lerp_(load_blk<BM>(pt, (n2 + xk0) * LL + ai, zero),
+                                   load_blk<BM>(pt, (n2 + xk1) * LL + ai, zero), wx);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const V C = mix3(q0, q1, q2, wa[r], wb[r], wc[r]);
+                    const int o = (row0 + r) * TCW + col;
+                    if constexpr (MASK == 3) {
+                        const float x0 = t0[o], x1 = t1[o];
+                        acc0[r] = fmaf(C.x, x0, fmaf(C.y, x1, acc0[r]));
+                        acc1[r] = fmaf(C.z, x0, fmaf(C.w, x1, acc1[r]));
+                    } else {
+                        acc0[r] = fmaf(C, t0[o], acc0[r]);
+                    }
                 }
             }
         }
     } else {
-        // y(c) = sum_a [sum_corners(c) w P(a)] x(c + a)
-        const Corner Z = zc[tz + h], X = xc[tx + h];
-        const float w00 = (1.f - Z.w) * (1.f - X.w), w01 = (1.f - Z.w) * X.w;
-        const float w10 = Z.w * (1.f - X.w), w11 = Z.w * X.w;
-        const int b00 = (Z.k0 * nkx + X.k0) * LL, b01 = (Z.k0 * nkx + X.k1) * LL;
-        const int b10 = (Z.k1 * nkx + X.k0) * LL, b11 = (Z.k1 * nkx + X.k1) * LL;
+        // y(c) = sum_a [sum_corners(c) w P(a)] x(c + a): the thread's rows c
+        // and column are fixed, so are their corners
+        const int row0 = ty * R + h;   // tile row of c = rz0
+        const int kf = zc[row0].k0;
+        row_weights<R>(zc + row0, kf, wa, wb, wc);
+        const int xk0 = xc[tx + h].k0, xk1 = xc[tx + h].k1;
+        const float wx = xc[tx + h].w;
+        const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
+        const int b00 = (n0 + xk0) * LL, b01 = (n0 + xk1) * LL, b10 = (n1 + xk0) * LL;
+        const int b11 = (n1 + xk1) * LL, b20 = (n2 + xk0) * LL, b21 = (n2 + xk1) * LL;
         for (int dz = -h; dz <= h; ++dz) {
-            const int row = tz + h + dz;
             const int arow = (dz + h) * L + h;
             for (int dx = -h; dx <= h; ++dx) {
-                const int col = tx + h + dx;
                 const int ai = arow + dx;
-                const float y0 = t0[row * TCW + col];
-                if (MASK == 3) {
-                    const float y1 = t1[row * TCW + col];
-                    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-                    C = fma4(w00, __ldg(pt + b00 + ai), C);
-                    C = fma4(w01, __ldg(pt + b01 + ai), C);
-                    C = fma4(w10, __ldg(pt + b10 + ai), C);
-                    C = fma4(w11, __ldg(pt + b11 + ai), C);
-                    acc0 = fmaf(comp<0>(C), y0, fmaf(comp<2>(C), y1, acc0));
-                    acc1 = fmaf(comp<1>(C), y0, fmaf(comp<3>(C), y1, acc1));
-                } else {
-                    float C = w00 * __ldg(pt1 + 4 * (b00 + ai) + BM);
-                    C = fmaf(w01, __ldg(pt1 + 4 * (b01 + ai) + BM), C);
-                    C = fmaf(w10, __ldg(pt1 + 4 * (b10 + ai) + BM), C);
-                    C = fmaf(w11, __ldg(pt1 + 4 * (b11 + ai) + BM), C);
-                    acc0 = fmaf(C, y0, acc0);
+                const V q0 = lerp_(load_blk<BM>(pt, b00 + ai, zero), load_blk<BM>(pt, b01 + ai, zero), wx);
+                const V q1 = lerp_(load_blk<BM>(pt, b10 + ai, zero), load_blk<BM>(pt, b11 + ai, zero), wx);
+                const V q2 = lerp_(load_blk<BM>(pt, b20 + ai, zero), load_blk<BM>(pt, b21 + ai, zero), wx);
+                const int col = tx + h + dx;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const V C = mix3(q0, q1, q2, wa[r], wb[r], wc[r]);
+                    const int o = (row0 + r + dz) * TCW + col;
+                    if constexpr (MASK == 3) {
+                        const float y0 = t0[o], y1 = t1[o];
+                        acc0[r] = fmaf(C.x, y0, fmaf(C.z, y1, acc0[r]));
+                        acc1[r] = fmaf(C.y, y0, fmaf(C.w, y1, acc1[r]));
+                    } else {
+                        acc0[r] = fmaf(C, t0[o], acc0[r]);
+                    }
                 }
             }
         }
     }
-    const long long o = (long long)rz * a.nx + rx;
-    if (MASK == 3) {
-        out[o] = acc0;
-        out[plane + o] = acc1;
-    } else {
-        out[P0 * plane + o] = acc0;
-        out[(1 - P0) * plane + o] = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int z = rz0 + r;
+        if (z >= a.nz) break;
+        const long long o = (long long)z * a.nx + rx;
+        if (MASK == 3) {
+            out[o] = acc0[r];
+            out[plane + o] = acc1[r];
+        } else {
+            out[P0 * plane + o] = acc0[r];
+            out[(1 - P0) * plane + o] = 0.f;
+        }
     }
 }
 
-size_t apply_smem(int mask, int half)
+size_t apply_smem(int mask, int half, int R)
 {
     const int np = mask == 3 ? 2 : 1;
-    const size_t rows = kTZ + 2 * half, cols = kTX + 2 * half;
+    const size_t rows = kRowThreads * R + 2 * half, cols = kTX + 2 * half;
     return np * rows * cols * sizeof(float) + (rows + cols) * sizeof(Corner);
 }
 
-template <int MASK, bool TR>
+template <int MASK, bool TR, int R>
 cudaError_t launch_t(const PsfHessDev &a, const float *in, float *out, cudaStream_t s)
 {
-    const size_t sm = apply_smem(MASK, a.half);
-    dim3 grid((a.nx + kTX - 1) / kTX, (a.nz + kTZ - 1) / kTZ);
-    k_psfh_apply<MASK, TR><<<grid, kThreads, sm, s>>>(a, in, out);
+    const size_t sm = apply_smem(MASK, a.half, R);
+    dim3 grid((a.nx + kTX - 1) / kTX, (a.nz + kRowThreads * R - 1) / (kRowThreads * R));
+    k_psfh_apply<MASK, TR, R><<<grid, kApplyThreads, sm, s>>>(a, in, out);
     return cudaGetLastError();
+}
+
+template <int MASK, bool TR>
+cudaError_t launch_r(const PsfHessDev &a, const float *in, float *out, cudaStream_t s)
+{
+    // rows per thread: the largest of 8, 4, 2, 1 not above the node spacing
+    if (a.s >= 8) return launch_t<MASK, TR, 8>(a, in, out, s);
+    if (a.s >= 4) return launch_t<MASK, TR, 4>(a, in, out, s);
+    if (a.s >= 2) return launch_t<MASK, TR, 2>(a, in, out, s);
+    return launch_t<MASK, TR, 1>(a, in, out, s);
 }
 
 }  // namespace
@@ -246,12 +320,12 @@ cudaError_t launch_psfh_patches(const float *psf_vp, const float *psf_ip, int nz
 cudaError_t launch_psfh_apply(const PsfHessDev &a, bool transpose, const float *in, float *out, cudaStream_t s)
 {
     switch (a.mask * 2 + (transpose ? 1 : 0)) {
-    case 2: return launch_t<1, false>(a, in, out, s);
-    case 3: return launch_t<1, true>(a, in, out, s);
-    case 4: return launch_t<2, false>(a, in, out, s);
-    case 5: return launch_t<2, true>(a, in, out, s);
-    case 6: return launch_t<3, false>(a, in, out, s);
-    case 7: return launch_t<3, true>(a, in, out, s);
+    case 2: return launch_r<1, false>(a, in, out, s);
+    case 3: return launch_r<1, true>(a, in, out, s);
+    case 4: return launch_r<2, false>(a, in, out, s);
+    case 5: return launch_r<2, true>(a, in, out, s);
+    case 6: return launch_r<3, false>(a, in, out, s);
+    case 7: return launch_r<3, true>(a, in, out, s);
     default: return cudaErrorInvalidValue;
     }
 }
