@@ -16,7 +16,7 @@
 //   of the four blocks (00, 01, 10, 11), so one 16-byte load serves all four.
 // k_psfh_apply<MASK, TR, R>: one thread per output column and R consecutive
 //   rows (R = the largest of 8, 4, 2, 1 not above s), CTAs of 32 columns x
-//   4 R rows. The input planes over the tile plus a half-wide halo and the
+//   2 R rows (small CTAs spread the one wave evenly over the SMs). The input planes over the tile plus a half-wide halo and the
 //   corner tables of the halo's rows and columns sit in shared memory. Per
 //   window offset a thread reads the six node windows covering its rows
 //   (three node rows, two node columns; R <= s rows cross at most one node
@@ -116,30 +116,31 @@ __device__ __forceinline__ float4 lerp_(float4 p0, float4 p1, float w)
 {
     return make_float4(lerp_(p0.x, p1.x, w), lerp_(p0.y, p1.y, w), lerp_(p0.z, p1.z, w), lerp_(p0.w, p1.w, w));
 }
-// a q0 + b q1 + c q2
-__device__ __forceinline__ float mix3(float q0, float q1, float q2, float a, float b, float c)
+__device__ __forceinline__ float sub_(float a, float b) { return a - b; }
+__device__ __forceinline__ float4 sub_(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+// q0 + b d1 + c d2 (= (1 - b - c) q0 + b q1 + c q2 with d1 = q1 - q0, d2 = q2 - q0)
+__device__ __forceinline__ float mix3(float q0, float d1, float d2, float b, float c)
 {
-    return fmaf(c, q2, fmaf(b, q1, a * q0));
+    return fmaf(c, d2, fmaf(b, d1, q0));
 }
-__device__ __forceinline__ float4 mix3(float4 q0, float4 q1, float4 q2, float a, float b, float c)
+__device__ __forceinline__ float4 mix3(float4 q0, float4 d1, float4 d2, float b, float c)
 {
-    return make_float4(mix3(q0.x, q1.x, q2.x, a, b, c), mix3(q0.y, q1.y, q2.y, a, b, c),
-                       mix3(q0.z, q1.z, q2.z, a, b, c), mix3(q0.w, q1.w, q2.w, a, b, c));
+    return make_float4(mix3(q0.x, d1.x, d2.x, b, c), mix3(q0.y, d1.y, d2.y, b, c), mix3(q0.z, d1.z, d2.z, b, c),
+                       mix3(q0.w, d1.w, d2.w, b, c));
 }
 
-// Weights of R consecutive rows (first corner row kf) on the node rows kf,
-// kf + 1, kf + 2: row r gets 1 - w on its k0 and w on its k1. R <= s keeps
-// every k0 in {kf, kf + 1} and every k1 in {kf, .., kf + 2}.
+// Weights of R consecutive rows (first corner row kf) on the node rows
+// kf + 1 and kf + 2 (the rest, on kf, is implied): row r puts 1 - w on its k0
+// and w on its k1. R <= s keeps every k0 in {kf, kf + 1} and every k1 in
+// {kf, .., kf + 2}.
 template <int R>
-__device__ __forceinline__ void row_weights(const Corner *zc, int kf, float (&wa)[R], float (&wb)[R],
-                                            float (&wc)[R])
+__device__ __forceinline__ void row_weights(const Corner *zc, int kf, float (&wb)[R], float (&wc)[R])
 {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const Corner Z = zc[r];
         const int s0 = Z.k0 - kf, s1 = Z.k1 - kf;
         const float u = 1.f - Z.w, w = Z.w;
-        wa[r] = (s0 == 0 ? u : 0.f) + (s1 == 0 ? w : 0.f);
         wb[r] = (s0 == 1 ? u : 0.f) + (s1 == 1 ? w : 0.f);
         wc[r] = s1 == 2 ? w : 0.f;
     }
@@ -150,7 +151,7 @@ __device__ __forceinline__ void row_weights(const Corner *zc, int kf, float (&wa
 // six node windows (three node rows x two node columns) that cover its R
 // rows, interpolates along x once, then along z per row, so a loaded value
 // serves R pixels.
-constexpr int kRowThreads = 4, kApplyThreads = kTX * kRowThreads;
+constexpr int kRowThreads = 2, kApplyThreads = kTX * kRowThreads;
 
 template <int MASK, bool TR, int R>
 __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a, const float *__restrict__ in,
@@ -164,19 +165,22 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
     extern __shared__ __align__(16) float sm[];
     const int h = a.half, L = 2 * h + 1, LL = L * L;
     const int TRW = TZ + 2 * h, TCW = kTX + 2 * h;
-    float *tile = sm;                                                  // [NP][TRW][TCW]
+    float *tile = sm;   // [TRW][TCW] of the input, plane pairs interleaved for two parameters
     Corner *zc = reinterpret_cast<Corner *>(tile + NP * TRW * TCW);    // [TRW]
     Corner *xc = zc + TRW;                                             // [TCW]
     const int t = threadIdx.x, tx = t % kTX, ty = t / kTX;
     const int Z0 = (int)blockIdx.y * TZ, X0 = (int)blockIdx.x * kTX;
     const long long plane = (long long)a.nz * a.nx;
 
-    for (int i = t; i < NP * TRW * TCW; i += kApplyThreads) {
-        const int q = i / (TRW * TCW), rem = i - q * TRW * TCW, r = rem / TCW, c = rem - r * TCW;
+    for (int i = t; i < TRW * TCW; i += kApplyThreads) {
+        const int r = i / TCW, c = i - r * TCW;
         const int gz = Z0 - h + r, gx = X0 - h + c;
-        tile[i] = (gz >= 0 && gz < a.nz && gx >= 0 && gx < a.nx)
-                      ? in[(P0 + q) * plane + (long long)gz * a.nx + gx]
-                      : 0.f;
+        const bool ok = gz >= 0 && gz < a.nz && gx >= 0 && gx < a.nx;
+        const long long g = ok ? (long long)gz * a.nx + gx : 0;
+        if (MASK == 3)
+            reinterpret_cast<float2 *>(tile)[i] = ok ? make_float2(in[g], in[plane + g]) : make_float2(0.f, 0.f);
+        else
+            tile[i] = ok ? in[P0 * plane + g] : 0.f;
     }
     for (int i = t; i < TRW + TCW; i += kApplyThreads) {
         if (i < TRW) zc[i] = corner_of(Z0 - h + i, a.nz, a.s, a.nkz);
@@ -188,12 +192,12 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
 
     const float4 *pt = a.pt;
     const int nkx = a.nkx, nkz1 = a.nkz - 1;
-    const float *t0 = tile, *t1 = tile + (NP - 1) * TRW * TCW;
+    const float2 *t2 = reinterpret_cast<const float2 *>(tile);
     const V zero = V{};
     float acc0[R], acc1[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc0[r] = acc1[r] = 0.f;
-    float wa[R], wb[R], wc[R];
+    float wb[R], wc[R];
 
     if (!TR) {
         // y(r) = sum_a [sum_corners(c) w P(a)] x(c), c = r - a: for offset
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
         for (int dz = -h; dz <= h; ++dz) {
             const int row0 = ty * R + h - dz;   // tile row of c = rz0 - dz
             const int kf = zc[row0].k0;
-            row_weights<R>(zc + row0, kf, wa, wb, wc);
+            row_weights<R>(zc + row0, kf, wb, wc);
             const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
             const int arow = (dz + h) * L + h;
             for (int dx = -h; dx <= h; ++dx) {
@@ -215,16 +219,17 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
                                    load_blk<BM>(pt, (n1 + xk1) * LL + ai, zero), wx);
                 const V q2 = lerp_(load_blk<BM>(pt, (n2 + xk0) * LL + ai, zero),
                                    load_blk<BM>(pt, (n2 + xk1) * LL + ai, zero), wx);
+                const V d1 = sub_(q1, q0), d2 = sub_(q2, q0);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V C = mix3(q0, q1, q2, wa[r], wb[r], wc[r]);
+                    const V C = mix3(q0, d1, d2, wb[r], wc[r]);
                     const int o = (row0 + r) * TCW + col;
                     if constexpr (MASK == 3) {
-                        const float x0 = t0[o], x1 = t1[o];
-                        acc0[r] = fmaf(C.x, x0, fmaf(C.y, x1, acc0[r]));
-                        acc1[r] = fmaf(C.z, x0, fmaf(C.w, x1, acc1[r]));
+                        const float2 xv = t2[o];
+                        acc0[r] = fmaf(C.x, xv.x, fmaf(C.y, xv.y, acc0[r]));
+                        acc1[r] = fmaf(C.z, xv.x, fmaf(C.w, xv.y, acc1[r]));
                     } else {
-                        acc0[r] = fmaf(C, t0[o], acc0[r]);
+                        acc0[r] = fmaf(C, tile[o], acc0[r]);
                     }
                 }
             }
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
         // and column are fixed, so are their corners
         const int row0 = ty * R + h;   // tile row of c = rz0
         const int kf = zc[row0].k0;
-        row_weights<R>(zc + row0, kf, wa, wb, wc);
+        row_weights<R>(zc + row0, kf, wb, wc);
         const int xk0 = xc[tx + h].k0, xk1 = xc[tx + h].k1;
         const float wx = xc[tx + h].w;
         const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
@@ -247,17 +252,18 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
                 const V q0 = lerp_(load_blk<BM>(pt, b00 + ai, zero), load_blk<BM>(pt, b01 + ai, zero), wx);
                 const V q1 = lerp_(load_blk<BM>(pt, b10 + ai, zero), load_blk<BM>(pt, b11 + ai, zero), wx);
                 const V q2 = lerp_(load_blk<BM>(pt, b20 + ai, zero), load_blk<BM>(pt, b21 + ai, zero), wx);
+                const V d1 = sub_(q1, q0), d2 = sub_(q2, q0);
                 const int col = tx + h + dx;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const V C = mix3(q0, q1, q2, wa[r], wb[r], wc[r]);
+                    const V C = mix3(q0, d1, d2, wb[r], wc[r]);
                     const int o = (row0 + r + dz) * TCW + col;
                     if constexpr (MASK == 3) {
-                        const float y0 = t0[o], y1 = t1[o];
-                        acc0[r] = fmaf(C.x, y0, fmaf(C.z, y1, acc0[r]));
-                        acc1[r] = fmaf(C.y, y0, fmaf(C.w, y1, acc1[r]));
+                        const float2 yv = t2[o];
+                        acc0[r] = fmaf(C.x, yv.x, fmaf(C.z, yv.y, acc0[r]));
+                        acc1[r] = fmaf(C.y, yv.x, fmaf(C.w, yv.y, acc1[r]));
                     } else {
-                        acc0[r] = fmaf(C, t0[o], acc0[r]);
+                        acc0[r] = fmaf(C, tile[o], acc0[r]);
                     }
                 }
             }
