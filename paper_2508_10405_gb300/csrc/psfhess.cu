@@ -208,17 +208,27 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
             row_weights<R>(zc + row0, kf, wb, wc);
             const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
             const int arow = (dz + h) * L + h;
+            // node values of offset dx = -h, then of dx + 1 while dx is used
+            int col = tx + 2 * h;
+            int xk0 = xc[col].k0, xk1 = xc[col].k1;
+            float wx = xc[col].w;
+            V p00 = load_blk<BM>(pt, (n0 + xk0) * LL + arow - h, zero);
+            V p01 = load_blk<BM>(pt, (n0 + xk1) * LL + arow - h, zero);
+            V p10 = load_blk<BM>(pt, (n1 + xk0) * LL + arow - h, zero);
+            V p11 = load_blk<BM>(pt, (n1 + xk1) * LL + arow - h, zero);
+            V p20 = load_blk<BM>(pt, (n2 + xk0) * LL + arow - h, zero);
+            V p21 = load_blk<BM>(pt, (n2 + xk1) * LL + arow - h, zero);
             for (int dx = -h; dx <= h; ++dx) {
-                const int col = tx + h - dx;
-                const int xk0 = xc[col].k0, xk1 = xc[col].k1;
-                const float wx = xc[col].w;
-                const int ai = arow + dx;
-                const V q0 = lerp_(load_blk<BM>(pt, (n0 + xk0) * LL + ai, zero),
-                                   load_blk<BM>(pt, (n0 + xk1) * LL + ai, zero), wx);
-                const V q1 = lerp_(load_blk<BM>(pt, (n1 + xk0) * LL + ai, zero),
-                                   load_blk<BM>(pt, (n1 + xk1) * LL + ai, zero), wx);
-                const V q2 = lerp_(load_blk<BM>(pt, (n2 + xk0) * LL + ai, zero),
-                                   load_blk<BM>(pt, (n2 + xk1) * LL + ai, zero), wx);
+                const int dn = min(dx + 1, h), cn = tx + h - dn, an = arow + dn;
+                const int yk0 = xc[cn].k0, yk1 = xc[cn].k1;
+                const float wn = xc[cn].w;
+                const V n00 = load_blk<BM>(pt, (n0 + yk0) * LL + an, zero);
+                const V n01 = load_blk<BM>(pt, (n0 + yk1) * LL + an, zero);
+                const V n10 = load_blk<BM>(pt, (n1 + yk0) * LL + an, zero);
+                const V n11 = load_blk<BM>(pt, (n1 + yk1) * LL + an, zero);
+                const V n20 = load_blk<BM>(pt, (n2 + yk0) * LL + an, zero);
+                const V n21 = load_blk<BM>(pt, (n2 + yk1) * LL + an, zero);
+                const V q0 = lerp_(p00, p01, wx), q1 = lerp_(p10, p11, wx), q2 = lerp_(p20, p21, wx);
                 const V d1 = sub_(q1, q0), d2 = sub_(q2, q0);
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
@@ -232,6 +242,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
                         acc0[r] = fmaf(C, tile[o], acc0[r]);
                     }
                 }
+                p00 = n00, p01 = n01, p10 = n10, p11 = n11, p20 = n20, p21 = n21;
+                col = cn, wx = wn;
             }
         }
     } else {
@@ -245,28 +257,34 @@ __global__ void __launch_bounds__(kApplyThreads) k_psfh_apply(const PsfHessDev a
         const int n0 = kf * nkx, n1 = min(kf + 1, nkz1) * nkx, n2 = min(kf + 2, nkz1) * nkx;
         const int b00 = (n0 + xk0) * LL, b01 = (n0 + xk1) * LL, b10 = (n1 + xk0) * LL;
         const int b11 = (n1 + xk1) * LL, b20 = (n2 + xk0) * LL, b21 = (n2 + xk1) * LL;
-        for (int dz = -h; dz <= h; ++dz) {
-            const int arow = (dz + h) * L + h;
-            for (int dx = -h; dx <= h; ++dx) {
-                const int ai = arow + dx;
-                const V q0 = lerp_(load_blk<BM>(pt, b00 + ai, zero), load_blk<BM>(pt, b01 + ai, zero), wx);
-                const V q1 = lerp_(load_blk<BM>(pt, b10 + ai, zero), load_blk<BM>(pt, b11 + ai, zero), wx);
-                const V q2 = lerp_(load_blk<BM>(pt, b20 + ai, zero), load_blk<BM>(pt, b21 + ai, zero), wx);
-                const V d1 = sub_(q1, q0), d2 = sub_(q2, q0);
-                const int col = tx + h + dx;
+        // the window offsets in storage order, the next offset's six node
+        // values loaded while the current one is used
+        V p00 = load_blk<BM>(pt, b00, zero), p01 = load_blk<BM>(pt, b01, zero);
+        V p10 = load_blk<BM>(pt, b10, zero), p11 = load_blk<BM>(pt, b11, zero);
+        V p20 = load_blk<BM>(pt, b20, zero), p21 = load_blk<BM>(pt, b21, zero);
+        int dz = -h, dx = -h;
+        for (int ai = 0; ai < LL; ++ai) {
+            const int an = min(ai + 1, LL - 1);
+            const V n00 = load_blk<BM>(pt, b00 + an, zero), n01 = load_blk<BM>(pt, b01 + an, zero);
+            const V n10 = load_blk<BM>(pt, b10 + an, zero), n11 = load_blk<BM>(pt, b11 + an, zero);
+            const V n20 = load_blk<BM>(pt, b20 + an, zero), n21 = load_blk<BM>(pt, b21 + an, zero);
+            const V q0 = lerp_(p00, p01, wx), q1 = lerp_(p10, p11, wx), q2 = lerp_(p20, p21, wx);
+            const V d1 = sub_(q1, q0), d2 = sub_(q2, q0);
+            const int ob = (row0 + dz) * TCW + tx + h + dx;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const V C = mix3(q0, d1, d2, wb[r], wc[r]);
-                    const int o = (row0 + r + dz) * TCW + col;
-                    if constexpr (MASK == 3) {
-                        const float2 yv = t2[o];
-                        acc0[r] = fmaf(C.x, yv.x, fmaf(C.z, yv.y, acc0[r]));
-                        acc1[r] = fmaf(C.y, yv.x, fmaf(C.w, yv.y, acc1[r]));
-                    } else {
-                        acc0[r] = fmaf(C, tile[o], acc0[r]);
-                    }
+            for (int r = 0; r < R; ++r) {
+                const V C = mix3(q0, d1, d2, wb[r], wc[r]);
+                const int o = ob + r * TCW;
+                if constexpr (MASK == 3) {
+                    const float2 yv = t2[o];
+                    acc0[r] = fmaf(C.x, yv.x, fmaf(C.z, yv.y, acc0[r]));
+                    acc1[r] = fmaf(C.y, yv.x, fmaf(C.w, yv.y, acc1[r]));
+                } else {
+                    acc0[r] = fmaf(C, tile[o], acc0[r]);
                 }
             }
+            p00 = n00, p01 = n01, p10 = n10, p11 = n11, p20 = n20, p21 = n21;
+            if (++dx > h) dx = -h, ++dz;
         }
     }
 #pragma unroll
