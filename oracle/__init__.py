@@ -15,6 +15,10 @@ Layers:
     (Sec. 3), the spike comb and PSF / remigration probes (App. D).
   * ``deblur.py``: the nonstationary 11 x 11 deblurring filters of App. E
     (FP64 normal equations per comb window, bilinear valence blending).
+  * ``psf_hessian.py``: the interpolated PSF Hessian of App. D and its
+    image-domain CGNR.
+  * ``data.py``: the muted data residuals of Sec. 4 (direct-wave and
+    far-offset mutes of observed minus background data).
 
 Pinned by the ``-m "not gpu"`` tests against: textbook staggered FD
 coefficients, the 2D and 3D homogeneous Green's functions, the normal
@@ -150,7 +154,11 @@ def _check(rc, what):
 def model(w, vp=None, rho=None, geom=None, wavelet=None, nt=None, vmax=None,
           src_ptr=None, src_idx=None) -> np.ndarray:
     """Nonlinear modelling (Eq. 1): pressure records [nrec_total, nt]. A custom
-    source list (CSR `src_ptr`, `src_idx`) overrides the one-source geometry."""
+    source list (CSR `src_ptr`, `src_idx`) overrides the one-source geometry;
+    shots with aperture windows are modelled on their windows' sub-models."""
+    g = w.geom if geom is None else geom
+    if src_ptr is None and wavelet is None and windowed(g):
+        return _model_windowed(w, vp, rho, g, nt, vmax)
     a = _Args(w, vp, rho, geom, wavelet, nt, vmax)
     d = np.zeros((a.geom.nrec_total, a.nt))
     args = list(a.common())
@@ -241,6 +249,15 @@ def _born_windowed(w, dm, vp, rho, geom, nt, vmax):
         sub, x0, nxw, vm = _window_case(w, geom, s, vp, rho, vmax)
         d[geom.rec_ptr[s]:geom.rec_ptr[s + 1]] = born(
             sub, np.ascontiguousarray(dm[..., x0:x0 + nxw]), nt=nt, vmax=vm)
+    return d
+
+
+def _model_windowed(w, vp, rho, geom, nt, vmax):
+    ntt = int(w.nt if nt is None else nt)
+    d = np.zeros((geom.nrec_total, ntt))
+    for s in range(geom.nshot):
+        sub, x0, nxw, vm = _window_case(w, geom, s, vp, rho, vmax)
+        d[geom.rec_ptr[s]:geom.rec_ptr[s + 1]] = model(sub, nt=nt, vmax=vm)
     return d
 
 
