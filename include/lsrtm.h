@@ -208,6 +208,31 @@ lsrtm_status lsrtm_born_static(const lsrtm_config *cfg, const float *vp, const f
                                const float *wavelet, const lsrtm_geometry *geom, const float *dm,
                                float *d, void *stream);
 
+/* Nonlinear modelling (Eq. 1) in the handle's own model (vp, rho given at
+ * creation; aperture windows as for lsrtm_born): d[r][n] = p^{n+1} at the
+ * receiver node, the same recording as lsrtm_born with the pressure in place
+ * of its perturbation. Observed data come from a handle created on the true
+ * model, synthetic background data from one on the background model.
+ *   d : [nrec_total][nt] output (host or device)
+ * Asynchronous for device outputs. */
+lsrtm_status lsrtm_model(lsrtm_handle *h, float *d);
+
+/* Muted data residual, the data-domain input of Sec. 4: observed minus
+ * background data times a mask that removes the direct arrivals and the
+ * long-offset refractions. Per receiver r (horizontal source-receiver offset
+ * o_r = |(x_r - x_s, y_r - y_s)| in metres) and sample n (t_n = (n + 1) dt):
+ *     d_out = ramp(t_n - o_r / v_mute - t0, t_taper) ramp(o_max - o_r, o_taper)
+ *             (d_obs - d_syn),
+ *     ramp(u, W) = 0 for u <= 0, 1 for u >= W, (1 - cos(pi u / W)) / 2 between
+ *     (W = 0: a step); no far-offset cut when o_max <= 0.
+ * The mute times are formed in FP64; the data arithmetic is FP32.
+ *   d_obs, d_syn : [nrec_total][nt] (host or device; d_syn may be NULL)
+ *   v_mute (m/s) > 0, t0 (s), t_taper (s) >= 0, o_max (m), o_taper (m) >= 0
+ *   d_out        : [nrec_total][nt] output (host or device; may be d_obs)
+ * Errors: LSRTM_ERR_ARG for out-of-range parameters. Synchronous. */
+lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const float *d_syn, double v_mute, double t0,
+                                 double t_taper, double o_max, double o_taper, float *d_out);
+
 /* Replaces the stream used by later calls. */
 lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
 

@@ -30,7 +30,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
            "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune",
-           "lsrtm_psf_hessian", "lsrtm_psf_cg"]
+           "lsrtm_psf_hessian", "lsrtm_psf_cg", "lsrtm_model", "lsrtm_mute_residual"]
 
 
 class LsrtmError(RuntimeError):
@@ -101,6 +101,8 @@ def load_library(path: str | None = None):
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
     L.lsrtm_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double), ip]
     L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+    L.lsrtm_model.argtypes = [vp, vp]
+    L.lsrtm_mute_residual.argtypes = [vp, vp, vp] + [ctypes.c_double] * 5 + [vp]
     L.lsrtm_psf_hessian.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     L.lsrtm_psf_cg.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double)]
@@ -288,6 +290,27 @@ class Lsrtm:
         _check(self._lib.lsrtm_deblur(self._h, _ptr(a), _ptr(b), int(spacing), int(flen), float(eps),
                                       _ptr(out), None if filt is None else _ptr(filt)))
         return (out, filt) if return_filters else out
+
+    def model(self, out=None):
+        """Nonlinear modelling (Eq. 1) in the handle's own model: pressure
+        records [nrec_total, nt]."""
+        self._sync_stream()
+        out = self._empty((self.nrec_total, self.nt)) if out is None else out
+        _check(self._lib.lsrtm_model(self._h, _ptr(out)))
+        return out
+
+    def mute_residual(self, d_obs, d_syn, v_mute, t0, t_taper, o_max=0.0, o_taper=0.0, out=None):
+        """Muted data residual (Sec. 4): the direct-wave mute after
+        offset / v_mute + t0 (raised-cosine rise over t_taper) times the
+        far-offset cut at o_max (rise over o_taper), applied to d_obs - d_syn
+        (d_syn may be None)."""
+        self._sync_stream()
+        a = _f32(d_obs)
+        b = None if d_syn is None else _f32(d_syn)
+        out = self._empty((self.nrec_total, self.nt)) if out is None else out
+        _check(self._lib.lsrtm_mute_residual(self._h, _ptr(a), None if b is None else _ptr(b), float(v_mute),
+                                             float(t0), float(t_taper), float(o_max), float(o_taper), _ptr(out)))
+        return out
 
     def psf_hessian(self, x, psf_vp, psf_ip, spacing=20, half=-1, transpose=False, param_mask=3, out=None):
         """y = P H P x (or P H^T P x) with the PSF Hessian interpolated on the

@@ -54,7 +54,7 @@ constexpr int kStatePlanes2D = 10;
 constexpr int kPsivPlanes2D = 4;
 constexpr int kStatePlanes3D = 20;
 
-enum GraphKind { G_BORN = 0, G_BG = 1, G_BG_HESS = 2, G_ADJ = 3 };
+enum GraphKind { G_BORN = 0, G_BG = 1, G_BG_HESS = 2, G_ADJ = 3, G_MODEL = 6 };
 
 }  // namespace
 
@@ -73,6 +73,10 @@ struct lsrtm_handle {
     long long nrec_total = 0;
     long long nint = 0;
     std::vector<int> rec_ptr;
+    std::vector<double> rec_off_h;   // horizontal source-receiver offset of every receiver row (m)
+    double *mute_td = nullptr;       // muting: per receiver the direct-wave mute time
+    float *mute_fo = nullptr;        // muting: per receiver the far-offset factor
+    float *dstage2 = nullptr;        // second [nrec_total][nt] stage (host inputs of the muting)
     // device model and geometry
     float *kdt = nullptr, *binv = nullptr;
     float2 *kd2 = nullptr, *br2 = nullptr;   // (dt kappa, perturbation) and (1/rho, perturbation)
@@ -567,6 +571,39 @@ lsrtm_status born_core(lsrtm_handle *h)
     return LSRTM_OK;
 }
 
+// Nonlinear modelling (Eq. 1) of every shot in the handle's own model: the
+// background time loop with the pressure p^{n+1} recorded into h->dstage.
+lsrtm_status model_core(lsrtm_handle *h)
+{
+    const int nt = h->g.nt;
+    for (int s0 = 0; s0 < h->nshot; s0 += h->batch) {
+        int bs = batch_size(h, s0);
+        CHECK(zero_slots(h, bs));
+        CHECK(run_loop(h, G_MODEL, s0, bs, [&]() -> lsrtm_status {
+            if (is3d(h)) {
+                Step3D a = step3_args(h, s0);
+                a.rec_bg = 1;
+                for (int n = 0; n < nt; ++n) {
+                    a.n = n;
+                    CU(launch_fwd3d(a, bs, false, false, false, 3, h->work));
+                }
+                return LSRTM_OK;
+            }
+            CHECK(gather_model(h, s0, bs, false));
+            Step2D a = step_args(h, s0);
+            a.rec_bg = 1;
+            for (int n = 0; n < nt; ++n) {
+                a.n = n;
+                a.in = h->st[n & 1];
+                a.out = h->st[(n + 1) & 1];
+                CU(launch_fwd2d(a, bs, false, false, false, h->work));
+            }
+            return LSRTM_OK;
+        }));
+    }
+    return LSRTM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Checkpointed reconstruction. The forward background pass of a batch saves
 // the full background state every K steps; the reverse pass then walks the
@@ -943,6 +980,16 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
     h->nrec_total = geo->rec_ptr[h->nshot];
     h->rec_ptr.assign(geo->rec_ptr, geo->rec_ptr + h->nshot + 1);
     const GridDev &gm = h->gm;
+    h->rec_off_h.assign(h->nrec_total, 0.0);
+    for (int s = 0; s < h->nshot; ++s) {
+        const long long ks = geo->src_idx[s];
+        const long long xs = ks % gm.nx, ys = (ks / gm.nx) % gm.ny;
+        for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r) {
+            const long long k = geo->rec_idx[r];
+            const long long xr = k % gm.nx, yr = (k / gm.nx) % gm.ny;
+            h->rec_off_h[r] = std::hypot((double)(xr - xs) * h->cfg.dx, (double)(yr - ys) * h->cfg.dy);
+        }
+    }
     // cell of interior point k in shot s's slot grid (its window), or -1 outside the window
     auto pad_cell = [&](long long k, int s) -> long long {
         long long ix = k % gm.nx, t = k / gm.nx, iy = t % gm.ny, iz = t / gm.ny;
@@ -1380,6 +1427,60 @@ lsrtm_status lsrtm_adjoint(lsrtm_handle *h, const float *d, float *g, float *pse
         CHECK(copy_out(h, pseudo_hess, h->hess_img, h->nint));
     }
     return end_call(h, !gdev || !hdev);
+}
+
+lsrtm_status lsrtm_model(lsrtm_handle *h, float *d)
+{
+    if (!h || !d) return fail(LSRTM_ERR_ARG, "null argument");
+    CHECK(begin_call(h));
+    CHECK(model_core(h));
+    CHECK(copy_out(h, d, h->dstage, h->nrec_total * h->g.nt));
+    return end_call(h, !is_device_ptr(d));
+}
+
+lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const float *d_syn, double v_mute, double t0,
+                                 double t_taper, double o_max, double o_taper, float *d_out)
+{
+    if (!h || !d_obs || !d_out) return fail(LSRTM_ERR_ARG, "null argument");
+    if (!(v_mute > 0.0) || !(t_taper >= 0.0) || !(o_taper >= 0.0) || !std::isfinite(t0) || !std::isfinite(o_max))
+        return fail(LSRTM_ERR_ARG, "v_mute must be > 0, the tapers >= 0 and t0, o_max finite");
+    const long long nrec = h->nrec_total, nt = h->g.nt, nd = nrec * nt;
+    CHECK(begin_call(h));
+    if (!h->mute_td) {
+        CHECK(dalloc_t(h, &h->mute_td, std::max<long long>(nrec, 1)));
+        CHECK(dalloc_t(h, &h->mute_fo, std::max<long long>(nrec, 1)));
+    }
+    // per receiver, in FP64: the mute time and the far-offset factor
+    std::vector<double> td(nrec);
+    std::vector<float> fo(nrec);
+    for (long long r = 0; r < nrec; ++r) {
+        const double o = h->rec_off_h[r];
+        td[r] = o / v_mute + t0;
+        double f = 1.0;
+        if (o_max > 0.0) {
+            const double u = o_max - o;
+            if (u <= 0.0) f = 0.0;
+            else if (o_taper > 0.0 && u < o_taper) f = 0.5 * (1.0 - std::cos(3.14159265358979323846 * u / o_taper));
+        }
+        fo[r] = (float)f;
+    }
+    if (nrec > 0) {
+        CU(cudaMemcpyAsync(h->mute_td, td.data(), nrec * sizeof(double), cudaMemcpyHostToDevice, h->work));
+        CU(cudaMemcpyAsync(h->mute_fo, fo.data(), nrec * sizeof(float), cudaMemcpyHostToDevice, h->work));
+    }
+    const float *a, *b = nullptr;
+    CHECK(stage_in(h, d_obs, h->dstage, nd, &a));
+    if (d_syn) {
+        if (!is_device_ptr(d_syn) && !h->dstage2) CHECK(dalloc_t(h, &h->dstage2, std::max<long long>(nd, 1)));
+        CHECK(stage_in(h, d_syn, h->dstage2, nd, &b));
+    }
+    const bool odev = is_device_ptr(d_out);
+    float *od = odev ? d_out : h->dstage;
+    CU(launch_mute_residual(a, b, h->mute_td, h->mute_fo, nrec, (int)nt, h->cfg.dt, t_taper, od, h->work));
+    h->launches++;
+    if (!odev) CHECK(copy_out(h, d_out, od, nd));
+    // the host vectors must outlive the queued copies
+    return end_call(h, true);
 }
 
 lsrtm_status lsrtm_remigrate(lsrtm_handle *h, const float *m, float *out)

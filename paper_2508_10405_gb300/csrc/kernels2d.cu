@@ -472,15 +472,24 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
         }
     }
 
-    if (BORN) {
-        // record dp^{n+1} at the receivers of this CTA
+    if (BORN || a.rec_bg) {
+        // record dp^{n+1} (Born) or the background p^{n+1} (nonlinear
+        // modelling) at the receivers of this CTA
         __syncthreads();
         int tile = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
         int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
-        const float2 *po = reinterpret_cast<const float2 *>(a.out + slot * a.sstride + B_P * plane);
-        for (int i = b + t; i < e; i += NTH) {
-            int2 rc = a.trec.rec[i];
-            a.dstage[(long long)rc.y * g.nt + a.n] = po[rc.x].y;
+        if constexpr (BORN) {
+            const float2 *po = reinterpret_cast<const float2 *>(a.out + slot * a.sstride + B_P * plane);
+            for (int i = b + t; i < e; i += NTH) {
+                int2 rc = a.trec.rec[i];
+                a.dstage[(long long)rc.y * g.nt + a.n] = a.rec_bg ? po[rc.x].x : po[rc.x].y;
+            }
+        } else {
+            const float *po = a.out + slot * a.sstride + G_P * plane;
+            for (int i = b + t; i < e; i += NTH) {
+                int2 rc = a.trec.rec[i];
+                a.dstage[(long long)rc.y * g.nt + a.n] = po[rc.x];
+            }
         }
     }
 }

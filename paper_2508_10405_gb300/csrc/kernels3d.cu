@@ -259,12 +259,16 @@ __global__ void __launch_bounds__(256) k3_p(const Step3D a)
             a.hess[c.slot * plane + cc] += dt * (0.5f * hr / (bi * bi) + kq * kq);
         }
     }
-    if (BORN) {
+    if (BORN || a.rec_bg) {
+        // record dp^{n+1} (Born) or the background p^{n+1} (nonlinear modelling)
         const int k = a.rmap[(long long)shot * plane + cc];
         if (k >= 0) {
+            float v;
+            if constexpr (BORN) v = a.rec_bg ? xof(pn) : yof(pn);
+            else v = xof(pn);
             const int e = a.rptr[shot + 1];
             for (int q = k; q < e && a.rcell[q] == cc; ++q)
-                a.dstage[(long long)a.rrow[q] * g.nt + a.n] = yof(pn);
+                a.dstage[(long long)a.rrow[q] * g.nt + a.n] = v;
         }
     }
 }

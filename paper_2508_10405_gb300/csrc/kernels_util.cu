@@ -1,7 +1,10 @@
 // Small kernels around the time loop: model and perturbation preparation
 // (Sec. 2 parameter map), residual injection, stacking of the per-shot images
 // and the chain rule of Sec. 3, pseudo-Hessian stacking (App. B), the spike
-// comb of App. D and the FP64-accumulated vector kernels of the CGNR driver.
+// comb of App. D, the muted data residual of Sec. 4 and the FP64-accumulated
+// vector kernels of the CGNR driver.
+#include <algorithm>
+
 #include "lsrtm_internal.cuh"
 
 namespace lsrtm {
@@ -281,6 +284,30 @@ __global__ void k_nonfinite(const float *x, long long n, int *flag)
     if (bad && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// out[r][n] = mask(r, n) (dobs[r][n] - dsyn[r][n]): the direct-wave mute
+// ramp(t_n - td[r], 1 / inv_tt) (a step when inv_tt = 0; t_n = (n + 1) dt,
+// computed in FP64) times the far-offset factor fo[r]. One block per receiver
+// row at a time, threads along the samples.
+__global__ void k_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
+                                long long nrec, int nt, double dt, double inv_tt, float *out)
+{
+    for (long long r = blockIdx.x; r < nrec; r += gridDim.x) {
+        const double t_d = td[r];
+        const float f = fo[r];
+        const long long base = r * nt;
+        for (int n = threadIdx.x; n < nt; n += blockDim.x) {
+            const double u = (n + 1) * dt - t_d;
+            float m = 0.f;
+            if (u > 0.0) {
+                const double v = u * inv_tt;
+                m = (inv_tt <= 0.0 || v >= 1.0) ? 1.f : 0.5f * (1.f - cospif((float)v));
+            }
+            const float d = dsyn ? dobs[base + n] - dsyn[base + n] : dobs[base + n];
+            out[base + n] = (m * f) * d;
+        }
+    }
+}
+
 __global__ void k_comb(GridDev g, int param, int spacing, float *m)
 {
     long long nint = (long long)g.nz * g.ny * g.nx;
@@ -431,6 +458,16 @@ cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s)
 {
     k_maxabs<<<grid_for(n), NT, 0, s>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
+                                 long long nrec, int nt, double dt, double t_taper, float *out, cudaStream_t s)
+{
+    if (nrec <= 0 || nt <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>(nrec, 152 * 16);
+    k_mute_residual<<<blocks, NT, 0, s>>>(dobs, dsyn, td, fo, nrec, nt, dt, t_taper > 0.0 ? 1.0 / t_taper : 0.0,
+                                          out);
     return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ struct Step2D {
     float src_scale;      // dt / cell volume
     TileRecs trec;
     float *dstage;        // [nrec_total][nt]: records (forward) or residual (adjoint)
+    int rec_bg;           // forward: record the background p instead of dp (nonlinear modelling)
     Bands bands;
     float *hess;          // [batch][plane] pseudo-Hessian accumulators (or null)
     float2 *img;          // [batch][plane] image accumulators (adjoint)
@@ -147,6 +148,7 @@ struct Step3D {
     Bands bands;
     float *hess;              // [batch][plane]
     float *dstage;            // records (forward) or residual (adjoint), [nrec_total][nt]
+    int rec_bg;               // forward: record the background p instead of dp (nonlinear modelling)
     const int *rmap;          // [nshot][plane]: first entry of the node's receivers in rcell/rrow, or -1
     const int *rptr;          // [nshot+1] per-shot ranges of rcell/rrow
     const int *rcell;         // receiver cells, sorted by cell within a shot
@@ -233,6 +235,9 @@ cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out
                                  cudaStream_t s);
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s);
+// Muted data residual: out = ramp((n + 1) dt - td[r], t_taper) fo[r] (dobs - dsyn), dsyn nullable.
+cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
+                                 long long nrec, int nt, double dt, double t_taper, float *out, cudaStream_t s);
 cudaError_t launch_comb(const GridDev &g, int param, int spacing, float *m, cudaStream_t s);
 // rmap[rcell[q]] = q for the first receiver q of each node in [q0, q1) (3D receiver maps).
 cudaError_t launch_rmap_scatter(int *rmap, const int *rcell, int q0, int q1, cudaStream_t s);
