@@ -72,6 +72,9 @@ def parse():
                     help="time the image-domain CGNR with the interpolated PSF Hessian (App. D) "
                          "on the marine-line image instead of the data-domain iteration")
     ap.add_argument("--psf-iters", type=int, default=100, help="CGNR iterations per --psf-cg step")
+    ap.add_argument("--model", action="store_true",
+                    help="time the data-domain input pipeline (nonlinear modelling in the true and the "
+                         "background model, muted residual) instead of the CGNR iteration")
     return ap.parse_args()
 
 
@@ -385,11 +388,168 @@ def psf_reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# Background-only time step: p, vx, vz read and written + dt kappa and 1/rho.
+MODEL_BYTES_PER_CELL = {2: 32.0, 3: 40.0}
+
+
+def true_model(w):
+    """The true model behind a preset's background and perturbation: the ln map
+    of Sec. 2 inverted, v = v0 e^{dm1}, rho = rho0 e^{dm2 - dm1}."""
+    return w.vp * np.exp(w.dm[0]), w.rho * np.exp(w.dm[1] - w.dm[0])
+
+
+def mute_args(w):
+    """Direct-wave mute after offset / v_top + 2 / f0 (a Ricker's length),
+    rising over 0.25 / f0; far-offset cut at 3/4 of the spread, tapered over
+    1/8 of it."""
+    spread = w.nx * w.dx
+    return (float(np.min(w.vp[0])), 2.0 / w.f0, 0.25 / w.f0, 0.75 * spread, 0.125 * spread)
+
+
+def model_cpu_sample(w, seconds, reps=1):
+    """The FP64 oracle's nonlinear modelling on a bounded sample (shots x first
+    steps); G cell-updates/s."""
+    import oracle
+    threads = oracle.num_threads()
+    if getattr(w.geom, "win_nx", None) is not None:
+        threads = 1
+    nshot = min(w.geom.nshot, max(1, threads))
+    geom = w.geom.subset(list(range(nshot)))
+    ncell = float(np.mean(shot_cells(w)[:nshot]))
+    ts = []
+    for nt_c in (4, 20):
+        t0 = time.perf_counter()
+        oracle.model(w, geom=geom, nt=nt_c)
+        ts.append(time.perf_counter() - t0)
+    per_step = max((ts[1] - ts[0]) / 16.0, 1e-6)
+    nt_s = int(max(16, min(w.nt, seconds / per_step)))
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.model(w, geom=geom, nt=nt_s)
+        times.append(time.perf_counter() - t0)
+    cells = nshot * ncell * nt_s
+    desc = (f"oracle nonlinear modelling of {nshot} of {w.geom.nshot} shots x first {nt_s} of {w.nt} steps "
+            f"({cells:.3g} cell-updates), FP64, " + ("one thread" if threads == 1 else "OpenMP over shots"))
+    return cells / min(times) / 1e9, threads, desc, times
+
+
+def model_bench(args, rank, world, local):
+    import dataclasses as dc
+    import torch
+    from paper_2508_10405_gb300 import Lsrtm
+    w = workload(args)
+    K, W = args.steps, args.warmup
+    vt, rt = true_model(w)
+    vmax = float(max(np.max(vt), np.max(w.vp)))
+    h_bg = Lsrtm.from_workload(w, pml_vmax=vmax)
+    h_tr = Lsrtm.from_workload(dc.replace(w, vp=vt, rho=rt), pml_vmax=vmax)
+    margs = mute_args(w)
+    d_obs = torch.empty((h_bg.nrec_total, h_bg.nt), dtype=torch.float32, device="cuda")
+    d_bg = torch.empty_like(d_obs)
+    res = torch.empty_like(d_obs)
+
+    def step():
+        h_tr.model(out=d_obs)
+        h_bg.model(out=d_bg)
+        h_bg.mute_residual(d_obs, d_bg, *margs, out=res)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    for h in (h_bg, h_tr):
+        h.timing(True)
+        h.timings(reset=True)
+    l0 = h_bg.kernel_launches() + h_tr.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / 1e3 / K
+    launches = h_bg.kernel_launches() + h_tr.kernel_launches() - l0
+    tms = [h.timings(reset=True) for h in (h_bg, h_tr)]
+    # the mute alone, device buffers
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record()
+    for _ in range(5):
+        h_bg.mute_residual(d_obs, d_bg, *margs, out=res)
+    m1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    mute_s = m0.elapsed_time(m1) / 1e3 / 5
+    cells_per_model = float(shot_cells(w).sum()) * w.nt
+    value = 2.0 * cells_per_model * world / t_step / 1e9
+    ms = sum(tm["background_ms"] for tm in tms)
+    nl = sum(tm["background_launches"] for tm in tms)
+    cells = sum(tm["background_cells"] for tm in tms)
+    bpc = MODEL_BYTES_PER_CELL[w.ndim]
+    achieved = bpc * (cells / nl) / (ms / 1e3 / nl) / 1e9
+    peak, peak_kind = peaks()
+    nd = h_bg.nrec_total * h_bg.nt
+    # end to end: the records and the residual to pinned host memory
+    hb = torch.empty((h_bg.nrec_total, h_bg.nt), dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(max(K, 1)):
+        h_tr.model(out=d_obs)
+        h_bg.model(out=d_bg)
+        h_bg.mute_residual(d_obs, d_bg, *margs, out=hb)
+        torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / max(K, 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, threads, desc, _ = model_cpu_sample(w, args.cpu_seconds)
+        cpu = {"value": val, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": "nonlinear modelling Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "nt": w.nt, "order": w.order,
+                       "shots_per_rank": w.geom.nshot,
+                       "step": "observed data in the true model + background data + muted residual",
+                       "mute": dict(zip(["v_mute", "t0", "t_taper", "o_max", "o_taper"], margs)),
+                       "l2": "inputs larger than L2 (state of all shots of a batch)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_fwd2d<background>",
+                         "algorithmic_bytes_per_cell": bpc, "avg_launch_ms": ms / nl,
+                         "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"},
+            "mute": {"ms": mute_s * 1e3, "gbs": 12.0 * nd / mute_s / 1e9, "bytes_per_sample": 12},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": 2.0 * cells_per_model * world / te / 1e9, "unit": "Gcell-updates/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(nd * 4),
+                    "calls": "lsrtm_model x2 + lsrtm_mute_residual into pinned host memory"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h_bg.close()
+    h_tr.close()
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
     if args.psf_cg:
         psf_reference_arm(args)
+        return
+    if args.model:
+        w = workload(args)
+        K, W = args.steps, args.warmup
+        per = max(2.0, min(args.cpu_seconds, 120.0 / max(K + W, 1)))
+        val, threads, desc, times = model_cpu_sample(w, per, reps=max(K, 1))
+        line = {"impl": "reference", "metric": "nonlinear modelling Gcell-updates/s", "value": val,
+                "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": K, "warmup": W,
+                "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "grid": [w.nz, w.nx], "nt": w.nt, "sample": desc},
+                "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": threads, "kind": "oracle",
+                                 "sample": desc},
+                "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     w = workload(args)
     K, W = args.steps, args.warmup
@@ -465,6 +625,9 @@ def main():
     torch.cuda.set_device(local)
     if args.psf_cg:
         psf_cg_bench(args, rank, world, local)
+        return
+    if args.model:
+        model_bench(args, rank, world, local)
         return
     if world > 1:
         dist.init_process_group("nccl")
