@@ -74,7 +74,8 @@ struct lsrtm_handle {
     long long nint = 0;
     std::vector<int> rec_ptr;
     std::vector<double> rec_off_h;   // horizontal source-receiver offset of every receiver row (m)
-    double *mute_td = nullptr;       // muting: per receiver the direct-wave mute time
+    int *mute_n0 = nullptr;          // muting: per receiver the first sample after the mute time
+    float *mute_a0 = nullptr;        // muting: per receiver (t_n0 - mute time) / taper
     float *mute_fo = nullptr;        // muting: per receiver the far-offset factor
     float *dstage2 = nullptr;        // second [nrec_total][nt] stage (host inputs of the muting)
     // device model and geometry
@@ -1446,16 +1447,26 @@ lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const floa
         return fail(LSRTM_ERR_ARG, "v_mute must be > 0, the tapers >= 0 and t0, o_max finite");
     const long long nrec = h->nrec_total, nt = h->g.nt, nd = nrec * nt;
     CHECK(begin_call(h));
-    if (!h->mute_td) {
-        CHECK(dalloc_t(h, &h->mute_td, std::max<long long>(nrec, 1)));
+    if (!h->mute_n0) {
+        CHECK(dalloc_t(h, &h->mute_n0, std::max<long long>(nrec, 1)));
+        CHECK(dalloc_t(h, &h->mute_a0, std::max<long long>(nrec, 1)));
         CHECK(dalloc_t(h, &h->mute_fo, std::max<long long>(nrec, 1)));
     }
-    // per receiver, in FP64: the mute time and the far-offset factor
-    std::vector<double> td(nrec);
-    std::vector<float> fo(nrec);
+    // per receiver, in FP64: the mute time td = o / v_mute + t0, the first
+    // sample n0 with t_n = (n + 1) dt past it, (t_n0 - td) / t_taper, and the
+    // far-offset factor
+    const double dt = h->cfg.dt;
+    std::vector<int> n0(nrec);
+    std::vector<float> a0(nrec), fo(nrec);
     for (long long r = 0; r < nrec; ++r) {
         const double o = h->rec_off_h[r];
-        td[r] = o / v_mute + t0;
+        const double td = o / v_mute + t0;
+        long long n = (long long)std::floor(td / dt) - 1;   // then step to the first n with (n + 1) dt - td > 0
+        n = std::max<long long>(n, 0);
+        while (n < nt && (n + 1) * dt - td <= 0.0) ++n;
+        while (n > 0 && n * dt - td > 0.0) --n;
+        n0[r] = (int)std::min<long long>(n, nt);
+        a0[r] = t_taper > 0.0 ? (float)(((n0[r] + 1) * dt - td) / t_taper) : 0.f;
         double f = 1.0;
         if (o_max > 0.0) {
             const double u = o_max - o;
@@ -1465,7 +1476,8 @@ lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const floa
         fo[r] = (float)f;
     }
     if (nrec > 0) {
-        CU(cudaMemcpyAsync(h->mute_td, td.data(), nrec * sizeof(double), cudaMemcpyHostToDevice, h->work));
+        CU(cudaMemcpyAsync(h->mute_n0, n0.data(), nrec * sizeof(int), cudaMemcpyHostToDevice, h->work));
+        CU(cudaMemcpyAsync(h->mute_a0, a0.data(), nrec * sizeof(float), cudaMemcpyHostToDevice, h->work));
         CU(cudaMemcpyAsync(h->mute_fo, fo.data(), nrec * sizeof(float), cudaMemcpyHostToDevice, h->work));
     }
     const float *a, *b = nullptr;
@@ -1476,7 +1488,8 @@ lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const floa
     }
     const bool odev = is_device_ptr(d_out);
     float *od = odev ? d_out : h->dstage;
-    CU(launch_mute_residual(a, b, h->mute_td, h->mute_fo, nrec, (int)nt, h->cfg.dt, t_taper, od, h->work));
+    CU(launch_mute_residual(a, b, h->mute_n0, h->mute_a0, h->mute_fo, nrec, (int)nt,
+                            t_taper > 0.0 ? (float)(dt / t_taper) : 0.f, od, h->work));
     h->launches++;
     if (!odev) CHECK(copy_out(h, d_out, od, nd));
     // the host vectors must outlive the queued copies

@@ -284,26 +284,50 @@ __global__ void k_nonfinite(const float *x, long long n, int *flag)
     if (bad && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-// out[r][n] = mask(r, n) (dobs[r][n] - dsyn[r][n]): the direct-wave mute
-// ramp(t_n - td[r], 1 / inv_tt) (a step when inv_tt = 0; t_n = (n + 1) dt,
-// computed in FP64) times the far-offset factor fo[r]. One block per receiver
-// row at a time, threads along the samples.
-__global__ void k_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
-                                long long nrec, int nt, double dt, double inv_tt, float *out)
+// out[r][n] = mask(r, n) (dobs[r][n] - dsyn[r][n]). The direct-wave mute of
+// receiver r is 0 before sample n0[r] (the first sample after the mute time,
+// decided in FP64 on the host), then the raised-cosine rise
+// (1 - cos(pi v)) / 2, v = (n - n0) b + a0[r] (the time past the mute time
+// over the taper width), 1 from v >= 1 on (b = 0: a step); fo[r] is the
+// far-offset factor. One block per receiver row at a time, threads along the
+// samples, four samples per thread access when the rows are 16-byte aligned.
+__device__ __forceinline__ float mute_factor(int n, int n0, float a0, float b, float f)
+{
+    if (n < n0) return 0.f;
+    const float v = fmaf((float)(n - n0), b, a0);
+    return (b <= 0.f || v >= 1.f) ? f : f * (0.5f * (1.f - cospif(v)));
+}
+
+template <bool VEC>
+__global__ void k_mute_residual(const float *dobs, const float *dsyn, const int *n0, const float *a0,
+                                const float *fo, long long nrec, int nt, float b, float *out)
 {
     for (long long r = blockIdx.x; r < nrec; r += gridDim.x) {
-        const double t_d = td[r];
-        const float f = fo[r];
+        const int s0 = n0[r];
+        const float a = a0[r], f = fo[r];
         const long long base = r * nt;
-        for (int n = threadIdx.x; n < nt; n += blockDim.x) {
-            const double u = (n + 1) * dt - t_d;
-            float m = 0.f;
-            if (u > 0.0) {
-                const double v = u * inv_tt;
-                m = (inv_tt <= 0.0 || v >= 1.0) ? 1.f : 0.5f * (1.f - cospif((float)v));
+        if (VEC) {
+            const float4 *o4 = reinterpret_cast<const float4 *>(dobs + base);
+            const float4 *s4 = reinterpret_cast<const float4 *>(dsyn + base);
+            float4 *w4 = reinterpret_cast<float4 *>(out + base);
+            for (int q = threadIdx.x; q < nt / 4; q += blockDim.x) {
+                float4 d = o4[q];
+                if (dsyn) {
+                    const float4 e = s4[q];
+                    d.x -= e.x, d.y -= e.y, d.z -= e.z, d.w -= e.w;
+                }
+                const int n = 4 * q;
+                d.x *= mute_factor(n, s0, a, b, f);
+                d.y *= mute_factor(n + 1, s0, a, b, f);
+                d.z *= mute_factor(n + 2, s0, a, b, f);
+                d.w *= mute_factor(n + 3, s0, a, b, f);
+                w4[q] = d;
             }
-            const float d = dsyn ? dobs[base + n] - dsyn[base + n] : dobs[base + n];
-            out[base + n] = (m * f) * d;
+        } else {
+            for (int n = threadIdx.x; n < nt; n += blockDim.x) {
+                const float d = dsyn ? dobs[base + n] - dsyn[base + n] : dobs[base + n];
+                out[base + n] = mute_factor(n, s0, a, b, f) * d;
+            }
         }
     }
 }
@@ -461,13 +485,16 @@ cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
-                                 long long nrec, int nt, double dt, double t_taper, float *out, cudaStream_t s)
+cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const int *n0, const float *a0,
+                                 const float *fo, long long nrec, int nt, float b, float *out, cudaStream_t s)
 {
     if (nrec <= 0 || nt <= 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>(nrec, 152 * 16);
-    k_mute_residual<<<blocks, NT, 0, s>>>(dobs, dsyn, td, fo, nrec, nt, dt, t_taper > 0.0 ? 1.0 / t_taper : 0.0,
-                                          out);
+    const bool vec = nt % 4 == 0 &&
+                     ((reinterpret_cast<uintptr_t>(dobs) | reinterpret_cast<uintptr_t>(dsyn) |
+                       reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (vec) k_mute_residual<true><<<blocks, NT, 0, s>>>(dobs, dsyn, n0, a0, fo, nrec, nt, b, out);
+    else k_mute_residual<false><<<blocks, NT, 0, s>>>(dobs, dsyn, n0, a0, fo, nrec, nt, b, out);
     return cudaGetLastError();
 }
 

@@ -235,9 +235,11 @@ cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out
                                  cudaStream_t s);
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s);
-// Muted data residual: out = ramp((n + 1) dt - td[r], t_taper) fo[r] (dobs - dsyn), dsyn nullable.
-cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const double *td, const float *fo,
-                                 long long nrec, int nt, double dt, double t_taper, float *out, cudaStream_t s);
+// Muted data residual: out = mute(r, n) fo[r] (dobs - dsyn), dsyn nullable; the
+// mute is 0 for n < n0[r], then (1 - cos(pi v)) / 2 with v = (n - n0[r]) b + a0[r]
+// (1 for v >= 1 or b = 0).
+cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const int *n0, const float *a0,
+                                 const float *fo, long long nrec, int nt, float b, float *out, cudaStream_t s);
 cudaError_t launch_comb(const GridDev &g, int param, int spacing, float *m, cudaStream_t s);
 // rmap[rcell[q]] = q for the first receiver q of each node in [q0, q1) (3D receiver maps).
 cudaError_t launch_rmap_scatter(int *rmap, const int *rcell, int q0, int q1, cudaStream_t s);
