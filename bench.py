@@ -72,6 +72,9 @@ def parse():
                     help="time the image-domain CGNR with the interpolated PSF Hessian (App. D) "
                          "on the marine-line image instead of the data-domain iteration")
     ap.add_argument("--psf-iters", type=int, default=100, help="CGNR iterations per --psf-cg step")
+    ap.add_argument("--deblur", action="store_true",
+                    help="time the image-domain deblurring of the marine-line image: the Fourier-form "
+                         "Wiener filter (App. E) and the space-domain 11 x 11 filters")
     ap.add_argument("--model", action="store_true",
                     help="time the data-domain input pipeline (nonlinear modelling in the true and the "
                          "background model, muted residual) instead of the CGNR iteration")
@@ -530,8 +533,110 @@ def model_bench(args, rank, world, local):
     h_tr.close()
 
 
+def wiener_flops(nz, nx, s):
+    """Algorithmic FP32 flops of the Wiener blocks: per block and plane three
+    2D DFTs of N = 2s points per axis as direct sums (2 passes of N^3 complex
+    multiply-adds, 8 flops each)."""
+    nk = len(range(s // 2, nz, s)) * len(range(s // 2, nx, s))
+    N = 2 * s
+    return 2.0 * nk * 3 * 2 * N ** 3 * 8
+
+
+def deblur_bench(args, rank, world, local):
+    import torch
+    from paper_2508_10405_gb300 import Lsrtm
+    from oracle import wiener as wf
+    nz, nx, s, eps = 300, 2000, 20, 1e-3
+    K, W = args.steps, args.warmup
+    wk = li.small_case(nz=nz, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+    h = Lsrtm.from_workload(wk)
+    m, r = li.image_pair(nz, nx, seed=5)
+    md = torch.tensor(m, dtype=torch.float32, device="cuda")
+    rd = torch.tensor(r, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(md)
+    for _ in range(W):
+        h.deblur_wiener(md, rd, s, eps, out=out)
+        h.deblur(md, rd, s, 11, eps)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = h.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        h.deblur_wiener(md, rd, s, eps, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    t_w = e0.elapsed_time(e1) / 1e3 / K
+    launches = h.kernel_launches() - l0
+    e0.record()
+    for _ in range(K):
+        h.deblur(md, rd, s, 11, eps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3 / K
+    clk = clocks.stop()
+    flops = wiener_flops(nz, nx, s)
+    # end to end with host buffers
+    mh, rh = (torch.tensor(a, dtype=torch.float32).pin_memory() for a in (m, r))
+    oh = torch.empty_like(mh).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(max(K, 1)):
+        h.deblur_wiener(mh, rh, s, eps, out=oh)
+        torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / max(K, 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        wf.wiener(m, r, s, eps)
+        tc = time.perf_counter() - t0
+        cpu = {"value": 1.0 / tc, "unit": "images/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle Wiener deblurring of the whole 300 x 2000 two-parameter image (numpy FFT, FP64)"}
+    if rank == 0:
+        line = {
+            "metric": "Wiener deblurring images/s", "value": world / t_w, "unit": "images/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": t_w * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "marine-line image 300 x 2000, two parameters, comb spacing 20, 40 x 40 blocks",
+                       "eps": eps, "step": "one Wiener deblurring of the image (1500 blocks per plane, blend)",
+                       "l2": "image 4.8 MB per input: L2-resident"},
+            "roofline": {"bound": "alu", "achieved": flops / t_w / 1e12, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / t_w / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_wiener_block + k_wiener_blend", "flops_per_launch": flops,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+            "space_domain_filters": {"ms": t_s * 1e3, "kernel": "k_deblur_solve + k_deblur_apply (11 x 11, FP64 "
+                                                               "normal equations)"},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": 1.0 / te, "unit": "images/s", "h2d_bytes_per_step": int(2 * mh.numel() * 4),
+                    "d2h_bytes_per_step": int(oh.numel() * 4), "calls": "lsrtm_deblur_wiener with pinned host buffers"},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
+        return
+    if args.deblur:
+        from oracle import wiener as wf
+        m, r = li.image_pair(300, 2000, seed=5)
+        ts = []
+        for _ in range(max(args.steps, 1)):
+            t0 = time.perf_counter()
+            wf.wiener(m, r, 20, 1e-3)
+            ts.append(time.perf_counter() - t0)
+        val = 1.0 / float(np.mean(ts))
+        desc = "oracle Wiener deblurring of the whole 300 x 2000 two-parameter image (numpy FFT, FP64)"
+        print(json.dumps({"impl": "reference", "metric": "Wiener deblurring images/s", "value": val,
+                          "unit": "images/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 / val, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "marine-line image 300 x 2000, spacing 20", "sample": desc},
+                          "cpu_baseline": {"value": val, "unit": "images/s", "cores": 1, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": val, "unit": "images/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
         return
     if args.psf_cg:
         psf_reference_arm(args)
@@ -628,6 +733,9 @@ def main():
         return
     if args.model:
         model_bench(args, rank, world, local)
+        return
+    if args.deblur:
+        deblur_bench(args, rank, world, local)
         return
     if world > 1:
         dist.init_process_group("nccl")

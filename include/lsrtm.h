@@ -263,6 +263,25 @@ lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
 lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_remig, int spacing, int flen,
                           double eps, float *dm_out, float *filters);
 
+/* Nonstationary Wiener deblurring, the Fourier form of App. E. Within a local
+ * block the Hessian is taken as circulant, H = F^H Lam F, and dm = F^H Lam^-1
+ * F m_rtm (Eq. sol) with Lam^-1 from the regularised least squares of App. E,
+ * the Wiener ratio Lam_i^-1 = conj([F m'']_i) [F m']_i / (|[F m'']_i|^2 + eps_k),
+ * m' = m_rtm, m'' = L^T L m'. Blocks: per comb node (z_k, x_k) = (s/2 + i s,
+ * s/2 + j s) the 2s x 2s pixels z_k - s .. z_k + s - 1 (same in x), zero
+ * outside the image; F is the block's 2D DFT; eps_k = eps * mean_i |[F m'']_i|^2
+ * (a block with m'' = 0 gives 0); block results are blended with the bilinear
+ * valence w_k = max(0, 1 - |z - z_k|/s) max(0, 1 - |x - x_k|/s); each
+ * parameter plane on its own. FP32 DFTs.
+ *   m_rtm, m_remig : [2][nz][nx] (host or device; read only)
+ *   spacing s      : 2 <= s <= 32
+ *   eps            : relative stabiliser, > 0 (1e-3 is typical)
+ *   dm_out         : [2][nz][nx] output (host or device)
+ * Errors: LSRTM_ERR_ARG for 3D handles or parameters out of range.
+ * Asynchronous for device outputs. */
+lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const float *m_remig, int spacing, double eps,
+                                 float *dm_out);
+
 /* Interpolated PSF Hessian (migration deconvolution with PSFs, App. D) of a
  * 2D image. The PSF image of a spike comb (nodes s/2 + k s along both axes,
  * as lsrtm_psf places them) holds a localised Hessian column around each

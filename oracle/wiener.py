@@ -67,20 +67,18 @@ def wiener_plane(m_rtm: np.ndarray, m_remig: np.ndarray, s: int, eps: float) -> 
     nz, nx = m_rtm.shape
     num = np.zeros((nz, nx))
     den = np.zeros((nz, nx))
-    zz = np.arange(nz)[:, None]
-    xx = np.arange(nx)[None, :]
     for z in nodes(nz, s):
         for x in nodes(nx, s):
             dmk = block_filter(block(m_rtm, z, x, s), block(m_remig, z, x, s), eps)
-            w = np.maximum(0.0, 1.0 - np.abs(zz - z) / s) * np.maximum(0.0, 1.0 - np.abs(xx - x) / s)
-            # the hat's support lies inside the block: rows z - s + 1 .. z + s - 1
-            full = np.zeros((nz, nx))
+            # the hat's support (|z - z_k| < s, |x - x_k| < s) lies inside the
+            # block, so the sums run over the block's pixels in the image
             z0, x0 = z - s, x - s
             zs, ze = max(0, z0), min(nz, z0 + 2 * s)
             xs, xe = max(0, x0), min(nx, x0 + 2 * s)
-            full[zs:ze, xs:xe] = dmk[zs - z0:ze - z0, xs - x0:xe - x0]
-            num += w * full
-            den += w
+            wz = np.maximum(0.0, 1.0 - np.abs(np.arange(zs, ze) - z) / s)[:, None]
+            wx = np.maximum(0.0, 1.0 - np.abs(np.arange(xs, xe) - x) / s)[None, :]
+            num[zs:ze, xs:xe] += wz * wx * dmk[zs - z0:ze - z0, xs - x0:xe - x0]
+            den[zs:ze, xs:xe] += wz * wx
     return np.where(den > 0.0, num / np.where(den > 0.0, den, 1.0), 0.0)
 
 

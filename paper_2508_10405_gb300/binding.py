@@ -30,7 +30,8 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_timing_enable", "lsrtm_timing_read", "lsrtm_set_stream",
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
            "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune",
-           "lsrtm_psf_hessian", "lsrtm_psf_cg", "lsrtm_model", "lsrtm_mute_residual"]
+           "lsrtm_psf_hessian", "lsrtm_psf_cg", "lsrtm_model", "lsrtm_mute_residual",
+           "lsrtm_deblur_wiener"]
 
 
 class LsrtmError(RuntimeError):
@@ -101,6 +102,7 @@ def load_library(path: str | None = None):
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
     L.lsrtm_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double), ip]
     L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+    L.lsrtm_deblur_wiener.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
     L.lsrtm_model.argtypes = [vp, vp]
     L.lsrtm_mute_residual.argtypes = [vp, vp, vp] + [ctypes.c_double] * 5 + [vp]
     L.lsrtm_psf_hessian.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -340,6 +342,16 @@ class Lsrtm:
                                       int(spacing), int(half), int(param_mask), _ptr(m), _ptr(out), int(niter),
                                       mis))
         return out, np.array(list(mis))
+
+    def deblur_wiener(self, m_rtm, m_remig, spacing=20, eps=1e-3, out=None):
+        """Nonstationary Wiener deblurring (App. E, Fourier form): per comb
+        node a 2s x 2s block filtered by conj(F m'') F m_rtm / (|F m''|^2 +
+        eps mean|F m''|^2), blended with the bilinear valence."""
+        self._sync_stream()
+        a, b = _f32(m_rtm), _f32(m_remig)
+        out = self._empty((2,) + self.shape) if out is None else out
+        _check(self._lib.lsrtm_deblur_wiener(self._h, _ptr(a), _ptr(b), int(spacing), float(eps), _ptr(out)))
+        return out
 
     def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3):
         """CGNR / PCGNR; returns (dm, misfit history of length niter+1)."""

@@ -20,11 +20,14 @@
 // memory (121 x 121 doubles = 117 KB for flen = 11).
 // k_deblur_apply: one thread per pixel and plane; FP32 taps, at most four
 // covering nodes.
+// The paper's own Fourier form of the filter (per-block Wiener ratio) follows
+// below the space-domain kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "lsrtm_internal.cuh"
+#include "wiener.cuh"
 
 namespace lsrtm {
 
@@ -195,7 +198,176 @@ __global__ void k_deblur_apply(const float *mref, const float *filt, int nz, int
     out[param * plane + i] = den > 0.f ? num / den : 0.f;
 }
 
+// ---------------------------------------------------------------------------
+// Nonstationary Wiener filter (App. E, Fourier form). Per comb node a block of
+// N x N = 2s x 2s pixels (z_k - s .. z_k + s - 1, the same in x; zero outside
+// the image). With A = F m'' and B = F m_rtm (F the N x N DFT) the block's
+// result is Re F^-1 [conj(A) B / (|A|^2 + eps_k) B], eps_k = eps mean|A|^2
+// (zero when m'' is zero), and the blocks are blended with the bilinear
+// valence of the space-domain filters.
+//
+// k_wiener_block: one CTA per (node, plane); the block, its spectra and a
+// transform buffer sit in shared memory as complex FP32; each 2D DFT is two
+// passes of direct N-term sums (rows, then columns) with a twiddle table;
+// the block result goes to blk[plane][node][N*N].
+// k_wiener_blend: one thread per pixel, the (up to) four covering blocks.
+// ---------------------------------------------------------------------------
+constexpr int kWienerThreads = 256, kWienerMaxS = 32;
+
+// dst = DFT2(src) (sign -1) or the unscaled inverse (sign +1), via tmp.
+__device__ void dft2(const float2 *src, float2 *tmp, float2 *dst, const float2 *tw, int N, bool inverse)
+{
+    const int NN = N * N;
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {   // along x: tmp[r][k] = sum_n src[r][n] w^(k n)
+        const int r = idx / N, k = idx - r * N;
+        const float2 *row = src + r * N;
+        float re = 0.f, im = 0.f;
+        int j = 0;
+        for (int n = 0; n < N; ++n) {
+            const float2 w = tw[j];
+            const float wi = inverse ? w.y : -w.y;
+            const float2 v = row[n];
+            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
+            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
+            j += k;
+            if (j >= N) j -= N;
+        }
+        tmp[idx] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {   // along z: dst[k][c] = sum_n tmp[n][c] w^(k n)
+        const int k = idx / N, c = idx - k * N;
+        float re = 0.f, im = 0.f;
+        int j = 0;
+        for (int n = 0; n < N; ++n) {
+            const float2 w = tw[j];
+            const float wi = inverse ? w.y : -w.y;
+            const float2 v = tmp[n * N + c];
+            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
+            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
+            j += k;
+            if (j >= N) j -= N;
+        }
+        dst[idx] = make_float2(re, im);
+    }
+    __syncthreads();
+}
+
+__device__ void load_block(const float *g, int nz, int nx, int zc, int xc, int N, float2 *dst)
+{
+    const int s = N / 2;
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        const int a = idx / N, b = idx - a * N;
+        const int z = zc - s + a, x = xc - s + b;
+        const float v = (z >= 0 && z < nz && x >= 0 && x < nx) ? g[(long long)z * nx + x] : 0.f;
+        dst[idx] = make_float2(v, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(kWienerThreads) k_wiener_block(const float *mref, const float *mrem, int nz, int nx,
+                                                                 int s, int nkx, float eps, float *blk)
+{
+    extern __shared__ __align__(16) float2 wsm[];
+    const int N = 2 * s, NN = N * N;
+    float2 *tw = wsm;            // [N] (cos, sin)(2 pi k / N)
+    float2 *P = tw + N;          // [NN] input / product
+    float2 *Q = P + NN;          // [NN] transform buffer
+    float2 *A = Q + NN;          // [NN] F m''
+    float2 *B = A + NN;          // [NN] F m_rtm
+    __shared__ float red[kWienerThreads / 32];
+    const int node = blockIdx.x, plane = blockIdx.y;
+    const int kz = node / nkx, kx = node - kz * nkx;
+    const int zc = s / 2 + kz * s, xc = s / 2 + kx * s;
+    const long long pl = (long long)nz * nx;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)N, &sn, &cs);
+        tw[k] = make_float2(cs, sn);
+    }
+    load_block(mrem + plane * pl, nz, nx, zc, xc, N, P);
+    __syncthreads();
+    dft2(P, Q, A, tw, N, false);
+    load_block(mref + plane * pl, nz, nx, zc, xc, N, P);
+    __syncthreads();
+    dft2(P, Q, B, tw, N, false);
+    // eps_k = eps * mean |A|^2
+    float pw = 0.f;
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) pw = fmaf(A[idx].x, A[idx].x, fmaf(A[idx].y, A[idx].y, pw));
+    for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pw;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < kWienerThreads / 32; ++w) tot += red[w];
+    const float eps_k = eps * tot / (float)NN;
+    // P = Lam^-1 B = conj(A) B B / (|A|^2 + eps_k)
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+        float2 r = make_float2(0.f, 0.f);
+        if (tot > 0.f) {
+            const float2 a = A[idx], b = B[idx];
+            const float den = fmaf(a.x, a.x, fmaf(a.y, a.y, eps_k));
+            const float2 l = make_float2((a.x * b.x + a.y * b.y) / den, (a.x * b.y - a.y * b.x) / den);   // conj(a) b / den
+            r = make_float2(l.x * b.x - l.y * b.y, l.x * b.y + l.y * b.x);
+        }
+        P[idx] = r;
+    }
+    __syncthreads();
+    dft2(P, Q, A, tw, N, true);
+    float *out = blk + ((long long)plane * gridDim.x + node) * NN;
+    const float scale = 1.f / (float)NN;
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) out[idx] = A[idx].x * scale;
+}
+
+__global__ void k_wiener_blend(const float *blk, int nz, int nx, int s, int nkz, int nkx, float *out)
+{
+    const long long plane = (long long)nz * nx;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= plane) return;
+    const int param = blockIdx.y;
+    const int z = (int)(i / nx), x = (int)(i - (long long)(i / nx) * nx);
+    const int N = 2 * s, NN = N * N;
+    const int iz = z >= s / 2 ? (z - s / 2) / s : -1, ix = x >= s / 2 ? (x - s / 2) / s : -1;
+    float num = 0.f, den = 0.f;
+    for (int a = 0; a < 2; ++a) {
+        const int kz = iz + a;
+        if (kz < 0 || kz >= nkz) continue;
+        const int dz = z - (s / 2 + kz * s);
+        const float wz = fmaxf(0.f, 1.f - fabsf((float)dz) / s);
+        for (int b = 0; b < 2; ++b) {
+            const int kx = ix + b;
+            if (kx < 0 || kx >= nkx) continue;
+            const int dx = x - (s / 2 + kx * s);
+            const float w = wz * fmaxf(0.f, 1.f - fabsf((float)dx) / s);
+            if (w <= 0.f) continue;
+            num = fmaf(w, blk[(((long long)param * nkz + kz) * nkx + kx) * NN + (dz + s) * N + (dx + s)], num);
+            den += w;
+        }
+    }
+    out[param * plane + i] = den > 0.f ? num / den : 0.f;
+}
+
 }  // namespace
+
+int wiener_max_spacing() { return kWienerMaxS; }
+
+size_t wiener_smem(int s)
+{
+    const size_t N = 2 * (size_t)s;
+    return (N + 4 * N * N) * sizeof(float2);
+}
+
+cudaError_t launch_wiener(const float *mref, const float *mrem, int nz, int nx, int s, double eps, float *blk,
+                          float *out, cudaStream_t st)
+{
+    const int nkz = deblur_nodes(nz, s), nkx = deblur_nodes(nx, s);
+    const size_t sm = wiener_smem(s);
+    cudaError_t e = cudaFuncSetAttribute(k_wiener_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_wiener_block<<<dim3(nkz * nkx, 2), kWienerThreads, sm, st>>>(mref, mrem, nz, nx, s, nkx, (float)eps, blk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long plane = (long long)nz * nx;
+    k_wiener_blend<<<dim3((unsigned)((plane + 255) / 256), 2), 256, 0, st>>>(blk, nz, nx, s, nkz, nkx, out);
+    return cudaGetLastError();
+}
 
 size_t deblur_solve_smem(int nz, int nx, int s, int flen)
 {

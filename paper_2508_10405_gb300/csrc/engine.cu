@@ -19,6 +19,7 @@
 
 #include "../../include/lsrtm.h"
 #include "lsrtm_internal.cuh"
+#include "wiener.cuh"
 
 using namespace lsrtm;
 
@@ -127,6 +128,8 @@ struct lsrtm_handle {
     float *db_filt = nullptr;    // deblurring filters, grown on demand
     size_t db_cap = 0;
     float *db_out = nullptr;     // [2][nint]
+    float *wn_blk = nullptr;     // Wiener block results, grown on demand
+    size_t wn_cap = 0;
     // interpolated PSF Hessian (App. D)
     float4 *ph_pt = nullptr;     // node windows, grown on demand
     size_t ph_cap = 0;
@@ -1757,6 +1760,35 @@ lsrtm_status lsrtm_deblur(lsrtm_handle *h, const float *m_rtm, const float *m_re
     if (flag) return fail(LSRTM_ERR_NONFINITE, "deblurring normal equations not positive definite (eps too small "
                                               "or non-finite images); those filters are set to zero");
     return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const float *m_remig, int spacing, double eps,
+                                 float *dm_out)
+{
+    if (!h || !m_rtm || !m_remig || !dm_out) return fail(LSRTM_ERR_ARG, "null argument");
+    if (h->g.ndim != 2) return fail(LSRTM_ERR_ARG, "lsrtm_deblur_wiener supports 2D images only");
+    if (spacing < 2 || spacing > wiener_max_spacing()) return fail(LSRTM_ERR_ARG, "spacing must be in [2, 32]");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(LSRTM_ERR_ARG, "eps must be > 0");
+    const int nz = h->gm.nz, nx = h->gm.nx;
+    if (nz <= spacing / 2 || nx <= spacing / 2)
+        return fail(LSRTM_ERR_ARG, "image smaller than half the node spacing: no deblurring node");
+    const int nkz = deblur_nodes(nz, spacing), nkx = deblur_nodes(nx, spacing);
+    const size_t nb = 2 * (size_t)nkz * nkx * 4 * spacing * spacing;
+    CHECK(begin_call(h));
+    if (nb > h->wn_cap) {
+        CHECK(dalloc_t(h, &h->wn_blk, nb));
+        h->wn_cap = nb;
+    }
+    if (!h->db_out) CHECK(dalloc_t(h, &h->db_out, 2 * (size_t)h->nint));
+    const float *a, *b;
+    CHECK(stage_in(h, m_rtm, h->mstage, 2 * h->nint, &a));
+    CHECK(stage_in(h, m_remig, h->gstage, 2 * h->nint, &b));
+    const bool odev = is_device_ptr(dm_out);
+    float *od = odev ? dm_out : h->db_out;
+    CU(launch_wiener(a, b, nz, nx, spacing, eps, h->wn_blk, od, h->work));
+    h->launches += 2;
+    if (!odev) CHECK(copy_out(h, dm_out, od, 2 * h->nint));
+    return end_call(h, !odev);
 }
 
 }  // extern "C"
