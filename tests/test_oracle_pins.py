@@ -315,6 +315,23 @@ def test_psf_is_sum_of_hessian_columns():
         np.testing.assert_allclose(got, H @ cmb.ravel(), rtol=0, atol=1e-12 * np.abs(H).max())
 
 
+def test_remigration_is_symmetric_and_positive():
+    """App. D/E: H = L^T L is symmetric and positive semi-definite, so the
+    remigration satisfies <H x, y> = <x, H y> and <H x, x> = |L x|^2 >= 0
+    (2D and 3D, CPML active)."""
+    for w in (li.small_case(nz=16, nx=20, nt=120, order=8, npml=6, nshot=2, seed=31, nrec=10),
+              li.small_case(ndim=3, nz=8, ny=9, nx=10, nt=50, order=4, npml=4, nshot=1, seed=32, nrec=6)):
+        rng = np.random.default_rng(7)
+        x = rng.standard_normal((2,) + w.shape)
+        y = rng.standard_normal((2,) + w.shape)
+        hx = oracle.remigrate(w, x)
+        hy = oracle.remigrate(w, y)
+        a, b = float(np.vdot(hx, y)), float(np.vdot(x, hy))
+        assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+        lx = oracle.born(w, x)
+        assert abs(float(np.vdot(hx, x)) - float(np.vdot(lx, lx))) <= 1e-12 * float(np.vdot(lx, lx))
+
+
 def test_pseudo_hessian_plane_wave():
     """App. B in nondimensional units (c = rho = 1): for a plane wave
     rho^2 |dv/dt|^2 = |grad p|^2 = |dp/dt|^2 = kappa^2 (div v)^2, so the
