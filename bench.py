@@ -800,10 +800,13 @@ def main():
     bpc = BYTES_PER_CELL[(dom, w.ndim)]
     achieved = bpc * cells_per_launch / avg_launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = ncu_traffic({"born": "k_fwd2d_born", "adjoint": "k_adj2d"}[dom], cells_per_launch)
+    # the committed DRAM counters are for the 2D kernels; 3D has none on the current source
+    traffic = ncu_traffic({"born": "k_fwd2d_born", "adjoint": "k_adj2d"}[dom], cells_per_launch) \
+        if w.ndim == 2 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": {"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"}[dom],
+                "kernel": ({"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"} if w.ndim == 2
+                           else {"born": "k3_v + k3_p <BORN>", "adjoint": "k3_a + k3_b"})[dom],
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_cell": bpc, "cells_per_launch": cells_per_launch,
