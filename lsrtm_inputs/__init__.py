@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "Geometry", "preset", "PRESETS", "ricker", "gardner_rho",
-    "gaussian_blobs", "small_case", "image_pair", "psf_images",
+    "gaussian_blobs", "small_case", "image_pair", "psf_images", "psf_images3",
 ]
 
 
@@ -454,4 +454,41 @@ def psf_images(nz: int = 300, nx: int = 2000, spacing: int = 20, seed: int = 9,
                     z0, z1 = max(0, z - r), min(nz, z + r + 1)
                     x0, x1 = max(0, x - r), min(nx, x + r + 1)
                     out[j][q, z0:z1, x0:x1] += amp * blob[z0 - z + r:z1 - z + r, x0 - x + r:x1 - x + r]
+    return out[0], out[1]
+
+
+def psf_images3(nz: int, ny: int, nx: int, spacing: int, seed: int = 9,
+                cross: float = 0.3) -> tuple[np.ndarray, np.ndarray]:
+    """3D counterpart of psf_images: (psf_vp, psf_ip), each [2, nz, ny, nx],
+    a blob around every node of the 3D comb (a Mexican hat along a tilted
+    axis in the z-x plane times Gaussians across it) with depth-dependent
+    width and amplitude, seeded per-node jitter, and odd-symmetric
+    cross-parameter responses."""
+    rng = np.random.default_rng(seed)
+    zk = np.arange(spacing // 2, nz, spacing)
+    yk = np.arange(spacing // 2, ny, spacing)
+    xk = np.arange(spacing // 2, nx, spacing)
+    out = [np.zeros((2, nz, ny, nx)), np.zeros((2, nz, ny, nx))]
+    r = max(1, spacing // 2)
+    g = np.arange(-r, r + 1, dtype=np.float64)
+    dz, dy, dx = np.meshgrid(g, g, g, indexing="ij")
+    for z in zk:
+        depth = z / max(nz - 1, 1)
+        for y in yk:
+            for x in xk:
+                for j in range(2):
+                    for q in range(2):
+                        sig = (0.1 + 0.08 * depth) * spacing * rng.uniform(0.85, 1.15)
+                        tilt = rng.uniform(-0.4, 0.4)
+                        amp = (1.0 - 0.6 * depth) * rng.uniform(0.8, 1.2)
+                        u = (dz * math.cos(tilt) + dx * math.sin(tilt)) / sig
+                        v = (-dz * math.sin(tilt) + dx * math.cos(tilt)) / (2.0 * sig)
+                        wy = dy / (2.0 * sig)
+                        env = np.exp(-0.5 * (u * u + v * v + wy * wy))
+                        blob = (1.0 - u * u) * env if q == j else cross * u * env
+                        z0, z1 = max(0, z - r), min(nz, z + r + 1)
+                        y0, y1 = max(0, y - r), min(ny, y + r + 1)
+                        x0, x1 = max(0, x - r), min(nx, x + r + 1)
+                        out[j][q, z0:z1, y0:y1, x0:x1] += amp * blob[z0 - z + r:z1 - z + r, y0 - y + r:y1 - y + r,
+                                                                     x0 - x + r:x1 - x + r]
     return out[0], out[1]

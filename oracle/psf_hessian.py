@@ -34,6 +34,10 @@ Definitions (the readings where App. D is silent are marked *):
 
 The columns are formed literally (interpolated patch times the input value,
 spread over the window); numpy only vectorises the loop over pixels.
+
+3D images ([2, nz, ny, nx]) use Eq. (trilinear) as printed: the eight
+corners of the node cell around the voxel, weights (1 - w1 or w1) (1 - w2
+or w2) (1 - w3 or w3) from the same per-axis rule, windows of (2 half + 1)^3.
 """
 from __future__ import annotations
 
@@ -90,6 +94,36 @@ def column(P: np.ndarray, s: int, nz: int, nx: int, cz: int, cx: int) -> np.ndar
             + wz * (1 - wx) * P[kz1, kx0] + wz * wx * P[kz1, kx1])
 
 
+def patches3(Q: np.ndarray, s: int, half: int) -> np.ndarray:
+    """Node patches [nkz, nky, nkx, L, L, L] (L = 2 half + 1) of one 3D PSF plane Q."""
+    nz, ny, nx = Q.shape
+    zk, yk, xk = nodes(nz, s), nodes(ny, s), nodes(nx, s)
+    L = 2 * half + 1
+    P = np.zeros((len(zk), len(yk), len(xk), L, L, L))
+    for i, z in enumerate(zk):
+        for j, y in enumerate(yk):
+            for k, x in enumerate(xk):
+                for a in range(-half, half + 1):
+                    for b in range(-half, half + 1):
+                        for c in range(-half, half + 1):
+                            if 0 <= z + a < nz and 0 <= y + b < ny and 0 <= x + c < nx:
+                                P[i, j, k, a + half, b + half, c + half] = Q[z + a, y + b, x + c]
+    return P
+
+
+def column3(P: np.ndarray, s: int, shape, cz: int, cy: int, cx: int) -> np.ndarray:
+    """Interpolated column patch H(c + a, c) of a 3D image: Eq. (trilinear), the
+    eight corners (z0|z1, y0|y1, x0|x1) with the products of the 1D weights."""
+    nz, ny, nx = shape
+    kz0, kz1, w3 = corners_1d(cz, nz, s)
+    ky0, ky1, w2 = corners_1d(cy, ny, s)
+    kx0, kx1, w1 = corners_1d(cx, nx, s)
+    return ((1 - w1) * (1 - w2) * (1 - w3) * P[kz0, ky0, kx0] + w1 * (1 - w2) * (1 - w3) * P[kz0, ky0, kx1]
+            + (1 - w1) * w2 * (1 - w3) * P[kz0, ky1, kx0] + w1 * w2 * (1 - w3) * P[kz0, ky1, kx1]
+            + (1 - w1) * (1 - w2) * w3 * P[kz1, ky0, kx0] + w1 * (1 - w2) * w3 * P[kz1, ky0, kx1]
+            + (1 - w1) * w2 * w3 * P[kz1, ky1, kx0] + w1 * w2 * w3 * P[kz1, ky1, kx1])
+
+
 def _planes(mask: int) -> list[int]:
     return [q for q in (0, 1) if mask & (1 << q)]
 
@@ -103,7 +137,8 @@ def block_patches(psf_vp, psf_ip, s: int, half: int, mask: int = 3) -> dict:
         if src[j] is None:
             raise ValueError(f"the PSF of parameter {j} is needed for mask {mask}")
         for i in _planes(mask):
-            out[(i, j)] = patches(np.asarray(src[j], np.float64)[i], s, half)
+            plane = np.asarray(src[j], np.float64)[i]
+            out[(i, j)] = patches(plane, s, half) if plane.ndim == 2 else patches3(plane, s, half)
     return out
 
 
@@ -133,9 +168,56 @@ def _shift(g: np.ndarray, a: int, b: int) -> np.ndarray:
     return out
 
 
+def _column_fields3(P: np.ndarray, s: int, shape, half: int):
+    """3D: for every window offset a, the field C_a[c] = H(c + a, c) over all c."""
+    nz, ny, nx = shape
+    kz0, kz1, w3 = axis_corners(nz, s)
+    ky0, ky1, w2 = axis_corners(ny, s)
+    kx0, kx1, w1 = axis_corners(nx, s)
+    I = np.ix_
+    for a in range(-half, half + 1):
+        for b in range(-half, half + 1):
+            for c in range(-half, half + 1):
+                p = P[:, :, :, a + half, b + half, c + half]
+                C = np.zeros(shape)
+                for kz, wz in ((kz0, 1 - w3), (kz1, w3)):
+                    for ky, wy in ((ky0, 1 - w2), (ky1, w2)):
+                        for kx, wx in ((kx0, 1 - w1), (kx1, w1)):
+                            C += (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]) * p[I(kz, ky, kx)]
+                yield (a, b, c), C
+
+
+def _shift_nd(g: np.ndarray, off) -> np.ndarray:
+    """g(p - off), zero where p - off leaves the array."""
+    out = np.zeros_like(g)
+    src, dst = [], []
+    for n, a in zip(g.shape, off):
+        s0, e0 = max(0, a), min(n, n + a)
+        if s0 >= e0:
+            return out
+        dst.append(slice(s0, e0))
+        src.append(slice(s0 - a, e0 - a))
+    out[tuple(dst)] = g[tuple(src)]
+    return out
+
+
+def _apply3(blocks: dict, s: int, half: int, x: np.ndarray, transpose: bool) -> np.ndarray:
+    y = np.zeros_like(x)
+    for (i, j), P in blocks.items():
+        for off, C in _column_fields3(P, s, x.shape[1:], half):
+            if not transpose:
+                y[i] += _shift_nd(C * x[j], off)
+            else:
+                y[j] += C * _shift_nd(x[i], tuple(-o for o in off))
+    return y
+
+
 def apply(blocks: dict, s: int, half: int, x: np.ndarray, transpose: bool = False) -> np.ndarray:
-    """y = P H P x (or P H^T P x): x, y [2, nz, nx]; `blocks` from block_patches."""
+    """y = P H P x (or P H^T P x): x, y [2, nz, nx] or [2, nz, ny, nx]; `blocks`
+    from block_patches."""
     x = np.asarray(x, np.float64)
+    if x.ndim == 4:
+        return _apply3(blocks, s, half, x, transpose)
     nz, nx = x.shape[1:]
     y = np.zeros_like(x)
     for (i, j), P in blocks.items():
@@ -173,9 +255,31 @@ def apply_at(blocks: dict, s: int, half: int, x: np.ndarray, plane: int, rz: int
     return acc
 
 
+def _explicit3(blocks: dict, s: int, half: int, shape) -> np.ndarray:
+    nz, ny, nx = shape
+    nv = nz * ny * nx
+    H = np.zeros((2 * nv, 2 * nv))
+    r = range(-half, half + 1)
+    for (i, j), P in blocks.items():
+        for cz in range(nz):
+            for cy in range(ny):
+                for cx in range(nx):
+                    col = column3(P, s, shape, cz, cy, cx)
+                    for a in r:
+                        for b in r:
+                            for c in r:
+                                z, y, x = cz + a, cy + b, cx + c
+                                if 0 <= z < nz and 0 <= y < ny and 0 <= x < nx:
+                                    H[i * nv + (z * ny + y) * nx + x, j * nv + (cz * ny + cy) * nx + cx] = \
+                                        col[a + half, b + half, c + half]
+    return H
+
+
 def explicit(blocks: dict, s: int, half: int, shape) -> np.ndarray:
-    """Dense P H P written entry by entry from column() (tiny images only);
-    rows and columns index [plane][z][x]."""
+    """Dense P H P written entry by entry from column() / column3() (tiny
+    images only); rows and columns index [plane][z][(y)][x]."""
+    if len(shape) == 3:
+        return _explicit3(blocks, s, half, shape)
     nz, nx = shape
     n = 2 * nz * nx
     H = np.zeros((n, n))

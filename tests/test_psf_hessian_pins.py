@@ -163,3 +163,62 @@ def test_two_parameters_without_cross_terms_decouple():
     assert np.allclose(both, vp + ip, rtol=0, atol=1e-13)
     with pytest.raises(ValueError):
         ph.block_patches(a, None, s, half, mask=3)
+
+
+# ------------------------------------------------------------------ 3D
+
+
+def _volume_from_patches(shape, s, half, patch_of_node):
+    Q = np.zeros(shape)
+    nz, ny, nx = shape
+    for i, z in enumerate(range(s // 2, nz, s)):
+        for j, y in enumerate(range(s // 2, ny, s)):
+            for k, x in enumerate(range(s // 2, nx, s)):
+                p = patch_of_node(i, j, k)
+                Q[z - half:z + half + 1, y - half:y + half + 1, x - half:x + half + 1] = p
+    return Q
+
+
+def test_stationary_psf_is_a_convolution_3d():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    shape, s, half = (20, 14, 26), 6, 2     # every node window inside the volume
+    rng = np.random.default_rng(10)
+    p = rng.standard_normal((2 * half + 1,) * 3)
+    Q = _volume_from_patches(shape, s, half, lambda i, j, k: p)
+    bl = ph.block_patches(np.stack([Q, 0 * Q]), None, s, half, mask=1)
+    x = np.zeros((2,) + shape)
+    x[0] = rng.standard_normal(shape)
+    y = ph.apply(bl, s, half, x)
+    assert np.allclose(y[0], ndimage.convolve(x[0], p, mode="constant"), rtol=0, atol=1e-12)
+    yt = ph.apply(bl, s, half, x, transpose=True)
+    assert np.allclose(yt[0], ndimage.correlate(x[0], p, mode="constant"), rtol=0, atol=1e-12)
+
+
+def test_affine_node_psfs_interpolate_exactly_3d():
+    shape, s, half = (20, 14, 26), 6, 2
+    zk, yk, xk = (np.arange(s // 2, n, s) for n in shape)
+    q = np.random.default_rng(11).standard_normal((2 * half + 1,) * 3)
+    f = lambda z, y, x: 0.6 + 0.011 * z - 0.017 * y + 0.023 * x
+    Q = _volume_from_patches(shape, s, half, lambda i, j, k: f(zk[i], yk[j], xk[k]) * q)
+    P = ph.block_patches(np.stack([Q, Q]), None, s, half, mask=1)[(0, 0)]
+    for cz in range(shape[0]):
+        for cy in range(0, shape[1], 3):
+            for cx in range(0, shape[2], 5):
+                col = ph.column3(P, s, shape, cz, cy, cx)
+                ez = min(max(cz, zk[0]), zk[-1])
+                ey = min(max(cy, yk[0]), yk[-1])
+                ex = min(max(cx, xk[0]), xk[-1])
+                assert np.allclose(col, f(ez, ey, ex) * q, rtol=0, atol=1e-13)
+
+
+def test_operator_equals_its_explicit_columns_3d():
+    shape, s = (5, 6, 7), 3
+    half = ph.default_half(s)
+    pv, pi = li.psf_images3(*shape, s, seed=12)
+    bl = ph.block_patches(pv, pi, s, half)
+    H = ph.explicit(bl, s, half, shape)
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal((2,) + shape)
+    y = rng.standard_normal((2,) + shape)
+    assert np.allclose(ph.apply(bl, s, half, x).ravel(), H @ x.ravel(), atol=1e-12)
+    assert np.allclose(ph.apply(bl, s, half, y, transpose=True).ravel(), H.T @ y.ravel(), atol=1e-12)
