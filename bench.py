@@ -72,6 +72,8 @@ def parse():
                     help="time the image-domain CGNR with the interpolated PSF Hessian (App. D) "
                          "on the marine-line image instead of the data-domain iteration")
     ap.add_argument("--psf-iters", type=int, default=100, help="CGNR iterations per --psf-cg step")
+    ap.add_argument("--psf-3d", action="store_true",
+                    help="with --psf-cg: a 128^3 volume, comb spacing 16, 7^3 node windows (Eq. trilinear)")
     ap.add_argument("--deblur", action="store_true",
                     help="time the image-domain deblurring of the marine-line image: the Fourier-form "
                          "Wiener filter (App. E) and the space-domain 11 x 11 filters")
@@ -237,6 +239,9 @@ PSF_CG = {"nz": 300, "nx": 2000, "spacing": 20, "half": 9, "mask": 3}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+PSF_CG3 = {"shape": (128, 128, 128), "spacing": 16, "half": 3, "mask": 3}
+
+
 def psf_cg_inputs(nz=None, nx=None):
     c = PSF_CG
     nz, nx = nz or c["nz"], nx or c["nx"]
@@ -245,12 +250,21 @@ def psf_cg_inputs(nz=None, nx=None):
     return pv, pi, m_rtm
 
 
-def psf_apply_flops(nz, nx, half, mask):
+def psf_cg3_inputs():
+    c = PSF_CG3
+    pv, pi = li.psf_images3(*c["shape"], c["spacing"], seed=9)
+    m_rtm = np.random.default_rng(5).standard_normal((2,) + c["shape"])
+    return pv, pi, m_rtm
+
+
+def psf_apply_flops(nz, nx, half, mask, ny=None):
     """Algorithmic FP32 flops of one application of H (or H^T): per pixel, window
     offset and parameter block, the interpolated entry (4 multiply-adds over
-    the corners) and its product with the input (1 multiply-add)."""
+    the corners in 2D, 8 in 3D) and its product with the input (1 multiply-add)."""
     nblocks = 4 if mask == 3 else 1
-    return float(nz) * nx * (2 * half + 1) ** 2 * nblocks * 10.0
+    if ny is None:
+        return float(nz) * nx * (2 * half + 1) ** 2 * nblocks * 10.0
+    return float(nz) * ny * nx * (2 * half + 1) ** 3 * nblocks * 18.0
 
 
 def psf_cpu_sample(seconds, niter_full):
@@ -279,12 +293,19 @@ def psf_cpu_sample(seconds, niter_full):
 def psf_cg_bench(args, rank, world, local):
     import torch
     from paper_2508_10405_gb300 import Lsrtm, binding
-    c = PSF_CG
-    nz, nx, s, half, mask = c["nz"], c["nx"], c["spacing"], c["half"], c["mask"]
     niter, K, W = args.psf_iters, args.steps, args.warmup
-    wk = li.small_case(nz=nz, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+    if args.psf_3d:
+        c = PSF_CG3
+        (nz, ny, nx), s, half, mask = c["shape"], c["spacing"], c["half"], c["mask"]
+        wk = li.small_case(ndim=3, nz=nz, ny=ny, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+        pv, pi, m = psf_cg3_inputs()
+    else:
+        c = PSF_CG
+        nz, nx, s, half, mask = c["nz"], c["nx"], c["spacing"], c["half"], c["mask"]
+        ny = None
+        wk = li.small_case(nz=nz, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+        pv, pi, m = psf_cg_inputs()
     h = Lsrtm.from_workload(wk)
-    pv, pi, m = psf_cg_inputs()
     pv_d, pi_d, m_d = (torch.tensor(a, dtype=torch.float32, device="cuda") for a in (pv, pi, m))
     for _ in range(W):
         h.psf_cg(m_d, pv_d, pi_d, niter, s, half, mask)
@@ -315,7 +336,7 @@ def psf_cg_bench(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     apply_s = e0.elapsed_time(e1) / 1e3 / reps
-    flops = psf_apply_flops(nz, nx, half, mask)
+    flops = psf_apply_flops(nz, nx, half, mask, ny)
     achieved = flops / apply_s / 1e12
     t_step = float(np.sum(t_steps)) / K
     value = niter * world / t_step
@@ -333,25 +354,39 @@ def psf_cg_bench(args, rank, world, local):
         assert rc == 0
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        val, threads, desc, _ = psf_cpu_sample(args.cpu_seconds, niter)
-        cpu = {"value": val, "unit": "iter/s", "cores": threads, "kind": "oracle", "sample": desc}
+        if args.psf_3d:
+            from oracle import psf_hessian as ph
+            sub = tuple(min(n, 24) for n in (nz, ny, nx))
+            bl = ph.block_patches(pv[:, :sub[0], :sub[1], :sub[2]], pi[:, :sub[0], :sub[1], :sub[2]], s, half)
+            t0 = time.perf_counter()
+            ph.cgnr(bl, s, half, m[:, :sub[0], :sub[1], :sub[2]], 1)
+            tc = time.perf_counter() - t0
+            ratio = float(np.prod(sub)) / (nz * ny * nx)
+            cpu = {"value": ratio / tc, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                   "sample": f"oracle CGNR, 1 iteration on a {sub} crop, scaled by the voxel ratio {ratio:.4f}"}
+        else:
+            val, threads, desc, _ = psf_cpu_sample(args.cpu_seconds, niter)
+            cpu = {"value": val, "unit": "iter/s", "cores": threads, "kind": "oracle", "sample": desc}
     if rank == 0:
         line = {
             "metric": "PSF-Hessian CGNR iterations/s", "value": value, "unit": "iter/s",
             "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": t_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"marine-line image {nz} x {nx}, comb spacing {s}, "
-                                   f"{2 * half + 1} x {2 * half + 1} node windows, two parameters",
+            "config": {"workload": (f"3D volume {nz} x {ny} x {nx}, comb spacing {s}, {2 * half + 1}^3 node "
+                                    f"windows, two parameters" if args.psf_3d else
+                                    f"marine-line image {nz} x {nx}, comb spacing {s}, "
+                                    f"{2 * half + 1} x {2 * half + 1} node windows, two parameters"),
                        "niter": niter, "step": f"one image-domain CGNR solve of {niter} iterations "
                                                "(node windows built, 2 niter + 1 applications of H or H^T, "
                                                "FP64 Krylov scalars)",
                        "final_misfit": float(mis[-1]),
-                       "l2": "L2 flushed (256 MB write) before every timed step; the solve's working "
-                             "set (about 40 MB) is L2-resident within a step"},
+                       "l2": f"L2 flushed (256 MB write) before every timed step; the solve's vectors take "
+                             f"{6 * m.size * 4 / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_psfh_apply<3>", "flops_per_launch": flops,
+                         "kernel": "k_psfh3_apply<3>" if args.psf_3d else "k_psfh_apply<3>",
+                         "flops_per_launch": flops,
                          "avg_launch_ms": apply_s * 1e3,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no tensor cores)"},
             "clocks": clk, "gpu_launches": int(launches),

@@ -283,7 +283,7 @@ lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const floa
                                  float *dm_out);
 
 /* Interpolated PSF Hessian (migration deconvolution with PSFs, App. D) of a
- * 2D image. The PSF image of a spike comb (nodes s/2 + k s along both axes,
+ * 2D or 3D image. The PSF image of a spike comb (nodes s/2 + k s along both axes,
  * as lsrtm_psf places them) holds a localised Hessian column around each
  * node; the column at any pixel c is interpolated from the windows of the
  * (up to) four surrounding nodes with the weights of Eq. (trilinear), 2D form:
@@ -291,12 +291,15 @@ lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const floa
  *     |a_z|, |a_x| <= half,  Q = 0 outside the image,
  *     1D weights (1 - w, w), w = (c - node_k0) / s between the first and the
  *     last node; beyond them the nearest end node alone (w = 0),
- * entries with c + a outside the image dropped. Block (i, j) of the two-
+ * entries with c + a outside the image dropped. In 3D the column takes the
+ * eight corners of the node cell with the products of the three 1D weights
+ * (Eq. trilinear as printed) and windows of (2 half + 1)^3 voxels; nz <= 65535.
+ * Block (i, j) of the two-
  * parameter Hessian (output plane i, input plane j; 0 = Vp, 1 = Ip) takes Q
  * = plane i of the PSF of the comb in parameter j. The operator applied is
  * P H P, P keeping the planes of param_mask; it is formed on the fly (never
  * stored).
- *   psf_vp, psf_ip : [2][nz][nx] PSF images of the combs in Vp and Ip (host
+ *   psf_vp, psf_ip : [2][nz][ny][nx] PSF images of the combs in Vp and Ip (host
  *                    or device; read only). The one of a parameter outside
  *                    param_mask may be NULL.
  *   spacing s      : comb spacing, 2 <= s <= 64
@@ -304,11 +307,10 @@ lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const floa
  *                    (s - 1) / 2 (the widest window clear of the neighbours')
  *   param_mask     : 1 Vp, 2 Ip, 3 both
  *   transpose      : 0 for y = P H P x, 1 for y = P H^T P x
- *   x, y           : [2][nz][nx] (host or device, not overlapping); planes
+ *   x, y           : [2][nz][ny][nx] (host or device, not overlapping); planes
  *                    outside param_mask are ignored in x and zero in y
- * Errors: LSRTM_ERR_ARG for 3D handles, parameters out of range, a missing
- * PSF, an image without comb nodes or overlapping x and y. Asynchronous for
- * device outputs. */
+ * Errors: LSRTM_ERR_ARG for parameters out of range, a missing PSF, an image
+ * without comb nodes or overlapping x and y. Asynchronous for device outputs. */
 lsrtm_status lsrtm_psf_hessian(lsrtm_handle *h, const float *psf_vp, const float *psf_ip, int spacing, int half,
                                int param_mask, int transpose, const float *x, float *y);
 
@@ -317,8 +319,8 @@ lsrtm_status lsrtm_psf_hessian(lsrtm_handle *h, const float *psf_vp, const float
  * niter iterations; the interpolated H is singular in general, and from zero
  * CGNR tends to the minimum-norm least-squares solution.
  *   psf_vp, psf_ip, spacing, half, param_mask : as for lsrtm_psf_hessian
- *   m_rtm   : [2][nz][nx] migrated image (host or device; read only)
- *   dm      : [2][nz][nx] output (host or device)
+ *   m_rtm   : [2][nz][ny][nx] migrated image (host or device; read only)
+ *   dm      : [2][nz][ny][nx] output (host or device)
  *   misfit  : optional host [niter + 1], ||P m_rtm - H dm_k|| / ||P m_rtm||
  * Errors: as lsrtm_psf_hessian; LSRTM_ERR_NONFINITE if the solution is not
  * finite. Synchronous. */

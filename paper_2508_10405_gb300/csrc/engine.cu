@@ -20,6 +20,7 @@
 #include "../../include/lsrtm.h"
 #include "lsrtm_internal.cuh"
 #include "wiener.cuh"
+#include "psfhess3d.cuh"
 
 using namespace lsrtm;
 
@@ -1795,24 +1796,38 @@ lsrtm_status lsrtm_deblur_wiener(lsrtm_handle *h, const float *m_rtm, const floa
 
 namespace {
 
+// The interpolated PSF Hessian of one call: 2D or 3D arguments of the kernels.
+struct PsfhPlan {
+    bool d3 = false;
+    PsfHessDev a2{};
+    PsfHess3Dev a3{};
+};
+
+cudaError_t psfh_apply(const PsfhPlan &pl, bool transpose, const float *in, float *out, cudaStream_t s)
+{
+    return pl.d3 ? launch_psfh3_apply(pl.a3, transpose, in, out, s) : launch_psfh_apply(pl.a2, transpose, in, out, s);
+}
+
 // Validates the PSF Hessian arguments, stages the PSF images and builds the
 // node windows; the caller has called begin_call.
 lsrtm_status psfh_setup(lsrtm_handle *h, const float *psf_vp, const float *psf_ip, int spacing, int half,
-                        int param_mask, PsfHessDev *a)
+                        int param_mask, PsfhPlan *pl)
 {
-    if (h->g.ndim != 2) return fail(LSRTM_ERR_ARG, "the PSF Hessian supports 2D images only");
+    const bool d3 = h->g.ndim == 3;
     if (param_mask < 1 || param_mask > 3) return fail(LSRTM_ERR_ARG, "param_mask must be 1, 2 or 3");
     if (spacing < 2 || spacing > 64) return fail(LSRTM_ERR_ARG, "spacing must be in [2, 64]");
     if (half < 0) half = (spacing - 1) / 2;
     if (half > kPsfHessMaxHalf) return fail(LSRTM_ERR_ARG, "half must be <= 15");
     if ((param_mask & 1) && !psf_vp) return fail(LSRTM_ERR_ARG, "param_mask includes Vp but psf_vp is NULL");
     if ((param_mask & 2) && !psf_ip) return fail(LSRTM_ERR_ARG, "param_mask includes Ip but psf_ip is NULL");
-    const int nz = h->gm.nz, nx = h->gm.nx;
-    if (nz <= spacing / 2 || nx <= spacing / 2)
+    const int nz = h->gm.nz, ny = h->gm.ny, nx = h->gm.nx;
+    if (nz <= spacing / 2 || nx <= spacing / 2 || (d3 && ny <= spacing / 2))
         return fail(LSRTM_ERR_ARG, "image smaller than half the node spacing: no comb node");
+    if (d3 && nz > 65535) return fail(LSRTM_ERR_ARG, "3D PSF Hessian: nz must be <= 65535");
     const int nkz = deblur_nodes(nz, spacing), nkx = deblur_nodes(nx, spacing);
+    const int nky = d3 ? deblur_nodes(ny, spacing) : 1;
     const long long L = 2 * half + 1;
-    const long long npt = (long long)nkz * nkx * L * L;
+    const long long npt = (long long)nkz * nky * nkx * L * L * (d3 ? L : 1);
     if (npt >= (1LL << 31)) return fail(LSRTM_ERR_ARG, "too many node windows for this spacing and half");
     const size_t m = 2 * (size_t)h->nint;
     if (!h->ph_vec) CHECK(dalloc_t(h, &h->ph_vec, 8 * m));
@@ -1824,9 +1839,15 @@ lsrtm_status psfh_setup(lsrtm_handle *h, const float *psf_vp, const float *psf_i
     const float *pv = nullptr, *pi = nullptr;
     if (param_mask & 1) CHECK(stage_in(h, psf_vp, h->ph_vec + 6 * m, m, &pv));
     if (param_mask & 2) CHECK(stage_in(h, psf_ip, h->ph_vec + 7 * m, m, &pi));
-    CU(launch_psfh_patches(pv, pi, nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt, h->work));
+    pl->d3 = d3;
+    if (d3) {
+        pl->a3 = PsfHess3Dev{nz, ny, nx, spacing, half, nkz, nky, nkx, param_mask, h->ph_pt};
+        CU(launch_psfh3_patches(pv, pi, pl->a3, h->ph_pt, h->work));
+    } else {
+        pl->a2 = PsfHessDev{nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt};
+        CU(launch_psfh_patches(pv, pi, nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt, h->work));
+    }
     h->launches++;
-    *a = PsfHessDev{nz, nx, spacing, half, nkz, nkx, param_mask, h->ph_pt};
     return LSRTM_OK;
 }
 
@@ -1840,14 +1861,14 @@ lsrtm_status lsrtm_psf_hessian(lsrtm_handle *h, const float *psf_vp, const float
     if (!h || !x || !y) return fail(LSRTM_ERR_ARG, "null argument");
     if ((const void *)x == (const void *)y) return fail(LSRTM_ERR_ARG, "x and y must not overlap");
     CHECK(begin_call(h));
-    PsfHessDev a;
+    PsfhPlan a;
     CHECK(psfh_setup(h, psf_vp, psf_ip, spacing, half, param_mask, &a));
     const size_t m = 2 * (size_t)h->nint;
     const float *xd;
     CHECK(stage_in(h, x, h->ph_vec + 5 * m, m, &xd));
     const bool odev = is_device_ptr(y);
     float *od = odev ? y : h->ph_vec + 4 * m;
-    CU(launch_psfh_apply(a, transpose != 0, xd, od, h->work));
+    CU(psfh_apply(a, transpose != 0, xd, od, h->work));
     h->launches++;
     if (!odev) CHECK(copy_out(h, y, od, m));
     return end_call(h, !odev);
@@ -1863,7 +1884,7 @@ lsrtm_status lsrtm_psf_cg(lsrtm_handle *h, const float *psf_vp, const float *psf
     if (!h || !m_rtm || !dm) return fail(LSRTM_ERR_ARG, "null argument");
     if (niter < 0) return fail(LSRTM_ERR_ARG, "niter < 0");
     CHECK(begin_call(h));
-    PsfHessDev a;
+    PsfhPlan a;
     CHECK(psfh_setup(h, psf_vp, psf_ip, spacing, half, param_mask, &a));
     const long long m = 2 * h->nint;
     float *v = h->ph_vec;
@@ -1881,17 +1902,17 @@ lsrtm_status lsrtm_psf_cg(lsrtm_handle *h, const float *psf_vp, const float *psf
     CU(launch_scale_copy(R, md, m, s));
     CU(launch_mul_mask(R, nullptr, param_mask, h->nint, s));
     CU(launch_dot(R, R, m, dd, h->dotwork, s));
-    CU(launch_psfh_apply(a, true, R, S, s));
+    CU(psfh_apply(a, true, R, S, s));
     CU(launch_scale_copy(Pp, S, m, s));
     CU(launch_dot(S, S, m, gamma, h->dotwork, s));
     CU(cudaMemcpyAsync(h->ph_mis, dd, sizeof(double), cudaMemcpyDeviceToDevice, s));
     h->launches += 6;
     for (int k = 0; k < niter; ++k) {
-        CU(launch_psfh_apply(a, false, Pp, Q, s));
+        CU(psfh_apply(a, false, Pp, Q, s));
         CU(launch_dot(Q, Q, m, qq, h->dotwork, s));
         CU(launch_axpy_ratio(X, Pp, gamma, qq, 1.0f, m, s));
         CU(launch_axpy_ratio(R, Q, gamma, qq, -1.0f, m, s));
-        CU(launch_psfh_apply(a, true, R, S, s));
+        CU(psfh_apply(a, true, R, S, s));
         CU(launch_dot(S, S, m, gnew, h->dotwork, s));
         CU(launch_xpby_ratio(Pp, S, gnew, gamma, m, s));
         CU(cudaMemcpyAsync(gamma, gnew, sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -1,7 +1,8 @@
 """Interpolated PSF Hessian and image-domain CGNR (App. D) on the GPU against
 the FP64 oracle.
 
-* H x and H^T y on images spanning several 32 x 8 tiles with ragged tails,
+* H x and H^T y on images spanning several tiles with ragged tails, 2D and 3D
+  (Eq. trilinear with eight corners),
   every mask, default and extreme window half-widths: every output pixel;
 * the dot test <H x, y> = <x, H^T y> on the GPU;
 * PSFs from the oracle's own migration of a small survey (the real Hessian);
@@ -187,4 +188,55 @@ def test_argument_errors():
         h.psf_hessian(a, b, b, 62, -1, False, 3)               # no comb node in a 30-row image
     with pytest.raises(LsrtmError):
         h.psf_cg(a, b, b, -1, 10)
+    h.close()
+
+
+# ------------------------------------------------------------------ 3D
+
+def _handle3(shape):
+    from paper_2508_10405_gb300 import Lsrtm
+    nz, ny, nx = shape
+    w = li.small_case(ndim=3, nz=nz, ny=ny, nx=nx, nt=8, order=4, npml=4, nshot=1, seed=1)
+    return Lsrtm.from_workload(w)
+
+
+@pytest.mark.parametrize("shape,s,half", [((20, 14, 26), 6, -1), ((17, 21, 45), 8, 2)])
+@pytest.mark.parametrize("mask", [1, 2, 3])
+def test_apply_3d_every_voxel(shape, s, half, mask):
+    pv, pi = li.psf_images3(*shape, s, seed=sum(shape))
+    pv, pi = _f32(pv), _f32(pi)
+    x = _f32(np.random.default_rng(3).standard_normal((2,) + shape))
+    hh = ph.default_half(s) if half < 0 else half
+    bl = ph.block_patches(pv if mask & 1 else None, pi if mask & 2 else None, s, hh, mask)
+    h = _handle3(shape)
+    for tr in (False, True):
+        got = _apply_gpu(h, x, pv if mask & 1 else None, pi if mask & 2 else None, s, half, mask, tr)
+        ref = ph.apply(bl, s, hh, x, transpose=tr)
+        e = rel(got, ref)
+        print(f"3D {shape} s={s} half={hh} mask={mask} transpose={tr}: {e:.3e}")
+        assert e < 1e-5
+        for q in (0, 1):
+            if not mask & (1 << q):
+                assert np.all(got[q] == 0)
+    h.close()
+
+
+def test_cgnr_and_dot_product_3d():
+    shape, s, niter = (18, 15, 22), 6, 6
+    pv, pi = li.psf_images3(*shape, s, seed=5)
+    pv, pi = _f32(pv), _f32(pi)
+    rng = np.random.default_rng(6)
+    m_rtm = _f32(rng.standard_normal((2,) + shape))
+    h = _handle3(shape)
+    x = rng.standard_normal((2,) + shape)
+    y = rng.standard_normal((2,) + shape)
+    a = float(np.vdot(_apply_gpu(h, x, pv, pi, s, -1, 3, False), _f32(y)))
+    b = float(np.vdot(_f32(x), _apply_gpu(h, y, pv, pi, s, -1, 3, True)))
+    assert abs(a - b) <= 1e-5 * max(abs(a), abs(b))
+    bl = ph.block_patches(pv, pi, s, ph.default_half(s))
+    ref, mis_ref = ph.cgnr(bl, s, ph.default_half(s), m_rtm, niter)
+    got, mis = h.psf_cg(_dev(m_rtm), _dev(pv), _dev(pi), niter, s)
+    print(f"3D CGNR: misfit {mis[-1]:.6f} / {mis_ref[-1]:.6f}, solution {rel(got.double().cpu().numpy(), ref):.3e}")
+    assert np.max(np.abs(mis - mis_ref)) < 1e-4
+    assert rel(got.double().cpu().numpy(), ref) < 1e-4
     h.close()
