@@ -483,12 +483,163 @@ __global__ void __launch_bounds__(k3Threads) k_psfh3_apply(const PsfHess3Dev a, 
     }
 }
 
+// The 3D kernel with the row blocking of the 2D one: each thread owns one
+// (y, x) column and R consecutive z rows (R <= s, so its rows span at most
+// three node rows); per window offset it loads the twelve node values
+// covering them (3 node rows x 2 x 2), interpolates along x and y once and
+// along z per row. Inputs are read through L1.
+template <int MASK, bool TR, int R>
+__global__ void __launch_bounds__(k3Threads) k_psfh3_rows(const PsfHess3Dev a, const float *__restrict__ in,
+                                                           float *__restrict__ out)
+{
+    using V = typename Blk<MASK>::T;
+    constexpr int P0 = MASK == 2 ? 1 : 0;
+    constexpr int BM = MASK == 2 ? 3 : 0;
+    __shared__ Corner zc[8 + 2 * kPsfHessMaxHalf], yc[k3Y + 2 * kPsfHessMaxHalf], xc[k3X + 2 * kPsfHessMaxHalf];
+    const int h = a.half, L = 2 * h + 1, LL = L * L, LLL = LL * L;
+    const int t = threadIdx.x, tx = t % k3X, ty = t / k3X;
+    const int X0 = (int)blockIdx.x * k3X, Y0 = (int)blockIdx.y * k3Y, Z0 = (int)blockIdx.z * R;
+    const int NZ = R + 2 * h, NY = k3Y + 2 * h, NX = k3X + 2 * h;
+    for (int i = t; i < NZ + NY + NX; i += k3Threads) {
+        if (i < NZ) zc[i] = corner_of(Z0 - h + i, a.nz, a.s, a.nkz);
+        else if (i < NZ + NY) yc[i - NZ] = corner_of(Y0 - h + (i - NZ), a.ny, a.s, a.nky);
+        else xc[i - NZ - NY] = corner_of(X0 - h + (i - NZ - NY), a.nx, a.s, a.nkx);
+    }
+    __syncthreads();
+    const int y = Y0 + ty, x = X0 + tx;
+    if (y >= a.ny || x >= a.nx) return;
+    const long long vol = (long long)a.nz * a.ny * a.nx, rowz = (long long)a.ny * a.nx;
+    const float *in0 = in + P0 * vol, *in1 = in + vol;
+    const float4 *pt = a.pt;
+    const int nky = a.nky, nkx = a.nkx, nkz1 = a.nkz - 1;
+    const V zero = V{};
+    float acc0[R], acc1[R], wb[R], wc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc0[r] = acc1[r] = 0.f;
+    if (!TR) {
+        for (int dz = -h; dz <= h; ++dz) {
+            const int row0 = h - dz;   // zc index of c_z = Z0 - dz
+            const int kf = zc[row0].k0;
+            row_weights<R>(zc + row0, kf, wb, wc);
+            const int nq[3] = {kf, min(kf + 1, nkz1), min(kf + 2, nkz1)};
+            for (int dy = -h; dy <= h; ++dy) {
+                const int cy = y - dy;
+                if (cy < 0 || cy >= a.ny) continue;
+                const Corner Y = yc[ty + h - dy];
+                for (int dx = -h; dx <= h; ++dx) {
+                    const int cx = x - dx;
+                    if (cx < 0 || cx >= a.nx) continue;
+                    const Corner X = xc[tx + h - dx];
+                    const int ai = ((dz + h) * L + (dy + h)) * L + (dx + h);
+                    V Q[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int b0 = (nq[q] * nky + Y.k0) * nkx, b1 = (nq[q] * nky + Y.k1) * nkx;
+                        const V v0 = lerp_(load_blk<BM>(pt, (b0 + X.k0) * LLL + ai, zero),
+                                           load_blk<BM>(pt, (b0 + X.k1) * LLL + ai, zero), X.w);
+                        const V v1 = lerp_(load_blk<BM>(pt, (b1 + X.k0) * LLL + ai, zero),
+                                           load_blk<BM>(pt, (b1 + X.k1) * LLL + ai, zero), X.w);
+                        Q[q] = lerp_(v0, v1, Y.w);
+                    }
+                    const V d1 = sub_(Q[1], Q[0]), d2 = sub_(Q[2], Q[0]);
+                    const long long cb = (long long)cy * a.nx + cx;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int cz = Z0 + r - dz;
+                        if (cz < 0 || cz >= a.nz) continue;
+                        const V C = mix3(Q[0], d1, d2, wb[r], wc[r]);
+                        const long long c = cz * rowz + cb;
+                        if constexpr (MASK == 3) {
+                            const float v0 = __ldg(in0 + c), v1 = __ldg(in1 + c);
+                            acc0[r] = fmaf(C.x, v0, fmaf(C.y, v1, acc0[r]));
+                            acc1[r] = fmaf(C.z, v0, fmaf(C.w, v1, acc1[r]));
+                        } else {
+                            acc0[r] = fmaf(C, __ldg(in0 + c), acc0[r]);
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+        const int kf = zc[h].k0;
+        row_weights<R>(zc + h, kf, wb, wc);
+        const Corner Y = yc[ty + h], X = xc[tx + h];
+        int base[3][2][2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int kz = min(kf + q, nkz1);
+            base[q][0][0] = ((kz * nky + Y.k0) * nkx + X.k0) * LLL;
+            base[q][0][1] = ((kz * nky + Y.k0) * nkx + X.k1) * LLL;
+            base[q][1][0] = ((kz * nky + Y.k1) * nkx + X.k0) * LLL;
+            base[q][1][1] = ((kz * nky + Y.k1) * nkx + X.k1) * LLL;
+        }
+        for (int dz = -h; dz <= h; ++dz) {
+            for (int dy = -h; dy <= h; ++dy) {
+                const int cy = y + dy;
+                if (cy < 0 || cy >= a.ny) continue;
+                for (int dx = -h; dx <= h; ++dx) {
+                    const int cx = x + dx;
+                    if (cx < 0 || cx >= a.nx) continue;
+                    const int ai = ((dz + h) * L + (dy + h)) * L + (dx + h);
+                    V Q[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const V v0 = lerp_(load_blk<BM>(pt, base[q][0][0] + ai, zero),
+                                           load_blk<BM>(pt, base[q][0][1] + ai, zero), X.w);
+                        const V v1 = lerp_(load_blk<BM>(pt, base[q][1][0] + ai, zero),
+                                           load_blk<BM>(pt, base[q][1][1] + ai, zero), X.w);
+                        Q[q] = lerp_(v0, v1, Y.w);
+                    }
+                    const V d1 = sub_(Q[1], Q[0]), d2 = sub_(Q[2], Q[0]);
+                    const long long cb = (long long)cy * a.nx + cx;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int cz = Z0 + r + dz;
+                        if (cz < 0 || cz >= a.nz) continue;
+                        const V C = mix3(Q[0], d1, d2, wb[r], wc[r]);
+                        const long long c = cz * rowz + cb;
+                        if constexpr (MASK == 3) {
+                            const float v0 = __ldg(in0 + c), v1 = __ldg(in1 + c);
+                            acc0[r] = fmaf(C.x, v0, fmaf(C.z, v1, acc0[r]));
+                            acc1[r] = fmaf(C.y, v0, fmaf(C.w, v1, acc1[r]));
+                        } else {
+                            acc0[r] = fmaf(C, __ldg(in0 + c), acc0[r]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int z = Z0 + r;
+        if (z >= a.nz) break;
+        const long long o = z * rowz + (long long)y * a.nx + x;
+        if (MASK == 3) {
+            out[o] = acc0[r];
+            out[vol + o] = acc1[r];
+        } else {
+            out[P0 * vol + o] = acc0[r];
+            out[(1 - P0) * vol + o] = 0.f;
+        }
+    }
+}
+
+template <int MASK, bool TR, int R>
+cudaError_t launch3_r(const PsfHess3Dev &a, const float *in, float *out, cudaStream_t s)
+{
+    dim3 grid((a.nx + k3X - 1) / k3X, (a.ny + k3Y - 1) / k3Y, (a.nz + R - 1) / R);
+    k_psfh3_rows<MASK, TR, R><<<grid, k3Threads, 0, s>>>(a, in, out);
+    return cudaGetLastError();
+}
+
 template <int MASK, bool TR>
 cudaError_t launch3_t(const PsfHess3Dev &a, const float *in, float *out, cudaStream_t s)
 {
-    dim3 grid((a.nx + k3X - 1) / k3X, (a.ny + k3Y - 1) / k3Y, a.nz);
-    k_psfh3_apply<MASK, TR><<<grid, k3Threads, 0, s>>>(a, in, out);
-    return cudaGetLastError();
+    if (a.s >= 8) return launch3_r<MASK, TR, 8>(a, in, out, s);
+    if (a.s >= 4) return launch3_r<MASK, TR, 4>(a, in, out, s);
+    if (a.s >= 2) return launch3_r<MASK, TR, 2>(a, in, out, s);
+    return launch3_r<MASK, TR, 1>(a, in, out, s);
 }
 
 }  // namespace
