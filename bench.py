@@ -385,7 +385,7 @@ def psf_cg_bench(args, rank, world, local):
                              f"{6 * m.size * 4 / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_psfh3_apply<3>" if args.psf_3d else "k_psfh_apply<3>",
+                         "kernel": "k_psfh3_rows<3>" if args.psf_3d else "k_psfh_apply<3>",
                          "flops_per_launch": flops,
                          "avg_launch_ms": apply_s * 1e3,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no tensor cores)"},
