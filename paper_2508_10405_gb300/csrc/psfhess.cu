@@ -330,13 +330,12 @@ cudaError_t launch_r(const PsfHessDev &a, const float *in, float *out, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
-// 3D (Eq. trilinear as printed): one thread per voxel, CTAs of 32 x 4 voxels
-// in one z plane; the corner tables of the z, y and x coordinates the CTA's
-// windows reach sit in shared memory, inputs and node windows are read
-// through L1. Per window offset eight node values (one float4 per corner)
-// are combined with the products of the three 1D weights.
+// 3D (Eq. trilinear as printed: eight corners, products of the three 1D
+// weights). CTAs of 32 x 4 (y, x) columns of R z rows; the corner tables of
+// the z, y and x coordinates the CTA's windows reach sit in shared memory,
+// inputs and node windows are read through L1.
 // ---------------------------------------------------------------------------
-constexpr int k3X = 32, k3Y = 4, k3Threads = k3X * k3Y, k3MaxL = 2 * kPsfHessMaxHalf + 1;
+constexpr int k3X = 32, k3Y = 4, k3Threads = k3X * k3Y;
 
 __global__ void k_psfh3_patches(const float *psf_vp, const float *psf_ip, const PsfHess3Dev a, float4 *pt)
 {
@@ -361,125 +360,6 @@ __global__ void k_psfh3_patches(const float *psf_vp, const float *psf_ip, const 
             e[b] = use ? src[po * vol + v] : 0.f;
         }
         pt[i] = make_float4(e[0], e[1], e[2], e[3]);
-    }
-}
-
-template <int MASK, bool TR>
-__global__ void __launch_bounds__(k3Threads) k_psfh3_apply(const PsfHess3Dev a, const float *__restrict__ in,
-                                                            float *__restrict__ out)
-{
-    constexpr int P0 = MASK == 2 ? 1 : 0;
-    constexpr int BM = MASK == 2 ? 3 : 0;
-    __shared__ Corner zc[k3MaxL], yc[k3Y + 2 * kPsfHessMaxHalf], xc[k3X + 2 * kPsfHessMaxHalf];
-    const int h = a.half, L = 2 * h + 1, LL = L * L, LLL = LL * L;
-    const int t = threadIdx.x, tx = t % k3X, ty = t / k3X;
-    const int X0 = (int)blockIdx.x * k3X, Y0 = (int)blockIdx.y * k3Y, z = (int)blockIdx.z;
-    // corner tables: forward reads c = r - a, the transpose only c = r
-    for (int i = t; i < L + (k3Y + 2 * h) + (k3X + 2 * h); i += k3Threads) {
-        if (i < L) zc[i] = corner_of(z - h + i, a.nz, a.s, a.nkz);
-        else if (i < L + k3Y + 2 * h) yc[i - L] = corner_of(Y0 - h + (i - L), a.ny, a.s, a.nky);
-        else xc[i - L - k3Y - 2 * h] = corner_of(X0 - h + (i - L - k3Y - 2 * h), a.nx, a.s, a.nkx);
-    }
-    __syncthreads();
-    const int y = Y0 + ty, x = X0 + tx;
-    if (y >= a.ny || x >= a.nx) return;
-    const long long vol = (long long)a.nz * a.ny * a.nx;
-    const float *in0 = in + P0 * vol, *in1 = in + vol;
-    const float4 *pt = a.pt;
-    const float *pt1 = reinterpret_cast<const float *>(a.pt);
-    const int nky = a.nky, nkx = a.nkx;
-    float acc0 = 0.f, acc1 = 0.f;
-    if (!TR) {
-        for (int dz = -h; dz <= h; ++dz) {
-            const int cz = z - dz;
-            if (cz < 0 || cz >= a.nz) continue;
-            const Corner Z = zc[h - dz];
-            for (int dy = -h; dy <= h; ++dy) {
-                const int cy = y - dy;
-                if (cy < 0 || cy >= a.ny) continue;
-                const Corner Y = yc[ty + h - dy];
-                for (int dx = -h; dx <= h; ++dx) {
-                    const int cx = x - dx;
-                    if (cx < 0 || cx >= a.nx) continue;
-                    const Corner X = xc[tx + h - dx];
-                    const int ai = ((dz + h) * L + (dy + h)) * L + (dx + h);
-                    const long long c = ((long long)cz * a.ny + cy) * a.nx + cx;
-                    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int kz = (q & 4) ? Z.k1 : Z.k0, ky = (q & 2) ? Y.k1 : Y.k0, kx = (q & 1) ? X.k1 : X.k0;
-                        const float w = ((q & 4) ? Z.w : 1.f - Z.w) * ((q & 2) ? Y.w : 1.f - Y.w) *
-                                        ((q & 1) ? X.w : 1.f - X.w);
-                        const int idx = ((kz * nky + ky) * nkx + kx) * LLL + ai;
-                        if (MASK == 3) {
-                            const float4 e = __ldg(pt + idx);
-                            C = make_float4(fmaf(w, e.x, C.x), fmaf(w, e.y, C.y), fmaf(w, e.z, C.z), fmaf(w, e.w, C.w));
-                        } else {
-                            C.x = fmaf(w, __ldg(pt1 + 4 * idx + BM), C.x);
-                        }
-                    }
-                    const float v0 = __ldg(in0 + c);
-                    if (MASK == 3) {
-                        const float v1 = __ldg(in1 + c);
-                        acc0 = fmaf(C.x, v0, fmaf(C.y, v1, acc0));
-                        acc1 = fmaf(C.z, v0, fmaf(C.w, v1, acc1));
-                    } else {
-                        acc0 = fmaf(C.x, v0, acc0);
-                    }
-                }
-            }
-        }
-    } else {
-        const Corner Z = zc[h], Y = yc[ty + h], X = xc[tx + h];
-        int base[8];
-        float wq[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int kz = (q & 4) ? Z.k1 : Z.k0, ky = (q & 2) ? Y.k1 : Y.k0, kx = (q & 1) ? X.k1 : X.k0;
-            wq[q] = ((q & 4) ? Z.w : 1.f - Z.w) * ((q & 2) ? Y.w : 1.f - Y.w) * ((q & 1) ? X.w : 1.f - X.w);
-            base[q] = ((kz * nky + ky) * nkx + kx) * LLL;
-        }
-        for (int dz = -h; dz <= h; ++dz) {
-            const int cz = z + dz;
-            if (cz < 0 || cz >= a.nz) continue;
-            for (int dy = -h; dy <= h; ++dy) {
-                const int cy = y + dy;
-                if (cy < 0 || cy >= a.ny) continue;
-                for (int dx = -h; dx <= h; ++dx) {
-                    const int cx = x + dx;
-                    if (cx < 0 || cx >= a.nx) continue;
-                    const int ai = ((dz + h) * L + (dy + h)) * L + (dx + h);
-                    const long long c = ((long long)cz * a.ny + cy) * a.nx + cx;
-                    float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (MASK == 3) {
-                            const float4 e = __ldg(pt + base[q] + ai);
-                            C = make_float4(fmaf(wq[q], e.x, C.x), fmaf(wq[q], e.y, C.y), fmaf(wq[q], e.z, C.z),
-                                            fmaf(wq[q], e.w, C.w));
-                        } else {
-                            C.x = fmaf(wq[q], __ldg(pt1 + 4 * (base[q] + ai) + BM), C.x);
-                        }
-                    }
-                    const float v0 = __ldg(in0 + c);
-                    if (MASK == 3) {
-                        const float v1 = __ldg(in1 + c);
-                        acc0 = fmaf(C.x, v0, fmaf(C.z, v1, acc0));
-                        acc1 = fmaf(C.y, v0, fmaf(C.w, v1, acc1));
-                    } else {
-                        acc0 = fmaf(C.x, v0, acc0);
-                    }
-                }
-            }
-        }
-    }
-    const long long o = ((long long)z * a.ny + y) * a.nx + x;
-    if (MASK == 3) {
-        out[o] = acc0;
-        out[vol + o] = acc1;
-    } else {
-        out[P0 * vol + o] = acc0;
-        out[(1 - P0) * vol + o] = 0.f;
     }
 }
 
