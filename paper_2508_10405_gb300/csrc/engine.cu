@@ -1465,10 +1465,15 @@ lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const floa
     for (long long r = 0; r < nrec; ++r) {
         const double o = h->rec_off_h[r];
         const double td = o / v_mute + t0;
-        long long n = (long long)std::floor(td / dt) - 1;   // then step to the first n with (n + 1) dt - td > 0
-        n = std::max<long long>(n, 0);
-        while (n < nt && (n + 1) * dt - td <= 0.0) ++n;
-        while (n > 0 && n * dt - td > 0.0) --n;
+        const double q = td / dt;
+        long long n;
+        if (!(q < (double)nt + 1.0)) {
+            n = nt;   // the mute time is past the record (or not finite): every sample muted
+        } else {
+            n = q > 1.0 ? (long long)std::floor(q) - 1 : 0;   // then the first n with (n + 1) dt - td > 0
+            while (n < nt && (n + 1) * dt - td <= 0.0) ++n;
+            while (n > 0 && n * dt - td > 0.0) --n;
+        }
         n0[r] = (int)std::min<long long>(n, nt);
         a0[r] = t_taper > 0.0 ? (float)(((n0[r] + 1) * dt - td) / t_taper) : 0.f;
         double f = 1.0;

@@ -125,6 +125,18 @@ def test_hard_mute_and_in_place():
     h.close()
 
 
+def test_mute_times_outside_the_record():
+    """A mute time past the record mutes every sample; one long before it
+    mutes none (the taper has ended at the first sample)."""
+    w = _line(nt=120)
+    d = torch.ones((w.geom.nrec_total, w.nt), device="cuda")
+    h = _h(w)
+    for v_mute, t0 in ((1e-300, 0.0), (2000.0, 1e300), (2000.0, 10.0)):
+        assert torch.count_nonzero(h.mute_residual(d, None, v_mute, t0, 0.01)).item() == 0
+    assert torch.equal(h.mute_residual(d, None, 2000.0, -1e300, 0.01), d)
+    h.close()
+
+
 def test_input_pipeline_against_the_oracle():
     w = _line()
     vp2, rho2 = w.vp.copy(), w.rho.copy()
