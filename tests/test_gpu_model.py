@@ -126,13 +126,18 @@ def test_hard_mute_and_in_place():
 
 
 def test_mute_times_outside_the_record():
-    """A mute time past the record mutes every sample; one long before it
-    mutes none (the taper has ended at the first sample)."""
+    """Mute times past the record mute every sample (a vanishing v_mute mutes
+    every receiver but the zero-offset ones, whose mute time is t0); one long
+    before it mutes none (the taper has ended at the first sample)."""
     w = _line(nt=120)
     d = torch.ones((w.geom.nrec_total, w.nt), device="cuda")
     h = _h(w)
-    for v_mute, t0 in ((1e-300, 0.0), (2000.0, 1e300), (2000.0, 10.0)):
+    for v_mute, t0 in ((2000.0, 1e300), (2000.0, 10.0)):
         assert torch.count_nonzero(h.mute_residual(d, None, v_mute, t0, 0.01)).item() == 0
+    got = h.mute_residual(d, None, 1e-300, 0.0, 0.01).double().cpu().numpy()
+    ref = od.mute_mask(w, 1e-300, 0.0, 0.01, 0.0, 0.0)
+    assert np.all(got[ref == 0.0] == 0.0) and np.max(np.abs(got - ref)) < 1e-6
+    assert np.all(got[od.offsets(w) > 0.0] == 0.0)
     assert torch.equal(h.mute_residual(d, None, 2000.0, -1e300, 0.01), d)
     h.close()
 
