@@ -1,10 +1,12 @@
 """Seeded synthetic inputs for the LSRTM operator pair.
 
 This module only draws and shapes inputs: velocity and density models, model
-perturbations, source wavelets and acquisition geometry. It contains none of
+perturbations, source wavelets and acquisition geometry, and the synthetic
+images of the image-domain steps (a migrated image and its blurred
+remigration, the PSF images of spike combs in 2D and 3D). It contains none of
 the operator arithmetic (no stencils, no model preparation, no absorbing
-boundary), so both the FP64 oracle and the CUDA path can take their inputs
-from it without sharing any of the method.
+boundary, no interpolation or filtering), so both the FP64 oracle and the
+CUDA path can take their inputs from it without sharing any of the method.
 
 The five workload presets stand in for the paper's Marmousi 2D, Overthrust 3D
 and Viking Graben experiments (Sec. 4 and Sec. 6), none of which is available
