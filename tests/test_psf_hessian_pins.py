@@ -222,3 +222,39 @@ def test_operator_equals_its_explicit_columns_3d():
     y = rng.standard_normal((2,) + shape)
     assert np.allclose(ph.apply(bl, s, half, x).ravel(), H @ x.ravel(), atol=1e-12)
     assert np.allclose(ph.apply(bl, s, half, y, transpose=True).ravel(), H.T @ y.ravel(), atol=1e-12)
+
+
+def test_two_parameter_solution_follows_the_block_inverse():
+    """The partitioned inverse behind the multiparameter inversion: with
+    N = H^T H in 2 x 2 parameter blocks and b = H^T m, the two-parameter
+    solution is the block inverse of N applied to b (Schur complement
+    S = N11 - N12 N22^-1 N21; x2 = N22^-1 b2 - N22^-1 N21 x1), which the
+    oracle's two-parameter CGNR reaches; its mono-parameter (Ip) CGNR reaches
+    the solution of the Ip block alone (P H P), which the coupling term makes
+    different."""
+    nz, nx, s, half = 10, 12, 4, 1
+    pv, pi = li.psf_images(nz, nx, s, seed=21)
+    bl = ph.block_patches(pv, pi, s, half)
+    H = ph.explicit(bl, s, half, (nz, nx))
+    n = nz * nx
+    N = H.T @ H
+    N11, N12, N21, N22 = N[:n, :n], N[:n, n:], N[n:, :n], N[n:, n:]
+    m = np.random.default_rng(22).standard_normal((2, nz, nx))
+    b = H.T @ m.ravel()
+    b1, b2 = b[:n], b[n:]
+    N22i = np.linalg.inv(N22)
+    S = N11 - N12 @ N22i @ N21
+    x1 = np.linalg.solve(S, b1 - N12 @ N22i @ b2)
+    x2 = N22i @ b2 - N22i @ N21 @ x1
+    assert np.allclose(np.concatenate([x1, x2]), np.linalg.solve(N, b), rtol=0, atol=1e-8 * np.abs(x1).max())
+    x, _ = ph.cgnr(bl, s, half, m, 600)
+    assert np.allclose(x.ravel(), np.concatenate([x1, x2]), rtol=0, atol=1e-7 * np.abs(x1).max())
+    # mono-parameter (Ip): the data are P m, the operator P H P
+    bl2 = ph.block_patches(None, pi, s, half, mask=2)
+    xm, _ = ph.cgnr(bl2, s, half, m, 600, mask=2)
+    H22 = H[n:, n:]
+    x2_mono = np.linalg.solve(H22.T @ H22, H22.T @ m[1].ravel())
+    assert np.allclose(xm[1].ravel(), x2_mono, rtol=0, atol=1e-7 * np.abs(x2_mono).max())
+    assert np.all(xm[0] == 0.0)
+    # the paper's point: the two differ, by the coupling term
+    assert not np.allclose(x2, x2_mono, atol=1e-3 * np.abs(x2).max())
