@@ -166,6 +166,20 @@ lsrtm_status lsrtm_cg_begin(lsrtm_handle *h, const float *d, const float *x0, in
 lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit);
 lsrtm_status lsrtm_cg_result(lsrtm_handle *h, float *dm, double *misfit0);
 
+/* Save and resume of a step-wise CGNR solve. lsrtm_cg_get_state copies the
+ * state the next iteration reads: the iterate x and the search direction p
+ * ([2][nz][ny][nx]), the data residual r ([nrec_total][nt]), the FP64
+ * scalars {gamma = <s, M^-1 s>, <d, d>} and the iteration count (host or
+ * device buffers; synchronous). To resume, call lsrtm_cg_begin with the same
+ * d, precond and param_mask (it rebuilds the preconditioner and the misfit
+ * normalisation), then lsrtm_cg_set_state with the saved state: the
+ * following lsrtm_cg_iterate calls repeat the uninterrupted solve bit for
+ * bit (the kernels are deterministic). Errors: LSRTM_ERR_STATE without an
+ * active solve; LSRTM_ERR_ARG for a negative iteration count. */
+lsrtm_status lsrtm_cg_get_state(lsrtm_handle *h, float *x, float *p, float *r, double *scalars, int *iter);
+lsrtm_status lsrtm_cg_set_state(lsrtm_handle *h, const float *x, const float *p, const float *r,
+                                const double *scalars, int iter);
+
 /* Device-time accounting of the time loops, measured with CUDA events on the
  * library's own stream around each loop: born = fused background + Born
  * forward loops, background = background-only loops (band saving), adjoint =

@@ -31,7 +31,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
            "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune",
            "lsrtm_psf_hessian", "lsrtm_psf_cg", "lsrtm_model", "lsrtm_mute_residual",
-           "lsrtm_deblur_wiener"]
+           "lsrtm_deblur_wiener", "lsrtm_cg_get_state", "lsrtm_cg_set_state"]
 
 
 class LsrtmError(RuntimeError):
@@ -102,6 +102,8 @@ def load_library(path: str | None = None):
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
     L.lsrtm_autotune.argtypes = [vp, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double), ip]
     L.lsrtm_deblur.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+    L.lsrtm_cg_get_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ip]
+    L.lsrtm_cg_set_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     L.lsrtm_deblur_wiener.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
     L.lsrtm_model.argtypes = [vp, vp]
     L.lsrtm_mute_residual.argtypes = [vp, vp, vp] + [ctypes.c_double] * 5 + [vp]
@@ -373,6 +375,28 @@ class Lsrtm:
         _check(self._lib.lsrtm_cg_begin(self._h, _ptr(d),
                                         None if x0 is None else _ptr(self._cg_keep[1]),
                                         int(bool(precond)), int(param_mask)))
+
+    def cg_get_state(self) -> dict:
+        """State of the active step-wise CGNR solve as host numpy arrays:
+        x, p [2, *shape], r [nrec_total, nt], scalars [gamma, <d,d>], iter."""
+        self._sync_stream()
+        x = np.empty((2,) + self.shape, np.float32)
+        p = np.empty_like(x)
+        r = np.empty((self.nrec_total, self.nt), np.float32)
+        sc = (ctypes.c_double * 2)()
+        it = ctypes.c_int()
+        _check(self._lib.lsrtm_cg_get_state(self._h, _ptr(x), _ptr(p), _ptr(r), sc, ctypes.byref(it)))
+        return {"x": x, "p": p, "r": r, "scalars": np.array(list(sc)), "iter": int(it.value)}
+
+    def cg_set_state(self, state: dict):
+        """Restores a state from cg_get_state after cg_begin with the same d,
+        precond and param_mask; later cg_iterate calls continue bit for bit."""
+        self._sync_stream()
+        x = np.ascontiguousarray(state["x"], np.float32)
+        p = np.ascontiguousarray(state["p"], np.float32)
+        r = np.ascontiguousarray(state["r"], np.float32)
+        sc = (ctypes.c_double * 2)(*[float(v) for v in state["scalars"]])
+        _check(self._lib.lsrtm_cg_set_state(self._h, _ptr(x), _ptr(p), _ptr(r), sc, int(state["iter"])))
 
     def cg_iterate(self, niter=1, misfit=False):
         """Runs niter CGNR iterations; returns their misfits if misfit=True."""

@@ -1668,6 +1668,55 @@ lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit)
     return LSRTM_OK;
 }
 
+lsrtm_status lsrtm_cg_get_state(lsrtm_handle *h, float *x, float *p, float *r, double *scalars, int *iter)
+{
+    if (!h || !x || !p || !r || !scalars || !iter) return fail(LSRTM_ERR_ARG, "null argument");
+    if (!h->cg_active) return fail(LSRTM_ERR_STATE, "lsrtm_cg_begin has not been called");
+    CHECK(begin_call(h));
+    const long long nm = 2 * h->nint, nd = h->nrec_total * h->g.nt;
+    CHECK(copy_out(h, x, h->cg_x, nm));
+    CHECK(copy_out(h, p, h->cg_p, nm));
+    CHECK(copy_out(h, r, h->cg_r, nd));
+    double sc[2] = {0.0, 0.0};
+    CU(cudaMemcpyAsync(&sc[0], h->scal + 0, sizeof(double), cudaMemcpyDeviceToHost, h->work));
+    CU(cudaMemcpyAsync(&sc[1], h->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, h->work));
+    CHECK(end_call(h, true));
+    CU(cudaMemcpy(scalars, sc, sizeof(sc), cudaMemcpyDefault));
+    *iter = h->cg_iter;
+    return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_cg_set_state(lsrtm_handle *h, const float *x, const float *p, const float *r,
+                                const double *scalars, int iter)
+{
+    if (!h || !x || !p || !r || !scalars) return fail(LSRTM_ERR_ARG, "null argument");
+    if (iter < 0) return fail(LSRTM_ERR_ARG, "iteration count < 0");
+    if (!h->cg_active) return fail(LSRTM_ERR_STATE, "lsrtm_cg_begin has not been called");
+    CHECK(begin_call(h));
+    const long long nm = 2 * h->nint, nd = h->nrec_total * h->g.nt;
+    double sc[2];
+    CU(cudaMemcpy(sc, scalars, sizeof(sc), cudaMemcpyDefault));
+    if (h->mis_cap < iter + 1) {
+        const int cap = std::max(2 * (iter + 1), 64);
+        double *nb = nullptr;
+        CHECK(dalloc_t(h, &nb, cap));
+        if (h->mis_dev) CU(cudaMemcpyAsync(nb, h->mis_dev, h->mis_cap * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           h->work));
+        h->mis_dev = nb;
+        h->mis_cap = cap;
+    }
+    CHECK(copy_out(h, h->cg_x, x, nm));
+    CHECK(copy_out(h, h->cg_p, p, nm));
+    CHECK(copy_out(h, h->cg_r, r, nd));
+    CU(cudaMemcpyAsync(h->scal + 0, &sc[0], sizeof(double), cudaMemcpyHostToDevice, h->work));
+    CU(cudaMemcpyAsync(h->scal + 3, &sc[1], sizeof(double), cudaMemcpyHostToDevice, h->work));
+    CU(launch_dot(h->cg_r, h->cg_r, nd, h->mis_dev + iter, h->dotwork, h->work));   // <r, r> of that iterate
+    h->launches++;
+    h->cg_iter = iter;
+    // the host copies of the scalars must outlive the queued copies
+    return end_call(h, true);
+}
+
 lsrtm_status lsrtm_cg_result(lsrtm_handle *h, float *dm, double *misfit0)
 {
     if (!h || !dm) return fail(LSRTM_ERR_ARG, "null argument");
