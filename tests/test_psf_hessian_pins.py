@@ -258,3 +258,15 @@ def test_two_parameter_solution_follows_the_block_inverse():
     assert np.all(xm[0] == 0.0)
     # the paper's point: the two differ, by the coupling term
     assert not np.allclose(x2, x2_mono, atol=1e-3 * np.abs(x2).max())
+
+
+def test_cgnr_reaches_the_minimum_norm_solution_3d():
+    shape, s, half = (6, 6, 6), 3, 1
+    a, _ = li.psf_images3(*shape, s, seed=14)
+    bl = ph.block_patches(a, a.copy(), s, half)    # the Ip columns repeat the Vp columns
+    H = ph.explicit(bl, s, half, shape)
+    d = np.random.default_rng(15).standard_normal((2,) + shape)
+    ref = np.linalg.pinv(H, rcond=1e-12) @ d.ravel()
+    x, mis = ph.cgnr(bl, s, half, d, 800)     # cond(H) ~ 480 on its range: ~800 iterations in FP64
+    assert np.linalg.norm(x.ravel() - ref) <= 1e-8 * np.linalg.norm(ref)
+    assert np.array_equal(x[0], x[1])
