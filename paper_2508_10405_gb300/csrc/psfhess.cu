@@ -16,8 +16,9 @@
 //   of the four blocks (00, 01, 10, 11), so one 16-byte load serves all four.
 // k_psfh_apply<MASK, TR, R>: one thread per output column and R consecutive
 //   rows (R = the largest of 8, 4, 2, 1 not above s), CTAs of 32 columns x
-//   2 R rows (small CTAs spread the one wave evenly over the SMs). The input planes over the tile plus a half-wide halo and the
-//   corner tables of the halo's rows and columns sit in shared memory. Per
+//   2 R rows (small CTAs spread the one wave evenly over the SMs). The input
+//   planes over the tile plus a half-wide halo and the corner tables of the
+//   halo's rows and columns sit in shared memory. Per
 //   window offset a thread reads the six node windows covering its rows
 //   (three node rows, two node columns; R <= s rows cross at most one node
 //   row) through L1, interpolates along x once and along z per row: one
@@ -25,6 +26,8 @@
 //   of a one-pixel-per-thread form) below the FMA pipe.
 //   TR = false: y(r) = sum_a H(r, r - a) x(r - a), the columns gathered at r;
 //   TR = true:  y(c) = sum_a H(c + a, c) x(c + a), the transpose.
+// k_psfh3_patches, k_psfh3_rows: the same for 3D images, with the eight
+//   corners of Eq. (trilinear) and (y, x) columns of R z rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
