@@ -199,8 +199,9 @@ lsrtm_status lsrtm_timing_enable(lsrtm_handle *h, int enable);
 lsrtm_status lsrtm_timing_read(lsrtm_handle *h, lsrtm_timings *out, int reset);
 
 /* Born modelling without any device allocation, for callers that cannot
- * call cudaMalloc (allocation-free graph capture, host applications that own
- * the GPU memory pool, real-time loops). The paper has no counterpart: this
+ * call cudaMalloc (host applications that own the GPU memory pool and forbid
+ * foreign allocations, real-time loops where an allocation and the device
+ * synchronisation it may cause are not allowed). The paper has no counterpart: this
  * is a deployment variant of lsrtm_born. It computes the same d = L dm for a
  * 2D grid, taking every byte of device workspace from one fixed 32 MiB
  * array that lives in this library's device image (each GPU that loads the
@@ -208,7 +209,8 @@ lsrtm_status lsrtm_timing_read(lsrtm_handle *h, lsrtm_timings *out, int reset);
  * allocating library routine.
  *   cfg     : as for lsrtm_create; 2D only, and cfg->pml_vmax must be > 0
  *   vp, rho, wavelet, dm : device pointers (layouts as for lsrtm_create / lsrtm_born)
- *   geom    : host arrays, as for lsrtm_create
+ *   geom    : host arrays, as for lsrtm_create; copied with cudaMemcpyAsync
+ *             before the call returns, so they may be freed afterwards
  *   d       : device pointer, [nrec_total][nt] output
  *   stream  : cudaStream_t for all the work (NULL = legacy default stream)
  * Problems whose workspace exceeds 32 MiB are rejected with LSRTM_ERR_OOM
@@ -216,8 +218,9 @@ lsrtm_status lsrtm_timing_read(lsrtm_handle *h, lsrtm_timings *out, int reset);
  * array and leave their contents in it; each call re-initialises what it
  * reads, but calls whose GPU work overlaps race, so order them. The first
  * call on a device looks up the array's device address and configures the
- * kernels; make it before any stream capture. Returns once the work is
- * queued. */
+ * kernels; make it before any stream capture. Inputs are not checked for
+ * finiteness (a non-finite model gives non-finite records, not an error).
+ * Returns once the work is queued. */
 lsrtm_status lsrtm_born_static(const lsrtm_config *cfg, const float *vp, const float *rho,
                                const float *wavelet, const lsrtm_geometry *geom, const float *dm,
                                float *d, void *stream);

@@ -213,6 +213,11 @@ class Lsrtm:
                    rec_idx=w.geom.rec_idx, win_x0=getattr(w.geom, "win_x0", None),
                    win_nx=getattr(w.geom, "win_nx", None), **kw)
 
+    @property
+    def model_shape(self) -> tuple:
+        """Interior model grid, (nz, nx) or (nz, ny, nx)."""
+        return self.shape
+
     # -- helpers
     def _empty(self, shape):
         import torch
@@ -264,6 +269,13 @@ class Lsrtm:
         _check(self._lib.lsrtm_adjoint(self._h, _ptr(d), _ptr(out),
                                        _ptr(ph) if ph is not None else None))
         return (out, ph) if pseudo_hessian else out
+
+    def pseudo_hessian(self):
+        """Pseudo-Hessian diagonal of App. B over this handle's shots,
+        [*shape] (cached by the library once computed)."""
+        import torch
+        z = torch.zeros((self.nrec_total, self.nt), dtype=torch.float32, device=self.device)
+        return self.adjoint(z, pseudo_hessian=True)[1]
 
     def psf(self, param, spacing, out=None):
         """PSF = L^T L comb (comb: unit spikes every `spacing` in plane `param`)."""

@@ -1111,11 +1111,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     CU(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     CU(cudaEventRecord(h->ev_in, h->user));
     CU(cudaStreamWaitEvent(h->work, h->ev_in, 0));
-    static bool configured = false;
-    if (!configured) {
-        CU(configure_2d_kernels());
-        configured = true;
-    }
+    CU(ensure_kernels_configured());
 
     GridDev &g = h->g;
     g.ndim = cfg->ndim;

@@ -6,7 +6,8 @@
 // columns on each side for M = 4) and marches down a z-chunk of the padded
 // grid:
 //   * along z the stencil operands live in per-thread register rings of
-//     length 2M (the march loop is unrolled by 2M, so the rings never move);
+//     length 2M plus a group of look-ahead entries (the march is unrolled by
+//     one group of rows and the rings shift after every group);
 //   * along x each row passes through one shared-memory row per field;
 //   * the global loads of row z + PD - 1 are issued as asynchronous copies
 //     (cp.async, zero-filled out of range) into a PD-deep shared-memory stage
@@ -19,6 +20,7 @@
 // step needs no grid-wide barrier. Inputs and outputs are separate (ping-pong)
 // buffers; each state field is read once and written once per step from HBM.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "lsrtm_internal.cuh"
@@ -959,6 +961,25 @@ cudaError_t configure_2d_kernels()
     cudaError_t e = attr_M<2>();
     if (e != cudaSuccess) return e;
     return attr_M<4>();
+}
+
+// Kernel attributes are per device: a flag per device index, set under a
+// mutex the first time a thread with that device current asks.
+cudaError_t ensure_kernels_configured()
+{
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    if ((e = configure_2d_kernels()) != cudaSuccess) return e;
+    if ((e = configure_3d_kernels()) != cudaSuccess) return e;
+    done[dev] = true;
+    return cudaSuccess;
 }
 
 cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess, cudaStream_t s)

@@ -175,6 +175,10 @@ cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands,
                          cudaStream_t s);
 cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s);
 cudaError_t configure_2d_kernels();
+cudaError_t configure_3d_kernels();
+// Sets the launch attributes (dynamic shared memory limits) of every kernel
+// on the current device, once per device; thread safe.
+cudaError_t ensure_kernels_configured();
 // Copies each windowed shot's model into its slot (both ping-pong buffers):
 // column x of the shot's grid takes model column npml + x0 + clamp(x - npml,
 // 0, nx_w - 1) of the full padded planes (edge replication of the window);

@@ -1,15 +1,19 @@
 // Born modelling for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA-graph
-// capture that must stay allocation-free, plugins whose host application owns
+// Some callers cannot call cudaMalloc: plugins whose host application owns
 // the GPU memory pool and forbids foreign allocations, and real-time loops
 // where an allocation (and the implicit device synchronisation it can cause)
 // is not allowed. lsrtm_born_static serves them: it computes the same d = L dm
 // as lsrtm_born, but every byte of device workspace it needs comes from one
 // file-scope __device__ array of fixed size (kStaticBytes), which every GPU
 // that loads this library holds until the process exits. The caller passes
-// all inputs and the output as device pointers; the call allocates nothing
-// on the device (no cudaMalloc, no cudaFree, no allocating library routine).
+// the model, wavelet, perturbation and output as device pointers and the
+// geometry as host arrays, which are copied into the array with
+// cudaMemcpyAsync before the call returns (the caller may free them
+// afterwards); the call allocates nothing on the device (no cudaMalloc, no
+// cudaFree, no allocating library routine). Inputs are not checked for
+// finiteness: a NaN or Inf in the model gives non-finite records rather than
+// an error status.
 //
 // Shared-state rules:
 //   * the array is shared by every call on a device and keeps the contents of
@@ -63,7 +67,7 @@ lsrtm_status static_workspace(void **out)
         e = cudaGetSymbolAddress(&p, g_static_ws);
         if (e != cudaSuccess || !p)
             return fail(LSRTM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        e = configure_2d_kernels();
+        e = ensure_kernels_configured();
         if (e != cudaSuccess)
             return fail(LSRTM_ERR_CUDA, std::string("kernel configuration: ") + cudaGetErrorString(e));
         g_ws_addr[dev] = p;

@@ -83,11 +83,12 @@ def test_3d_pseudo_hessian_psf_and_cg():
     dobs = oracle.born(w, w.dm)
     x, mis = h.cg_solve(torch.tensor(dobs, dtype=torch.float32, device="cuda"), 3)
     xr, misr = oracle.lsrtm_cg(w, dobs, 3)
-    assert np.all(np.abs(mis - misr) < 1e-3), (mis, misr)
-    assert rel(cpu(x), xr) < 1e-3
+    print(f"3D CGNR: misfit max abs diff {np.max(np.abs(mis - misr)):.3e}, iterate rel L2 {rel(cpu(x), xr):.3e}")
+    assert np.all(np.abs(mis - misr) < TOL), (mis, misr)
+    assert rel(cpu(x), xr) < TOL
 
 
-@pytest.mark.parametrize("fmt,tol", [("bf16", 1e-2), ("fp16", 1e-3)])
+@pytest.mark.parametrize("fmt,tol", [("bf16", 1e-3), ("fp16", 1e-3)])
 def test_3d_16bit_bands(fmt, tol):
     from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16
     w = li.small_case(**CASES3["o4"])
@@ -140,5 +141,29 @@ def test_3d_full_size_two_shots():
     g16 = h16.adjoint(Lm)
     e16 = rel(cpu(g16), cpu(g32))
     print(f"3D full-size migration with BF16 bands vs FP32 bands: rel L2 {e16:.3e}")
-    assert e16 < 1e-2
+    assert e16 < 1e-3
     h16.close()
+
+
+def test_3d_full_size_migration_vs_oracle():
+    """Full 3D grid, order 8, nt = 3000, one shot of the dipping-layer
+    workload: the residual is zero except in the first n_s samples, so L^T d
+    equals the oracle's L^T of that shot with nt = n_s; on the GPU the
+    background is first rebuilt from the boundary bands through all of the
+    3000 - n_s later steps, which tests the 3D reconstruction over the full
+    time axis. A Gaussian scatterer below the source gives the early
+    background field a clear image to compare."""
+    w = li.preset(4)
+    w.geom = w.geom.subset([5])
+    ns = 40
+    rng = np.random.default_rng(44)
+    nrec = w.geom.nrec_total
+    part = rng.standard_normal((nrec, ns))
+    h = handle(w)
+    dfull = torch.zeros((nrec, w.nt), dtype=torch.float32, device="cuda")
+    dfull[:, :ns] = torch.tensor(part, dtype=torch.float32, device="cuda")
+    g = cpu(h.adjoint(dfull))
+    h.close()
+    ref = oracle.adjoint(w, part, nt=ns)
+    print(f"3D full-size migration, residual in the first {ns} of {w.nt} steps: rel L2 {rel(g, ref):.3e}")
+    assert rel(g, ref) < TOL

@@ -189,8 +189,9 @@ def test_cg_matches_oracle_cg():
     h = handle(w)
     x, mis = h.cg_solve(torch.tensor(d, dtype=torch.float32, device="cuda"), 4)
     xr, misr = oracle.lsrtm_cg(w, d, 4)
-    assert np.all(np.abs(mis - misr) < 1e-3), (mis, misr)
-    assert rel(cpu(x), xr) < 1e-3
+    print(f"CGNR: misfit max abs diff {np.max(np.abs(mis - misr)):.3e}, iterate rel L2 {rel(cpu(x), xr):.3e}")
+    assert np.all(np.abs(mis - misr) < TOL), (mis, misr)
+    assert rel(cpu(x), xr) < TOL
 
 
 def test_pcg_and_monoparameter_match_oracle():
@@ -200,16 +201,18 @@ def test_pcg_and_monoparameter_match_oracle():
     x, mis = h.cg_solve(torch.tensor(d, dtype=torch.float32, device="cuda"), 3, precond=True,
                         param_mask=2)
     xr, misr = oracle.lsrtm_cg(w, d, 3, precond=True, param_mask=2)
+    print(f"PCGNR Ip: misfit max abs diff {np.max(np.abs(mis - misr)):.3e}, iterate rel L2 {rel(cpu(x), xr):.3e}")
     assert np.all(cpu(x)[0] == 0)
-    assert np.all(np.abs(mis - misr) < 1e-3), (mis, misr)
-    assert rel(cpu(x), xr) < 1e-3
+    assert np.all(np.abs(mis - misr) < TOL), (mis, misr)
+    assert rel(cpu(x), xr) < TOL
 
 
-@pytest.mark.parametrize("fmt,tol", [("bf16", 1e-2), ("fp16", 1e-3)])
+@pytest.mark.parametrize("fmt,tol", [("bf16", 1e-3), ("fp16", 1e-3)])
 def test_16bit_bands_error_stated(fmt, tol):
     """16-bit boundary bands with one FP32 scale per band per step: the image
     error against the FP64 oracle and against the FP32-band result is stated
-    and bounded (BF16 keeps 8 mantissa bits, FP16 11)."""
+    and held to the 1e-3 bar of the mixed-precision path (BF16 keeps 8
+    mantissa bits, FP16 11)."""
     from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16
     w = li.small_case(**CASES["o8"])
     rng = np.random.default_rng(3)

@@ -1,6 +1,7 @@
 """lsrtm_born_static: Born modelling for callers that cannot allocate device
-memory (allocation-free graph capture, host applications that own the GPU
-memory pool, real-time loops). It must give the same records as lsrtm_born
+memory (host applications that own the GPU memory pool and forbid foreign
+allocations, real-time loops that must not allocate). It must give the same
+records as lsrtm_born
 (the handle-based entry point) within the parity tolerance, on consecutive
 calls that share its fixed static workspace, and must refuse problems larger
 than that workspace with a clear error.
@@ -21,7 +22,7 @@ torch = pytest.importorskip("torch")
 TOL = 1e-4
 
 
-def _static_call(lib, w, dm_dev, d_dev):
+def _static_call(lib, w, dm_dev, d_dev, dev=None):
     from paper_2508_10405_gb300.binding import Config, GeometryC
     cfg = Config(2, w.nz, 1, w.nx, w.dz, w.dy, w.dx, w.dt, w.nt, w.order, w.npml, w.f0,
                  float(np.max(w.vp)), 0, 0, 0, 0, 0, 0)
@@ -30,9 +31,11 @@ def _static_call(lib, w, dm_dev, d_dev):
     ri = np.ascontiguousarray(w.geom.rec_idx, np.int32)
     ip = ctypes.POINTER(ctypes.c_int)
     geo = GeometryC(len(src), src.ctypes.data_as(ip), rp.ctypes.data_as(ip), ri.ctypes.data_as(ip))
-    vp = torch.tensor(w.vp, dtype=torch.float32, device="cuda")
-    rho = torch.tensor(w.rho, dtype=torch.float32, device="cuda")
-    wav = torch.tensor(w.wavelet, dtype=torch.float32, device="cuda")
+    if dev is None:
+        dev = (torch.tensor(w.vp, dtype=torch.float32, device="cuda"),
+               torch.tensor(w.rho, dtype=torch.float32, device="cuda"),
+               torch.tensor(w.wavelet, dtype=torch.float32, device="cuda"))
+    vp, rho, wav = dev
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib.lsrtm_born_static(ctypes.byref(cfg), ctypes.c_void_p(vp.data_ptr()),
                                ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(wav.data_ptr()),
@@ -56,14 +59,24 @@ def test_static_born_matches_handle_born_on_consecutive_calls():
     dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
     ref = h.born(dm)
     torch.cuda.synchronize()
-    outs = []
+    outs = [torch.full((w.geom.nrec_total, w.nt), float("nan"), dtype=torch.float32, device="cuda")
+            for _ in range(2)]
+    # the inputs of the calls exist before the first one, so the device's free
+    # memory can only change if a call allocates
+    vp = torch.tensor(w.vp, dtype=torch.float32, device="cuda")
+    rho = torch.tensor(w.rho, dtype=torch.float32, device="cuda")
+    wav = torch.tensor(w.wavelet, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free = []
     for call in range(2):
-        d = torch.full((w.geom.nrec_total, w.nt), float("nan"), dtype=torch.float32, device="cuda")
-        rc = _static_call(lib, w, dm, d)
+        rc = _static_call(lib, w, dm, outs[call], dev=(vp, rho, wav))
         assert rc == 0, lib.lsrtm_last_error().decode()
-        err = _rel(d, ref)
+        free.append(torch.cuda.mem_get_info()[0])
+    # (the first call may load kernel code; the second may not take any memory)
+    assert free[1] == free[0], ("lsrtm_born_static changed the free device memory", free)
+    for call in range(2):
+        err = _rel(outs[call], ref)
         assert err < TOL, (call, err)
-        outs.append(d)
     # the second call reuses the same static workspace and reproduces the first
     assert _rel(outs[1], outs[0]) < TOL
     # a different problem in between leaves no trace in a later call
