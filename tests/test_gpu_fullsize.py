@@ -94,6 +94,23 @@ def test_dot_product_full_size(cfg2):
     assert abs(a - b) / a < 1e-6, (a, b)
 
 
+def test_bf16_bands_full_size(cfg2):
+    """The mixed-precision bar at the benchmark's size: the migration image
+    with BF16 bands (one FP32 scale per band per step) within relative L2
+    1e-3 of the FP32-band image, for the data L dm of the workload."""
+    from paper_2508_10405_gb300 import BAND_BF16, Lsrtm
+    w, h = cfg2
+    dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    d = h.born(dm)
+    g32 = h.adjoint(d).double().cpu().numpy()
+    h16 = Lsrtm.from_workload(w, band_precision=BAND_BF16)
+    g16 = h16.adjoint(d).double().cpu().numpy()
+    h16.close()
+    e = rel(g16, g32)
+    print(f"full-size migration, BF16 vs FP32 bands: rel L2 {e:.3e}")
+    assert e < 1e-3, e
+
+
 def _grad_gpu(w, x, d_obs):
     from paper_2508_10405_gb300 import Lsrtm, born_op
     h = Lsrtm.from_workload(w)
