@@ -250,6 +250,14 @@ lsrtm_status lsrtm_model(lsrtm_handle *h, float *d);
 lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const float *d_syn, double v_mute, double t0,
                                  double t_taper, double o_max, double o_taper, float *d_out);
 
+/* Waits for all work queued by the handle and reports a failure that a
+ * kernel recorded on the device (a bounded wait for its tile copies that
+ * gave up, or a refused misaligned copy) as LSRTM_ERR_CUDA; the record is
+ * cleared. Operator calls are asynchronous, so such a failure surfaces here
+ * or at the next synchronous call. The paper has no counterpart: this is
+ * host-side error handling. */
+lsrtm_status lsrtm_synchronize(lsrtm_handle *h);
+
 /* Replaces the stream used by later calls. */
 lsrtm_status lsrtm_set_stream(lsrtm_handle *h, void *stream);
 

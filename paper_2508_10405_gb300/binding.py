@@ -31,7 +31,7 @@ EXPORTS = ["lsrtm_create", "lsrtm_born", "lsrtm_adjoint", "lsrtm_psf", "lsrtm_re
            "lsrtm_workspace_bytes", "lsrtm_kernel_launches", "lsrtm_destroy", "lsrtm_last_error",
            "lsrtm_born_static", "lsrtm_reconstruction", "lsrtm_deblur", "lsrtm_autotune",
            "lsrtm_psf_hessian", "lsrtm_psf_cg", "lsrtm_model", "lsrtm_mute_residual",
-           "lsrtm_deblur_wiener", "lsrtm_cg_get_state", "lsrtm_cg_set_state"]
+           "lsrtm_deblur_wiener", "lsrtm_cg_get_state", "lsrtm_cg_set_state", "lsrtm_synchronize"]
 
 
 class LsrtmError(RuntimeError):
@@ -97,6 +97,7 @@ def load_library(path: str | None = None):
     L.lsrtm_timing_enable.argtypes = [vp, ctypes.c_int]
     L.lsrtm_timing_read.argtypes = [vp, ctypes.POINTER(Timings), ctypes.c_int]
     L.lsrtm_set_stream.argtypes = [vp, vp]
+    L.lsrtm_synchronize.argtypes = [vp]
     L.lsrtm_born_static.argtypes = [ctypes.POINTER(Config), vp, vp, vp, ctypes.POINTER(GeometryC), vp, vp, vp]
     ip = ctypes.POINTER(ctypes.c_int)
     L.lsrtm_reconstruction.argtypes = [vp, ip, ip, ip]
@@ -229,6 +230,11 @@ class Lsrtm:
     @property
     def handle(self):
         return self._h
+
+    def synchronize(self):
+        """Waits for the handle's queued work; raises LsrtmError if a kernel
+        recorded a failure on the device."""
+        _check(self._lib.lsrtm_synchronize(self._h))
 
     def workspace_bytes(self) -> int:
         return int(self._lib.lsrtm_workspace_bytes(self._h))

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liblsrtm.so")
-SOURCES = ["engine.cu", "kernels2d.cu", "kernels3d.cu", "kernels_util.cu", "noalloc.cu", "deblur.cu", "psfhess.cu"]
+SOURCES = ["engine.cu", "kernels2d.cu", "kernels3d.cu", "kernels3d_fused.cu", "kernels_util.cu", "noalloc.cu", "deblur.cu", "psfhess.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fno-strict-aliasing"]

@@ -101,6 +101,9 @@ struct lsrtm_handle {
     int batch = 1;
     float *st[2] = {nullptr, nullptr};
     long long sstride = 0;
+    long long sstride1 = 0;      // slot stride of st[1] (3D: the fused kernels' pong buffer)
+    Step3F f3born[2];            // fused 3D Born step arguments reading st[0] / st[1]
+    int *kerr = nullptr;         // device error word of the fused kernels
     float *psiv = nullptr;
     long long vstride = 0;
     float2 *img = nullptr;
@@ -235,12 +238,17 @@ lsrtm_status begin_call(lsrtm_handle *h)
 }
 
 // Orders the caller's stream after the work queued by this call.
+lsrtm_status check_kernel_error(lsrtm_handle *h);
+
 lsrtm_status end_call(lsrtm_handle *h, bool sync)
 {
     CU(cudaGetLastError());
     CU(cudaEventRecord(h->ev_out, h->work));
     CU(cudaStreamWaitEvent(h->user, h->ev_out, 0));
-    if (sync) CU(cudaStreamSynchronize(h->work));
+    if (sync) {
+        CU(cudaStreamSynchronize(h->work));
+        CHECK(check_kernel_error(h));
+    }
     return LSRTM_OK;
 }
 
@@ -372,7 +380,7 @@ long long loop_launches(const lsrtm_handle *h, int kind)
 {
     const long long nt = h->g.nt;
     const long long pack = (kind == G_BG || kind == G_BG_HESS) && h->bands.fmt != BAND_F32 ? nt : 0;
-    if (h->g.ndim != 3) return nt + pack;
+    if (h->g.ndim != 3 || kind == G_BORN) return nt + pack;   // 2D and the fused 3D Born: one launch per step
     return (kind == G_ADJ ? 2 * nt - 1 : 2 * nt) + pack;
 }
 
@@ -461,9 +469,8 @@ int batch_size(const lsrtm_handle *h, int shot0) { return std::min(h->batch, h->
 
 lsrtm_status zero_slots(lsrtm_handle *h, int bs)
 {
-    size_t sb = (size_t)bs * h->sstride * sizeof(float);
-    CU(cudaMemsetAsync(h->st[0], 0, sb, h->work));
-    if (h->st[1]) CU(cudaMemsetAsync(h->st[1], 0, sb, h->work));
+    CU(cudaMemsetAsync(h->st[0], 0, (size_t)bs * h->sstride * sizeof(float), h->work));
+    if (h->st[1]) CU(cudaMemsetAsync(h->st[1], 0, (size_t)bs * h->sstride1 * sizeof(float), h->work));
     if (h->psiv) CU(cudaMemsetAsync(h->psiv, 0, (size_t)bs * h->vstride * sizeof(float), h->work));
     if (h->bands.stage)
         CU(cudaMemsetAsync(h->bands.stage, 0, (size_t)bs * 2 * h->bands.nb * sizeof(float), h->work));
@@ -555,10 +562,13 @@ lsrtm_status born_core(lsrtm_handle *h)
         CHECK(zero_slots(h, bs));
         CHECK(run_loop(h, G_BORN, s0, bs, [&]() -> lsrtm_status {
             if (is3d(h)) {
-                Step3D a = step3_args(h, s0);
                 for (int n = 0; n < nt; ++n) {
+                    Step3F &a = h->f3born[n & 1];
                     a.n = n;
-                    CU(launch_fwd3d(a, bs, true, false, false, 3, h->work));
+                    a.shot0 = s0;
+                    a.trec = h->trv;
+                    a.tzc = h->tzc;
+                    CU(launch_born3f(a, bs, h->work));
                 }
                 return LSRTM_OK;
             }
@@ -940,14 +950,18 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
 lsrtm_status build_tiles(lsrtm_handle *h)
 {
     const GridDev &g = h->g;
-    int ntx = (g.Nx + h->txo - 1) / h->txo, ntz = (g.Nz + h->tzc - 1) / h->tzc;
-    int ntiles = ntx * ntz;
+    // 2D: CTA tiles of txo columns x tzc rows; 3D: kTile3X x kTile3Y columns x tzc rows
+    const bool d3 = g.ndim == 3;
+    const int tw = d3 ? kTile3X : h->txo;
+    int ntx = (g.Nx + tw - 1) / tw, ntz = (g.Nz + h->tzc - 1) / h->tzc;
+    int nty = d3 ? (g.Ny + kTile3Y - 1) / kTile3Y : 1;
+    int ntiles = ntx * nty * ntz;
     std::vector<std::vector<int2>> lists((size_t)h->nshot * ntiles);
     for (int s = 0; s < h->nshot; ++s)
         for (int r = h->rec_ptr[s]; r < h->rec_ptr[s + 1]; ++r) {
             int2 e = h->rec_cells_h[r];
-            int z = (int)(e.x / g.rowz), x = (int)(e.x % g.pitch);
-            int t = (z / h->tzc) * ntx + x / h->txo;
+            int z = (int)(e.x / g.rowz), y = (int)((e.x % g.rowz) / g.pitch), x = (int)(e.x % g.pitch);
+            int t = ((z / h->tzc) * nty + (d3 ? y / kTile3Y : 0)) * ntx + x / tw;
             lists[(size_t)s * ntiles + t].push_back(e);
         }
     std::vector<int> ptr(lists.size() + 1, 0);
@@ -1050,7 +1064,13 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         for (int s = 0; s < h->nshot; ++s)
             CU(launch_rmap_scatter(h->rmap + (size_t)s * g.plane, h->rcell, rptr[s], rptr[s + 1], h->work));
         CU(cudaStreamSynchronize(h->work));
-        return LSRTM_OK;
+        // receivers per fused-kernel tile
+        h->rec_cells_h.resize(h->nrec_total);
+        for (int s = 0; s < h->nshot; ++s)
+            for (int r = geo->rec_ptr[s]; r < geo->rec_ptr[s + 1]; ++r)
+                h->rec_cells_h[r] = make_int2((int)pad_cell(geo->rec_idx[r], s), r);
+        CHECK(dalloc_t(h, &h->trec, std::max<size_t>(h->rec_cells_h.size(), 1)));
+        return build_tiles(h);
     }
     h->rec_cells_h.resize(h->nrec_total);
     for (int s = 0; s < h->nshot; ++s)
@@ -1099,6 +1119,50 @@ lsrtm_status setup_windows(lsrtm_handle *h, const lsrtm_geometry *geo)
     return LSRTM_OK;
 }
 
+// Arguments of the fused 3D Born step reading buffer `b` (0: st[0], 1: st[1]),
+// with its tensor maps; the launches change only n, in/out and shot0.
+lsrtm_status setup_fused3d(lsrtm_handle *h)
+{
+    for (int b = 0; b < 2; ++b) {
+        Step3F &a = h->f3born[b];
+        a = Step3F{};
+        a.g = h->g;
+        a.pml = h->pml;
+        a.in = h->st[b];
+        a.out = h->st[1 - b];
+        a.in_pairs = (int)((b ? h->sstride1 : h->sstride) / (2 * h->g.plane));
+        a.out_pairs = (int)((b ? h->sstride : h->sstride1) / (2 * h->g.plane));
+        a.psiv = h->st[0] + 2LL * kBornPairs3F * h->g.plane;
+        a.psiv_pairs = (int)(h->sstride / (2 * h->g.plane));
+        a.br2 = h->br2;
+        a.tzc = h->tzc;
+        a.wav = h->wav;
+        a.wav_per_shot = h->cfg.wavelet_per_shot;
+        a.src_cell = h->src_cell;
+        a.src_scale = h->src_scale;
+        a.dstage = h->dstage;
+        a.err = h->kerr;
+        cudaError_t e = fused3d_born_maps(a, h->kd2, h->br2, h->batch);
+        if (e != cudaSuccess) return fail(LSRTM_ERR_CUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
+    }
+    return LSRTM_OK;
+}
+
+// Reads and clears the fused kernels' error word (synchronises the work stream).
+lsrtm_status check_kernel_error(lsrtm_handle *h)
+{
+    if (!h->kerr) return LSRTM_OK;
+    int e = 0;
+    CU(cudaMemcpyAsync(&e, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+    CU(cudaStreamSynchronize(h->work));
+    if (!e) return LSRTM_OK;
+    CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), h->work));
+    return fail(LSRTM_ERR_CUDA, (e & 2) ? "a fused 3D kernel refused a misaligned tile copy"
+                                        : "a fused 3D kernel gave up waiting for its tile copies");
+}
+
+int geo_nshot(const lsrtm_geometry *geo) { return geo && geo->nshot > 0 ? geo->nshot : 1; }
+
 lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *rho,
                          const float *wavelet, const lsrtm_geometry *geo, void *stream,
                          lsrtm_handle *h)
@@ -1142,7 +1206,13 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     h->nint = (long long)g.nz * g.ny * g.nx;
     // CTA blocking: output columns fixed by the kernel, z-chunks of about 112 rows
     h->txo = march2d_txo(g.M);
-    {
+    if (d3) {
+        // enough CTAs for two waves of one CTA per SM, chunks of at least 8M rows
+        const int ntxy = ((g.Nx + kTile3X - 1) / kTile3X) * ((g.Ny + kTile3Y - 1) / kTile3Y);
+        const int want = (2 * 152 + ntxy * geo_nshot(geo) - 1) / std::max(1, ntxy * geo_nshot(geo));
+        const int nchunk = std::max(1, std::min(want, g.Nz / (8 * g.M)));
+        h->tzc = (g.Nz + nchunk - 1) / nchunk;
+    } else {
         int nchunk = std::max(1, (g.Nz + 56) / 112);
         h->tzc = (g.Nz + nchunk - 1) / nchunk;
     }
@@ -1178,8 +1248,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     }
     CHECK(dalloc_t(h, &h->kdt, g.plane));
     CHECK(dalloc_t(h, &h->binv, g.plane));
-    CHECK(dalloc_t(h, &h->kd2, g.plane));
-    CHECK(dalloc_t(h, &h->br2, g.plane));
+    CHECK(dalloc_t(h, &h->kd2, 2 * g.plane));   // (kd2, br2) adjacent: one tensor map covers both
+    h->br2 = h->kd2 + g.plane;
     CU(launch_model_prep(g, vp_d, rho_d, h->kdt, h->binv, h->work));
     h->launches++;
     h->gm = g;
@@ -1268,7 +1338,11 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     // of 20 planes (pairs, CPML memories, images) + the pseudo-Hessian plane
     h->sstride = (d3 ? kStatePlanes3D : (h->win ? kWinStatePlanes2D : kStatePlanes2D)) * g.plane;
     h->vstride = d3 ? 0 : kPsivPlanes2D * g.plane;
-    size_t per_slot = d3 ? ((size_t)h->sstride + g.plane) * sizeof(float)
+    // 3D: st[0] (20 planes; the fused kernels use its first 14 as ping and the
+    // last 6 as the in-place node CPML memories), st[1] (14 planes, pong), the
+    // float2 image plane and the pseudo-Hessian plane
+    h->sstride1 = d3 ? 2LL * kBornPairs3F * g.plane : h->sstride;
+    size_t per_slot = d3 ? ((size_t)h->sstride + h->sstride1 + 3 * g.plane) * sizeof(float)
                          : (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
     if (h->bands.fmt != BAND_F32) per_slot += 2 * (size_t)h->bands.nb * sizeof(float);   // FP32 band stage
     int batch = cfg->plan == LSRTM_PLAN_PLAIN ? 1 : (cfg->shots_per_batch > 0 ? cfg->shots_per_batch : h->nshot);
@@ -1354,12 +1428,12 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         h->segbands.stage = h->bands.stage;
     }
     CHECK(dalloc_t(h, &h->st[0], (size_t)batch * h->sstride));
-    if (!d3) {
-        CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride));
-        CHECK(dalloc_t(h, &h->psiv, (size_t)batch * h->vstride));
-        CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
-    }
+    CHECK(dalloc_t(h, &h->st[1], (size_t)batch * h->sstride1));
+    if (!d3) CHECK(dalloc_t(h, &h->psiv, (size_t)batch * h->vstride));
+    CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
     CHECK(dalloc_t(h, &h->hess, (size_t)batch * g.plane));
+    CHECK(dalloc_t(h, &h->kerr, 4));
+    if (d3) CHECK(setup_fused3d(h));
     CU(cudaStreamSynchronize(h->work));
     return LSRTM_OK;
 }
@@ -2069,6 +2143,14 @@ lsrtm_status lsrtm_reconstruction(const lsrtm_handle *h, int *mode, int *interva
     if (interval) *interval = h->ckpt ? h->ck_K : 0;
     if (batch) *batch = h->batch;
     return LSRTM_OK;
+}
+
+lsrtm_status lsrtm_synchronize(lsrtm_handle *h)
+{
+    if (!h) return fail(LSRTM_ERR_ARG, "null handle");
+    CU(cudaStreamSynchronize(h->work));
+    CU(cudaGetLastError());
+    return check_kernel_error(h);
 }
 
 size_t lsrtm_workspace_bytes(const lsrtm_handle *h) { return h ? h->bytes : 0; }

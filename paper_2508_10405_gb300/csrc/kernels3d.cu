@@ -547,8 +547,6 @@ cudaError_t launch_pack_adjoint3d(const GridDev &g, const float *final_state, in
     return cudaGetLastError();
 }
 
-cudaError_t configure_3d_kernels() { return cudaSuccess; }
-
 cudaError_t launch_image_accumulate3d(const GridDev &g, const float *st, long long sstride, int batch,
                                       double2 *acc, cudaStream_t s)
 {

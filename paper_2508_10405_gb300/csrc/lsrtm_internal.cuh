@@ -5,6 +5,7 @@
 // A shot's state is a block of planes; shots of a batch are consecutive blocks.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -154,6 +155,40 @@ struct Step3D {
     const int *rcell;         // receiver cells, sorted by cell within a shot
     const int *rrow;          // global receiver rows
 };
+
+// Fused 3D time-step kernels (kernels3d_fused.cu): CTAs of kTile3X x kTile3Y
+// (x, y) columns marching a z-chunk of tzc rows, ping-pong state buffers.
+constexpr int kTile3X = 32, kTile3Y = 16;
+// Pair-plane offsets within a slot. Born ping-pong: (p, dp), (vx, dvx),
+// (vy, dvy), (vz, dvz), (psi_p, dpsi_p) x y z; the node CPML memories
+// (psi_v, dpsi_v) x y z live in a separate in-place block.
+enum { F3_P = 0, F3_VX = 1, F3_VY = 2, F3_VZ = 3, F3_PPX = 4, F3_PPY = 5, F3_PPZ = 6 };
+constexpr int kBornPairs3F = 7;
+
+struct Step3F {
+    // TMA descriptors (64-byte aligned, first): the input state's pair planes
+    // in four box shapes, the model pair planes (plane 0 kd2, plane 1 br2)
+    CUtensorMap in_core, in_wide, in_xbox, in_ybox, m_core, m_ybr;
+    GridDev g;
+    Pml pml;
+    const float *in;          // input state, slot s at in + s * in_pairs pair planes
+    float *out;               // output state, slot stride out_pairs pair planes
+    float *psiv;              // in-place node CPML memories, slot stride psiv_pairs pair planes
+    int in_pairs, out_pairs, psiv_pairs;
+    const float2 *br2;        // (1/rho, dln rho / rho), for the first rows of a march
+    int n, tzc, shot0;
+    const float *wav;
+    int wav_per_shot;
+    const int *src_cell;
+    float src_scale;
+    TileRecs trec;            // receivers per (shot, z-chunk, y tile, x tile)
+    float *dstage;            // records [nrec_total][nt]
+    int *err;                 // error word: 1 = a wait gave up, 2 = a misaligned copy was refused
+};
+cudaError_t make_tmap3(CUtensorMap *m, const void *base, const GridDev &g, int esz, long long nq, int bx, int by);
+cudaError_t fused3d_born_maps(Step3F &a, const float2 *kd2, const float2 *br2, int batch);
+size_t fused3d_born_smem(int M);
+cudaError_t launch_born3f(const Step3F &a, int batch, cudaStream_t s);
 
 // 3D launchers (kernels3d.cu). stages: 1 = velocity stage, 2 = pressure stage, 3 = both.
 cudaError_t launch_fwd3d(const Step3D &a, int batch, bool born, bool bands, bool hess, int stages,
