@@ -1123,6 +1123,9 @@ lsrtm_status setup_windows(lsrtm_handle *h, const lsrtm_geometry *geo)
 // with its tensor maps; the launches change only n, in/out and shot0.
 lsrtm_status setup_fused3d(lsrtm_handle *h)
 {
+    // the kernels index within a slot with 32-bit offsets
+    if (std::max(h->sstride, h->sstride1) >= (1LL << 31))
+        return fail(LSRTM_ERR_ARG, "3D grid too large for the fused kernels (slot above 2^31 floats)");
     for (int b = 0; b < 2; ++b) {
         Step3F &a = h->f3born[b];
         a = Step3F{};

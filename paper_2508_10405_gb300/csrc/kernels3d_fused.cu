@@ -3,15 +3,15 @@
 // its exact transpose (App. A), reading each state field once from HBM and
 // writing it once (ping-pong buffers).
 //
-// A CTA of 512 threads owns a 32 x 16 tile of (x, y) columns, one column per
-// thread, and marches down a z-chunk:
+// A CTA of 384 threads owns a 32 x 12 tile of (x, y) columns, one column per
+// thread, and marches down a z-chunk (two CTAs per SM):
 //   * z stencils: per-thread register rings of length 2M (+1 look-ahead),
 //     shifted after every row;
 //   * x and y stencils: shared-memory tiles of the current row. Every tile a
 //     row needs (the centre column block, the x-extended and y-extended
 //     halo blocks, the model) arrives by TMA (cp.async.bulk.tensor, one
-//     elected thread) into a 3-deep stage ring guarded by mbarriers, two
-//     rows ahead of the compute; the tensor maps zero-fill outside the padded
+//     elected thread) into a 2-deep stage ring guarded by mbarriers, one
+//     row ahead of the compute; the tensor maps zero-fill outside the padded
 //     array, which is the operators' boundary convention;
 //   * the velocity (half-node) stage is recomputed on the x and y halos, so
 //     the pressure stage of the same row needs nothing from other CTAs and a
@@ -34,7 +34,8 @@ namespace lsrtm {
 namespace {
 
 constexpr int TX = kTile3X, TY = kTile3Y, NTH = TX * TY;
-constexpr int PD = 3;                       // stage ring depth
+constexpr int PD = 2;                       // stage ring depth
+constexpr int kMinBlocks = 2;               // resident CTAs per SM the register budget targets
 constexpr unsigned kWaitLimit = 1u << 22;   // mbarrier polls before giving up
 
 // ---- packed arithmetic
@@ -199,7 +200,7 @@ __device__ __forceinline__ void born_issue(const Step3F &a, unsigned char *st, u
 }
 
 template <int M>
-__global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3F a)
+__global__ void __launch_bounds__(NTH, kMinBlocks) k3f_born(const __grid_constant__ Step3F a)
 {
     using G = Geo<M>;
     using S = BornSmem<M>;
@@ -262,18 +263,25 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
 
     bool failed = false;
     int fail_row = 0;
+    const int pl = (int)plane;   // in-slot offsets fit in 32 bits (checked by the host)
+    const int rowz = (int)g.rowz, pitch = g.pitch;
+    const int cxy32 = y * pitch + x;
     for (int z = zstart; z < zc1; ++z) {
         const int j = z - zstart;
-        if (t == 0 && z + PD - 1 < zc1) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            born_issue<M>(a, sm + ((j + PD - 1) % PD) * S::STAGE, bar + (j + PD - 1) % PD, slot, x0, y0, z + PD - 1,
-                          zc0, px, py);
-        }
         const bool to = !mbar_wait(bar + j % PD, (unsigned)(j / PD) & 1u);
+        // (this barrier also certifies that every thread is done with row z-1,
+        // its stage and the vx / vy tiles)
         if (__syncthreads_or(to)) {
             failed = true;
             fail_row = z;
             break;
+        }
+        // the last warp has no item in the last round of the halo loop: it
+        // refills the stage of row z-1 with row z+PD-1
+        if (t == NTH - 1 && z + PD - 1 < zc1) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            born_issue<M>(a, sm + ((j + PD - 1) % PD) * S::STAGE, bar + (j + PD - 1) % PD, slot, x0, y0, z + PD - 1,
+                          zc0, px, py);
         }
         const unsigned char *st = sm + (j % PD) * S::STAGE;
         const float2 *cPA = reinterpret_cast<const float2 *>(st + S::PA);
@@ -288,15 +296,16 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
         float2 vzn = make_float2(0.f, 0.f);
         if (colok && k >= 0 && k < g.Nz) {
             float2 Gz = st2<M>(g.cz, [&](int l) { return P[M - 1 + l]; }, [&](int l) { return P[M - l]; });
+            const bool own = k >= zc0 && k < zc1;
             if (k <= g.z0 - 2 || k >= g.z0 + g.nz) {
                 const float2 ps = fma2(a.pml.bh[0][k], cPZ[t], mul2(a.pml.ah[0][k], Gz));
-                if (k >= zc0 && k < zc1) out[F3_PPZ * plane + k * g.rowz + cxy] = ps;
+                if (own) out[F3_PPZ * pl + k * rowz + cxy32] = ps;
                 Gz = add2(Gz, ps);
             }
             const float bu = 0.5f * (br_old.x + brk1.x);
             vzn = fma2(-dt * bu, Gz, cVZ[t]);
             vzn.y = fmaf(0.5f * dt * (br_old.y + brk1.y), Gz.x, vzn.y);
-            if (k >= zc0 && k < zc1) out[F3_VZ * plane + k * g.rowz + cxy] = vzn;
+            if (own) out[F3_VZ * pl + k * rowz + cxy32] = vzn;
         }
         br_old = brk1;
         VZ[W - 1] = vzn;
@@ -309,54 +318,60 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
             const float2 *bBR = reinterpret_cast<const float2 *>(st + S::BR);
             const float2 *bPX = reinterpret_cast<const float2 *>(st + S::PX);
             const float2 *bPY = reinterpret_cast<const float2 *>(st + S::PY);
-            const long long rz = (long long)z * g.rowz;
-            // ---- vx on the x halo of the row: half nodes xh = x0 - M + jx
-            for (int i = t; i < TY * G::NXI; i += NTH) {
-                const int iy = i / G::NXI, jx = i - iy * G::NXI;
-                const int xh = x0 - M + jx, yy = y0 + iy;
-                float2 v = make_float2(0.f, 0.f);
-                if (xh >= 0 && xh < g.Nx && yy < g.Ny) {
-                    const float2 *pr = wP + (iy + G::YO2) * G::XW2 + (jx - M + G::XO2);
-                    float2 Gx = st2<M>(g.cx, [&](int l) { return pr[l]; }, [&](int l) { return pr[1 - l]; });
-                    const int cb = jx - M + G::XO1;   // xbox column of half node xh
-                    if (px && (xh <= g.x0 - 2 || xh >= g.x0 + g.nx)) {
-                        const float2 ps = fma2(a.pml.bh[2][xh], bPX[iy * G::XW1 + cb], mul2(a.pml.ah[2][xh], Gx));
-                        if (jx >= M && jx < M + TX) out[F3_PPX * plane + rz + (long long)yy * g.pitch + xh] = ps;
-                        Gx = add2(Gx, ps);
+            const int rz = z * rowz;
+            // ---- velocities on the halos of the row, one loop over both:
+            // items [0, NVX) are vx at half nodes xh = x0 - M + jx of row iy,
+            // the rest vy at half nodes yh = y0 - M + jy of column ix
+            constexpr int NVX = TY * G::NXI, NIT = NVX + G::YH1 * TX;
+            for (int i = t; i < NIT; i += NTH) {
+                if (i < NVX) {
+                    const int iy = i / G::NXI, jx = i - iy * G::NXI;
+                    const int xh = x0 - M + jx, yy = y0 + iy;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (xh >= 0 && xh < g.Nx && yy < g.Ny) {
+                        const float2 *pr = wP + (iy + G::YO2) * G::XW2 + (jx - M + G::XO2);
+                        float2 Gx = st2<M>(g.cx, [&](int l) { return pr[l]; }, [&](int l) { return pr[1 - l]; });
+                        const int cb = iy * G::XW1 + jx - M + G::XO1;   // xbox entry of half node xh
+                        const bool own = jx >= M && jx < M + TX;
+                        const int o = rz + yy * pitch + xh;
+                        if (px && (xh <= g.x0 - 2 || xh >= g.x0 + g.nx)) {
+                            const float2 ps = fma2(a.pml.bh[2][xh], bPX[cb], mul2(a.pml.ah[2][xh], Gx));
+                            if (own) out[F3_PPX * pl + o] = ps;
+                            Gx = add2(Gx, ps);
+                        }
+                        const float2 *brr = bBR + M * G::XW1 + cb;
+                        const float2 b0 = brr[0];
+                        const float2 b1 = xh + 1 >= g.Nx ? make_float2(b0.x, 0.f) : brr[1];
+                        v = fma2(-dt * 0.5f * (b0.x + b1.x), Gx, bVX[cb]);
+                        v.y = fmaf(0.5f * dt * (b0.y + b1.y), Gx.x, v.y);
+                        if (own) out[F3_VX * pl + o] = v;
                     }
-                    const float2 *brr = bBR + (iy + M) * G::XW1 + cb;
-                    const float2 b0 = brr[0];
-                    const bool last = xh + 1 >= g.Nx;
-                    const float2 b1 = last ? make_float2(b0.x, 0.f) : brr[1];
-                    v = fma2(-dt * 0.5f * (b0.x + b1.x), Gx, bVX[iy * G::XW1 + cb]);
-                    v.y = fmaf(0.5f * dt * (b0.y + b1.y), Gx.x, v.y);
-                    if (jx >= M && jx < M + TX) out[F3_VX * plane + rz + (long long)yy * g.pitch + xh] = v;
-                }
-                oVX[iy * G::XW1 + jx] = v;
-            }
-            // ---- vy on the y halo of the row: half nodes yh = y0 - M + jy
-            for (int i = t; i < G::YH1 * TX; i += NTH) {
-                const int jy = i / TX, ix = i - jy * TX;
-                const int yh = y0 - M + jy, xx = x0 + ix;
-                float2 v = make_float2(0.f, 0.f);
-                if (yh >= 0 && yh < g.Ny && xx < g.Nx) {
-                    const float2 *pc = wP + (jy + M - 1) * G::XW2 + (ix + G::XO2);
-                    float2 Gy = st2<M>(g.cy, [&](int l) { return pc[l * G::XW2]; },
-                                       [&](int l) { return pc[(1 - l) * G::XW2]; });
-                    if (py && (yh <= g.y0 - 2 || yh >= g.y0 + g.ny)) {
-                        const float2 ps = fma2(a.pml.bh[1][yh], bPY[jy * TX + ix], mul2(a.pml.ah[1][yh], Gy));
-                        if (jy >= M && jy < M + TY) out[F3_PPY * plane + rz + (long long)yh * g.pitch + xx] = ps;
-                        Gy = add2(Gy, ps);
+                    oVX[iy * G::XW1 + jx] = v;
+                } else {
+                    const int i2 = i - NVX;
+                    const int jy = i2 / TX, ix = i2 - jy * TX;
+                    const int yh = y0 - M + jy, xx = x0 + ix;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (yh >= 0 && yh < g.Ny && xx < g.Nx) {
+                        const float2 *pc = wP + (jy + M - 1) * G::XW2 + (ix + G::XO2);
+                        float2 Gy = st2<M>(g.cy, [&](int l) { return pc[l * G::XW2]; },
+                                           [&](int l) { return pc[(1 - l) * G::XW2]; });
+                        const bool own = jy >= M && jy < M + TY;
+                        const int o = rz + yh * pitch + xx;
+                        if (py && (yh <= g.y0 - 2 || yh >= g.y0 + g.ny)) {
+                            const float2 ps = fma2(a.pml.bh[1][yh], bPY[i2], mul2(a.pml.ah[1][yh], Gy));
+                            if (own) out[F3_PPY * pl + o] = ps;
+                            Gy = add2(Gy, ps);
+                        }
+                        const float2 *brc = bBR + jy * G::XW1 + ix + G::XO1;
+                        const float2 b0 = brc[0];
+                        const float2 b1 = yh + 1 >= g.Ny ? make_float2(b0.x, 0.f) : brc[G::XW1];
+                        v = fma2(-dt * 0.5f * (b0.x + b1.x), Gy, bVY[i2]);
+                        v.y = fmaf(0.5f * dt * (b0.y + b1.y), Gy.x, v.y);
+                        if (own) out[F3_VY * pl + o] = v;
                     }
-                    const float2 *brc = bBR + jy * G::XW1 + ix + G::XO1;
-                    const float2 b0 = brc[0];
-                    const bool last = yh + 1 >= g.Ny;
-                    const float2 b1 = last ? make_float2(b0.x, 0.f) : brc[G::XW1];
-                    v = fma2(-dt * 0.5f * (b0.x + b1.x), Gy, bVY[jy * TX + ix]);
-                    v.y = fmaf(0.5f * dt * (b0.y + b1.y), Gy.x, v.y);
-                    if (jy >= M && jy < M + TY) out[F3_VY * plane + rz + (long long)yh * g.pitch + xx] = v;
+                    oVY[i2] = v;
                 }
-                oVY[jy * TX + ix] = v;
             }
             __syncthreads();
             // ---- pressure at row z on the thread's own column
@@ -366,21 +381,21 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
                 float2 Qx = st2<M>(g.cx, [&](int l) { return vxr[l - 1]; }, [&](int l) { return vxr[-l]; });
                 float2 Qy = st2<M>(g.cy, [&](int l) { return vyc[(l - 1) * TX]; }, [&](int l) { return vyc[-l * TX]; });
                 float2 Qz = st2<M>(g.cz, [&](int l) { return VZ[M + l - 1]; }, [&](int l) { return VZ[M - l]; });
-                const long long c = rz + cxy;
+                const int c = rz + cxy32;
                 if (x <= g.x0 - 1 || x >= g.x0 + g.nx) {
-                    float2 *m = psv + 0 * plane + c;
+                    float2 *m = psv + c;
                     const float2 ps = fma2(a.pml.bi[2][x], *m, mul2(a.pml.ai[2][x], Qx));
                     *m = ps;
                     Qx = add2(Qx, ps);
                 }
                 if (y <= g.y0 - 1 || y >= g.y0 + g.ny) {
-                    float2 *m = psv + 1 * plane + c;
+                    float2 *m = psv + pl + c;
                     const float2 ps = fma2(a.pml.bi[1][y], *m, mul2(a.pml.ai[1][y], Qy));
                     *m = ps;
                     Qy = add2(Qy, ps);
                 }
                 if (z <= g.z0 - 1 || z >= g.z0 + g.nz) {
-                    float2 *m = psv + 2 * plane + c;
+                    float2 *m = psv + 2 * pl + c;
                     const float2 ps = fma2(a.pml.bi[0][z], *m, mul2(a.pml.ai[0][z], Qz));
                     *m = ps;
                     Qz = add2(Qz, ps);
@@ -391,10 +406,9 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
                 float2 pn = fma2(-kd.x, Q, p0);
                 pn.y = fmaf(-kd.y, Q.x, pn.y);
                 if (c == src) pn.x += wsrc;
-                out[F3_P * plane + c] = pn;
+                out[F3_P * pl + c] = pn;
             }
         }
-        __syncthreads();   // stage j % PD and the vx / vy tiles are free again
 #pragma unroll
         for (int m = 0; m < W - 1; ++m) {
             P[m] = P[m + 1];
@@ -419,7 +433,7 @@ __global__ void __launch_bounds__(NTH, 1) k3f_born(const __grid_constant__ Step3
     const int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
     for (int i = b + t; i < e; i += NTH) {
         const int2 rc = a.trec.rec[i];
-        a.dstage[(long long)rc.y * g.nt + a.n] = out[F3_P * plane + rc.x].y;
+        a.dstage[(long long)rc.y * g.nt + a.n] = out[F3_P * plane + rc.x].y;   // (all rows written: barrier above)
     }
 }
 

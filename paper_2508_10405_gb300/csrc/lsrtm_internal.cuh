@@ -158,7 +158,7 @@ struct Step3D {
 
 // Fused 3D time-step kernels (kernels3d_fused.cu): CTAs of kTile3X x kTile3Y
 // (x, y) columns marching a z-chunk of tzc rows, ping-pong state buffers.
-constexpr int kTile3X = 32, kTile3Y = 16;
+constexpr int kTile3X = 32, kTile3Y = 12;
 // Pair-plane offsets within a slot. Born ping-pong: (p, dp), (vx, dvx),
 // (vy, dvy), (vz, dvz), (psi_p, dpsi_p) x y z; the node CPML memories
 // (psi_v, dpsi_v) x y z live in a separate in-place block.
