@@ -103,6 +103,7 @@ struct lsrtm_handle {
     long long sstride = 0;
     long long sstride1 = 0;      // slot stride of st[1] (3D: the fused kernels' pong buffer)
     Step3F f3born[2];            // fused 3D Born step arguments reading st[0] / st[1]
+    Adj3F f3adj[2];              // fused 3D adjoint step arguments reading st[0] / st[1]
     int *kerr = nullptr;         // device error word of the fused kernels
     float *psiv = nullptr;
     long long vstride = 0;
@@ -380,7 +381,7 @@ long long loop_launches(const lsrtm_handle *h, int kind)
 {
     const long long nt = h->g.nt;
     const long long pack = (kind == G_BG || kind == G_BG_HESS) && h->bands.fmt != BAND_F32 ? nt : 0;
-    if (h->g.ndim != 3 || kind == G_BORN) return nt + pack;   // 2D and the fused 3D Born: one launch per step
+    if (h->g.ndim != 3 || kind == G_BORN || kind == G_ADJ) return nt + pack;   // 2D, fused 3D Born and adjoint
     return (kind == G_ADJ ? 2 * nt - 1 : 2 * nt) + pack;
 }
 
@@ -466,6 +467,9 @@ lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs,
 }
 
 int batch_size(const lsrtm_handle *h, int shot0) { return std::min(h->batch, h->nshot - shot0); }
+
+lsrtm_status adj3f_step(lsrtm_handle *h, int i, int n, int s0, const Bands &bands);
+lsrtm_status adj3f_start(lsrtm_handle *h, int fs0, int s0, int bs);
 
 lsrtm_status zero_slots(lsrtm_handle *h, int bs)
 {
@@ -770,15 +774,9 @@ lsrtm_status ck_reverse(lsrtm_handle *h, int s0, int bs, int j)
     sb.shot0 = s0;
     sb.t0 = t0;
     const bool d3 = is3d(h);
-    return run_loop_n(h, G_SEG + 2 * j + 1, 2, s0, bs, d3 ? 2 * r - (lo == 0 ? 1 : 0) : r, r,
-                      [&]() -> lsrtm_status {
+    return run_loop_n(h, G_SEG + 2 * j + 1, 2, s0, bs, r, r, [&]() -> lsrtm_status {
         if (d3) {
-            Step3D a = step3_args(h, s0);
-            a.bands = sb;
-            for (int n = hi; n >= lo; --n) {
-                a.n = n;
-                CU(launch_adj3d(a, bs, h->work));
-            }
+            for (int n = hi; n >= lo; --n) CHECK(adj3f_step(h, nt - 1 - n, n, s0, sb));
             return LSRTM_OK;
         }
         Step2D a = step_args(h, s0);
@@ -818,14 +816,13 @@ lsrtm_status adjoint_core_ckpt(lsrtm_handle *h, float *gout, bool want_hess)
         CHECK(zero_slots(h, bs));
         if (h->img) CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
         if (is3d(h)) {
-            CU(launch_pack_adjoint3d(h->g, h->final_state, 0, bs, h->st[0], h->sstride, h->work));
-            CU(launch_adj3d_init(step3_args(h, s0), bs, h->work));
+            CHECK(adj3f_start(h, 0, s0, bs));
         } else {
             CU(launch_pack_adjoint(h->g, h->final_state, 0, bs, h->st[0], h->sstride, h->work));
             CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, nt - 1,
                                       reinterpret_cast<float2 *>(h->st[0]), h->sstride / 2, h->work));
+            h->launches += 2;
         }
-        h->launches += 2;
         for (int j = h->ck_nseg - 1; j >= 0; --j) {
             int t0, hi, lo;
             seg_range(h, j, &t0, &hi, &lo);
@@ -833,10 +830,7 @@ lsrtm_status adjoint_core_ckpt(lsrtm_handle *h, float *gout, bool want_hess)
             CHECK(ck_recompute(h, s0, bs, j));
             CHECK(ck_reverse(h, s0, bs, j));
         }
-        if (is3d(h))
-            CU(launch_image_accumulate3d(h->g, h->st[0], h->sstride, bs, h->img_acc, h->work));
-        else
-            CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, nullptr, nullptr, h->img_acc, h->work));
+        CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, nullptr, nullptr, h->img_acc, h->work));
         h->launches++;
     }
     if (hess) {
@@ -864,19 +858,12 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
         CHECK(zero_slots(h, bs));
         if (h->img) CU(cudaMemsetAsync(h->img, 0, (size_t)bs * plane * sizeof(float2), h->work));
         if (is3d(h)) {
-            CU(launch_pack_adjoint3d(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
-            Step3D a0 = step3_args(h, s0);
-            CU(launch_adj3d_init(a0, bs, h->work));
-            h->launches += 2;
+            CHECK(adj3f_start(h, s0, s0, bs));
             CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
-                Step3D a = step3_args(h, s0);
-                for (int i = 0; i < nt; ++i) {
-                    a.n = nt - 1 - i;
-                    CU(launch_adj3d(a, bs, h->work));
-                }
+                for (int i = 0; i < nt; ++i) CHECK(adj3f_step(h, i, nt - 1 - i, s0, h->bands));
                 return LSRTM_OK;
             }));
-            CU(launch_image_accumulate3d(h->g, h->st[0], h->sstride, bs, h->img_acc, h->work));
+            CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, nullptr, nullptr, h->img_acc, h->work));
             h->launches++;
         } else {
             CU(launch_pack_adjoint(h->g, h->final_state, s0, bs, h->st[0], h->sstride, h->work));
@@ -1147,7 +1134,52 @@ lsrtm_status setup_fused3d(lsrtm_handle *h)
         a.err = h->kerr;
         cudaError_t e = fused3d_born_maps(a, h->kd2, h->br2, h->batch);
         if (e != cudaSuccess) return fail(LSRTM_ERR_CUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
+        Adj3F &d = h->f3adj[b];
+        d = Adj3F{};
+        d.g = h->g;
+        d.pml = h->pml;
+        d.in = h->st[b];
+        d.out = h->st[1 - b];
+        d.in_planes = (int)((b ? h->sstride1 : h->sstride) / h->g.plane);
+        d.out_planes = (int)((b ? h->sstride : h->sstride1) / h->g.plane);
+        d.kdt = h->kdt;
+        d.binv = h->binv;
+        d.img = h->img;
+        d.tzc = h->tzc;
+        d.wav = h->wav;
+        d.wav_per_shot = h->cfg.wavelet_per_shot;
+        d.src_cell = h->src_cell;
+        d.src_scale = h->src_scale;
+        d.dstage = h->dstage;
+        d.err = h->kerr;
+        e = fused3d_adj_maps(d, h->kdt, h->binv, h->batch);
+        if (e != cudaSuccess) return fail(LSRTM_ERR_CUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
     }
+    return LSRTM_OK;
+}
+
+// One fused 3D adjoint step n of a batch; i = nt - 1 - n selects the input buffer.
+lsrtm_status adj3f_step(lsrtm_handle *h, int i, int n, int s0, const Bands &bands)
+{
+    Adj3F &a = h->f3adj[i & 1];
+    a.n = n;
+    a.shot0 = s0;
+    a.bands = bands;
+    a.trec = h->trv;
+    a.tzc = h->tzc;
+    CU(launch_adj3f(a, batch_size(h, s0), h->work));
+    return LSRTM_OK;
+}
+
+// Start of a fused 3D reverse pass: (p, 0), (v, 0) from the saved final
+// states (fs0: index of the batch's first shot in the final-state store) and
+// the residual of step nt-1 added to lambda_p.
+lsrtm_status adj3f_start(lsrtm_handle *h, int fs0, int s0, int bs)
+{
+    CU(launch_pack3f(h->g, h->final_state, fs0, bs, h->st[0], h->sstride, h->work));
+    CU(launch_inject_residual(h->g, h->trv, bs, s0, h->dstage, h->g.nt - 1, reinterpret_cast<float2 *>(h->st[0]),
+                              h->sstride / 2, h->work));
+    h->launches += 2;
     return LSRTM_OK;
 }
 
@@ -1249,8 +1281,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
             return fail(LSRTM_ERR_CFL, buf);
         }
     }
-    CHECK(dalloc_t(h, &h->kdt, g.plane));
-    CHECK(dalloc_t(h, &h->binv, g.plane));
+    CHECK(dalloc_t(h, &h->kdt, 2 * g.plane));   // (kdt, binv) adjacent: one tensor map covers both
+    h->binv = h->kdt + g.plane;
     CHECK(dalloc_t(h, &h->kd2, 2 * g.plane));   // (kd2, br2) adjacent: one tensor map covers both
     h->br2 = h->kd2 + g.plane;
     CU(launch_model_prep(g, vp_d, rho_d, h->kdt, h->binv, h->work));

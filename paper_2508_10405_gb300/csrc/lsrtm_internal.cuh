@@ -185,6 +185,43 @@ struct Step3F {
     float *dstage;            // records [nrec_total][nt]
     int *err;                 // error word: 1 = a wait gave up, 2 = a misaligned copy was refused
 };
+// Fused 3D adjoint layout (float planes of a slot): pairs (p, lambda_p) 0-1,
+// (vx, lambda_vx) 2-3, (vy, lambda_vy) 4-5, (vz, lambda_vz) 6-7, then the
+// lambda CPML memories psi_p x y z (8-10) and psi_v x y z (11-13).
+enum { A3F_PL = 0, A3F_VX = 2, A3F_VY = 4, A3F_VZ = 6, A3F_LPPX = 8, A3F_LPPY = 9, A3F_LPPZ = 10,
+       A3F_LPVX = 11, A3F_LPVY = 12, A3F_LPVZ = 13 };
+constexpr int kAdjPlanes3F = 14;
+
+struct Adj3F {
+    // input-state pair planes (core, wide, xbox, ybox), input-state float
+    // planes (core, xwide, ywide, xbox, ybox), model float planes (plane 0
+    // dt kappa, plane 1 1/rho: core, wide, ybr)
+    CUtensorMap p_core, p_wide, p_xbox, p_ybox;
+    CUtensorMap f_core, f_xwide, f_ywide, f_xbox, f_ybox;
+    CUtensorMap m_core, m_wide, m_ybr;
+    GridDev g;
+    Pml pml;
+    const float *in;          // input state, slot stride in_planes float planes
+    float *out;               // output state, slot stride out_planes
+    int in_planes, out_planes;
+    const float *kdt, *binv;  // for the first rows of a march
+    float2 *img;              // [batch][plane] image accumulators (in place)
+    int n, tzc, shot0;
+    const float *wav;
+    int wav_per_shot;
+    const int *src_cell;
+    float src_scale;
+    Bands bands;
+    TileRecs trec;
+    const float *dstage;      // residual [nrec_total][nt]
+    int *err;
+};
+cudaError_t fused3d_adj_maps(Adj3F &a, const float *kdt, const float *binv, int batch);
+cudaError_t launch_adj3f(const Adj3F &a, int batch, cudaStream_t s);
+// (p, 0), (vx, 0), (vy, 0), (vz, 0) into the fused layout from final states
+// [p][vz][vy][vx] (shot index fs0 + slot).
+cudaError_t launch_pack3f(const GridDev &g, const float *final_state, int fs0, int batch, float *st,
+                          long long sstride, cudaStream_t s);
 cudaError_t make_tmap3(CUtensorMap *m, const void *base, const GridDev &g, int esz, long long nq, int bx, int by);
 cudaError_t fused3d_born_maps(Step3F &a, const float2 *kd2, const float2 *br2, int batch);
 size_t fused3d_born_smem(int M);
