@@ -332,8 +332,6 @@ Step3D step3_args(lsrtm_handle *h, int shot0)
     a.pml = h->pml;
     a.kdt = h->kdt;
     a.binv = h->binv;
-    a.kd2 = h->kd2;
-    a.br2 = h->br2;
     a.st = h->st[0];
     a.sstride = h->sstride;
     a.shot0 = shot0;
@@ -500,14 +498,14 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                 for (int n = 0; n < nt; ++n) {
                     a.n = n;
                     if (n + 1 < nt) {
-                        CU(launch_fwd3d(a, bs, false, true, hess, 3, h->work));
+                        CU(launch_fwd3d(a, bs, true, hess, 3, h->work));
                     } else {
-                        CU(launch_fwd3d(a, bs, false, true, hess, 1, h->work));
+                        CU(launch_fwd3d(a, bs, true, hess, 1, h->work));
                         for (int s = 0; s < bs; ++s)
                             CU(cudaMemcpyAsync(h->final_state + (size_t)(s0 + s) * 4 * plane,
                                                h->st[0] + s * h->sstride, plane * sizeof(float),
                                                cudaMemcpyDeviceToDevice, h->work));
-                        CU(launch_fwd3d(a, bs, false, true, hess, 2, h->work));
+                        CU(launch_fwd3d(a, bs, true, hess, 2, h->work));
                     }
                     if (h->bands.fmt != BAND_F32) CU(launch_band_pack(h->bands, bs, s0, n, h->work));
                 }
@@ -604,7 +602,7 @@ lsrtm_status model_core(lsrtm_handle *h)
                 a.rec_bg = 1;
                 for (int n = 0; n < nt; ++n) {
                     a.n = n;
-                    CU(launch_fwd3d(a, bs, false, false, false, 3, h->work));
+                    CU(launch_fwd3d(a, bs, false, false, 3, h->work));
                 }
                 return LSRTM_OK;
             }
@@ -667,13 +665,13 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
                 a.n = n;
                 if (n % K == 0) CHECK(ck_copy(h, n / K, h->st[0], h->sstride, 10, 0, bs, true));
                 if (n + 1 < nt) {
-                    CU(launch_fwd3d(a, bs, false, false, hess, 3, h->work));
+                    CU(launch_fwd3d(a, bs, false, hess, 3, h->work));
                     continue;
                 }
-                CU(launch_fwd3d(a, bs, false, false, hess, 1, h->work));
+                CU(launch_fwd3d(a, bs, false, hess, 1, h->work));
                 CU(cudaMemcpy2DAsync(h->final_state, 4 * plane * sizeof(float), h->st[0], h->sstride * sizeof(float),
                                      plane * sizeof(float), bs, cudaMemcpyDeviceToDevice, h->work));
-                CU(launch_fwd3d(a, bs, false, false, hess, 2, h->work));
+                CU(launch_fwd3d(a, bs, false, hess, 2, h->work));
             }
             return LSRTM_OK;
         }));
@@ -740,7 +738,7 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
             a.bands = sb;
             for (int n = t0; n < hi; ++n) {
                 a.n = n;
-                CU(launch_fwd3d(a, bs, false, true, false, 3, h->work));
+                CU(launch_fwd3d(a, bs, true, false, 3, h->work));
                 if (pack) CU(launch_band_pack(sb, bs, s0, n, h->work));
             }
             return LSRTM_OK;

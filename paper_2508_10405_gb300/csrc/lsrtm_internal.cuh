@@ -132,12 +132,11 @@ struct Step2D {
 // then dt kappa, 1/rho and the two Born pairs of the shot's window.
 constexpr int kWinStatePlanes2D = 16;
 
-// Arguments of the 3D time-step kernels (state updated in place).
+// Arguments of the 3D background time-step kernels (state updated in place).
 struct Step3D {
     GridDev g;
     Pml pml;
     const float *kdt, *binv;
-    const float2 *kd2, *br2;  // Born pairs, as in Step2D
     float *st;                // slot 0 of the batch; slot stride sstride floats
     long long sstride;
     int n;
@@ -148,8 +147,8 @@ struct Step3D {
     float src_scale;
     Bands bands;
     float *hess;              // [batch][plane]
-    float *dstage;            // records (forward) or residual (adjoint), [nrec_total][nt]
-    int rec_bg;               // forward: record the background p instead of dp (nonlinear modelling)
+    float *dstage;            // pressure records [nrec_total][nt] (nonlinear modelling)
+    int rec_bg;               // record the pressure p^{n+1}
     const int *rmap;          // [nshot][plane]: first entry of the node's receivers in rcell/rrow, or -1
     const int *rptr;          // [nshot+1] per-shot ranges of rcell/rrow
     const int *rcell;         // receiver cells, sorted by cell within a shot
@@ -227,15 +226,9 @@ cudaError_t fused3d_born_maps(Step3F &a, const float2 *kd2, const float2 *br2, i
 size_t fused3d_born_smem(int M);
 cudaError_t launch_born3f(const Step3F &a, int batch, cudaStream_t s);
 
-// 3D launchers (kernels3d.cu). stages: 1 = velocity stage, 2 = pressure stage, 3 = both.
-cudaError_t launch_fwd3d(const Step3D &a, int batch, bool born, bool bands, bool hess, int stages,
-                         cudaStream_t s);
-cudaError_t launch_adj3d_init(const Step3D &a, int batch, cudaStream_t s);
-cudaError_t launch_adj3d(const Step3D &a, int batch, cudaStream_t s);
-cudaError_t launch_pack_adjoint3d(const GridDev &g, const float *final_state, int shot0, int batch,
-                                  float *st, long long sstride, cudaStream_t s);
-cudaError_t launch_image_accumulate3d(const GridDev &g, const float *st, long long sstride, int batch,
-                                      double2 *acc, cudaStream_t s);
+// 3D background launchers (kernels3d.cu). stages: 1 = velocity stage, 2 =
+// pressure stage, 3 = both.
+cudaError_t launch_fwd3d(const Step3D &a, int batch, bool bands, bool hess, int stages, cudaStream_t s);
 
 // 2D kernels: CTAs of kThreads2D threads, one x-column per thread; a CTA owns
 // march2d_txo(M) output columns and a z-chunk of Step2D::tzc rows.
