@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", type=int, default=2, help="preset number (default 2)")
     ap.add_argument("--shots-per-batch", type=int, default=0)
-    ap.add_argument("--bands", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap.add_argument("--bands", choices=["fp32", "bf16", "fp16"], default="bf16",
+                    help="boundary-band precision of the batched (timed) plan")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -68,6 +69,9 @@ def parse():
     ap.add_argument("--plain-shots", type=int, default=4,
                     help="shots on which the plain per-shot FP32 plan is timed for the "
                          "per-iteration comparison (0: skip)")
+    ap.add_argument("--image-shots", type=int, default=2,
+                    help="shots on which the plain and the batched plans each run the workload's full "
+                         "CGNR (its iteration count) for the final-image distance (0: skip)")
     ap.add_argument("--psf-cg", action="store_true",
                     help="time the image-domain CGNR with the interpolated PSF Hessian (App. D) "
                          "on the marine-line image instead of the data-domain iteration")
@@ -156,15 +160,15 @@ class ClockSampler:
         return out
 
 
-def kernel_src_sha():
+def kernel_src_sha(ndim=2):
     h = hashlib.sha256()
-    for f in ("kernels2d.cu", "lsrtm_internal.cuh"):
+    for f in ("kernels2d.cu" if ndim == 2 else "kernels3d_fused.cu", "lsrtm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2508_10405_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, cells_per_launch):
+def ncu_traffic(kernel, cells_per_launch, ndim=2):
     """DRAM bytes per launch from the committed ncu summary of this kernel, if
     it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -172,7 +176,7 @@ def ncu_traffic(kernel, cells_per_launch):
         with open(path) as f:
             t = json.load(f)
         e = t[kernel]
-        if e.get("src_sha") != kernel_src_sha():
+        if e.get("src_sha") != kernel_src_sha(ndim):
             return None
         return float(e["dram_bytes_per_cell"]) * cells_per_launch
     except Exception:
@@ -713,44 +717,57 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def plain_compare(w, nshots, s_batched, bands, torch):
-    """Per-iteration time of the plain plan (one shot per launch, no graphs,
-    FP32 bands, background recomputed inside every L^T) timed on the first
-    `nshots` shots and scaled to all shots (the plain plan runs shots one
-    after another), against the batched plan's measured iteration; and the
-    relative L2 distance of the two plans' images after two CGNR iterations
-    on those shots (batched with the benchmark's band precision)."""
+def plain_compare(w, nshots, s_batched, bands, torch, image_shots):
+    """The plain plan (one shot per launch, no graphs, FP32 bands, background
+    recomputed inside every L^T) against the batched mixed-precision plan.
+    Per-iteration time: the plain plan timed on the first `nshots` shots
+    (fastest of two CGNR iterations, z-chunking autotuned like the batched
+    handle) and scaled to all shots by padded cells, against the batched
+    plan's measured iteration. Final-image distance: both plans run the
+    workload's full CGNR (w.cg_iters iterations) on the first `image_shots`
+    shots from the same observed data; the relative L2 distance of the two
+    final images."""
     from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
+    bp = {"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[bands]
     nshots = min(nshots, w.geom.nshot)
     sub = dataclasses.replace(w, geom=w.geom.subset(list(range(nshots))))
     hp = Lsrtm.from_workload(sub, plan=PLAN_PLAIN, band_precision=BAND_FP32)
-    hb = Lsrtm.from_workload(sub, plan=PLAN_BATCHED,
-                             band_precision={"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[bands])
+    tune = hp.autotune()
     dm = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
     d = hp.born(dm)
-    res = {}
-    for name, h in (("plain", hp), ("batched", hb)):
-        h.cg_begin(d)
+    hp.cg_begin(d)
+    times = []
+    for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h.cg_iterate(1)
+        hp.cg_iterate(1)
         torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        h.cg_iterate(1)
-        torch.cuda.synchronize()
-        res[name] = (min(t1 - t0, time.perf_counter() - t1), h.cg_result()[0])
+        times.append(time.perf_counter() - t0)
+    hp.close()
     frac = float(shot_cells(w)[:nshots].sum() / shot_cells(w).sum())
-    s_plain = res["plain"][0] / frac
-    xp, xb = res["plain"][1].double(), res["batched"][1].double()
+    s_plain = min(times) / frac
     out = {"s_per_iter_plain": s_plain, "s_per_iter_batched": s_batched,
            "speedup": s_plain / s_batched,
-           "image_rel_l2_after_2_iters": float(torch.linalg.norm(xb - xp) / torch.linalg.norm(xp)),
            "plain": "one shot per launch, no graph, FP32 bands, background recomputed in every L^T",
-           "batched_bands": bands,
+           "batched": f"all shots per launch, CUDA graphs, {bands} bands cached across iterations",
+           "plain_autotune_tzc": tune.get("tzc"),
            "sample": f"plain timed on {nshots} of {w.geom.nshot} shots (fastest of 2 iterations), "
                      f"scaled by padded cells"}
-    hp.close()
-    hb.close()
+    ni = max(1, int(w.cg_iters))
+    if image_shots > 0:
+        ns = min(image_shots, w.geom.nshot)
+        sub = dataclasses.replace(w, geom=w.geom.subset(list(range(ns))))
+        xs = {}
+        for name, plan, band in (("plain", PLAN_PLAIN, BAND_FP32), ("batched", PLAN_BATCHED, bp)):
+            h = Lsrtm.from_workload(sub, plan=plan, band_precision=band)
+            dd = d[: h.nrec_total] if ns <= nshots else h.born(dm)
+            x, mis = h.cg_solve(dd, ni)
+            xs[name] = (x.double(), mis)
+            h.close()
+        xp, xb = xs["plain"][0], xs["batched"][0]
+        out["final_image_rel_l2"] = float(torch.linalg.norm(xb - xp) / torch.linalg.norm(xp))
+        out["final_misfit"] = {"plain": float(xs["plain"][1][-1]), "batched": float(xs["batched"][1][-1])}
+        out["final_image"] = f"{ni} CGNR iterations on {ns} shot(s), same observed data"
     return out
 
 
@@ -835,13 +852,12 @@ def main():
     bpc = BYTES_PER_CELL[(dom, w.ndim)]
     achieved = bpc * cells_per_launch / avg_launch_s / 1e9
     peak, peak_kind = peaks()
-    # the committed DRAM counters are for the 2D kernels; 3D has none on the current source
-    traffic = ncu_traffic({"born": "k_fwd2d_born", "adjoint": "k_adj2d"}[dom], cells_per_launch) \
-        if w.ndim == 2 else None
+    traffic = ncu_traffic(({"born": "k_fwd2d_born", "adjoint": "k_adj2d"} if w.ndim == 2
+                           else {"born": "k3f_born", "adjoint": "k3f_adj"})[dom], cells_per_launch, w.ndim)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": ({"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"} if w.ndim == 2
-                           else {"born": "k3_v + k3_p <BORN>", "adjoint": "k3_a + k3_b"})[dom],
+                           else {"born": "k3f_born", "adjoint": "k3f_adj"})[dom],
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_cell": bpc, "cells_per_launch": cells_per_launch,
@@ -883,7 +899,7 @@ def main():
 
     plain = None
     if args.plain_shots > 0 and args.plan == "batched":
-        plain = plain_compare(w, args.plain_shots, t_max / K, args.bands, torch)
+        plain = plain_compare(w, args.plain_shots, t_max / K, args.bands, torch, args.image_shots)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

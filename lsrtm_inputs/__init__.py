@@ -92,6 +92,7 @@ class Workload:
     geom: Geometry
     cg_iters: int = 0
     notes: str = ""
+    free_surface: bool = False   # free surface on the first interior row
 
     @property
     def shape(self):

@@ -48,6 +48,7 @@ class Cfg(ctypes.Structure):
         ("npml", ctypes.c_int), ("order", ctypes.c_int), ("nt", ctypes.c_int),
         ("dz", ctypes.c_double), ("dy", ctypes.c_double), ("dx", ctypes.c_double),
         ("dt", ctypes.c_double), ("f0", ctypes.c_double), ("vmax", ctypes.c_double),
+        ("free_surface", ctypes.c_int),
     ]
 
 
@@ -118,7 +119,8 @@ def cfg_of(w, nt=None, vmax=None) -> Cfg:
     background velocity unless `vmax` is given."""
     return Cfg(w.ndim, w.nz, w.ny, w.nx, w.npml, w.order, int(w.nt if nt is None else nt),
                w.dz, w.dy, w.dx, w.dt, w.f0,
-               float(np.max(w.vp) if vmax is None else vmax))
+               float(np.max(w.vp) if vmax is None else vmax),
+               int(bool(getattr(w, "free_surface", False))))
 
 
 def _src_csr(geom):

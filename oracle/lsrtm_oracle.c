@@ -35,6 +35,13 @@
  *     alpha = pi f0 (1 - dist/L), kappa_pml = 1; dist is measured from the
  *     interface half node (interior edge - 1/2), so every interior node and
  *     every interface half node has no CPML memory.
+ *   - optional free surface on the first interior row z_s (method of images):
+ *     p = 0 on z_s; above it the rows are ghosts holding the odd mirror of p
+ *     (p(z_s - j) = -p(z_s + j)) and the even mirror of v_z (half row
+ *     z_s - 1 - j equals half row z_s + j), imposed after every pressure and
+ *     velocity update; no CPML on top; the model rows above z_s are the mirror
+ *     of those below it. L^T applies the transposes of these maps (the ghost
+ *     values folded onto their mirrors, then cleared).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -49,6 +56,7 @@
 typedef struct {
     int ndim, nz, ny, nx, npml, order, nt;
     double dz, dy, dx, dt, f0, vmax;
+    int free_surface;
 } orc_cfg;
 
 /* Direction index: 0 = z, 1 = y, 2 = x. */
@@ -65,6 +73,7 @@ typedef struct {
     double *ai[3], *bi[3], *ah[3], *bh[3];
     double *kap, *rho, *bu[3];
     double cellvol;
+    int fs;          /* free surface on row o[0] */
 } grid;
 
 /* ---------------------------------------------------------------- FD coeffs */
@@ -143,6 +152,7 @@ static int grid_init(grid *g, const orc_cfg *cfg, const double *vp, const double
     if (cfg->ndim == 2) { g->nd = 2; g->dirs[0] = 0; g->dirs[1] = 2; g->cellvol = cfg->dz * cfg->dx; }
     else { g->nd = 3; g->dirs[0] = 0; g->dirs[1] = 1; g->dirs[2] = 2; g->cellvol = cfg->dz * cfg->dy * cfg->dx; }
 
+    g->fs = cfg->free_surface != 0;
     g->kap = (double *)malloc(sizeof(double) * g->ncell);
     g->rho = (double *)malloc(sizeof(double) * g->ncell);
     if (!g->kap || !g->rho) return 2;
@@ -152,6 +162,7 @@ static int grid_init(grid *g, const orc_cfg *cfg, const double *vp, const double
         for (int y = 0; y < g->n[1]; ++y)
             for (int x = 0; x < g->n[2]; ++x) {
                 int iz = z - g->o[0], iy = y - g->o[1], ix = x - g->o[2];
+                if (iz < 0 && g->fs) iz = -iz;   /* mirror above the free surface */
                 if (iz < 0) iz = 0; if (iz >= g->ni[0]) iz = g->ni[0] - 1;
                 if (iy < 0) iy = 0; if (iy >= nyi) iy = nyi - 1;
                 if (ix < 0) ix = 0; if (ix >= g->ni[2]) ix = g->ni[2] - 1;
@@ -189,6 +200,7 @@ static int grid_init(grid *g, const orc_cfg *cfg, const double *vp, const double
         for (int i = 0; i < N; ++i) {
             double di = fmax(0.0, fmax((x0 - 0.5) - i, i - (x1 - 0.5)));
             double dh = fmax(0.0, fmax((x0 - 0.5) - (i + 0.5), (i + 0.5) - (x1 - 0.5)));
+            if (d == 0 && g->fs && i < x0) di = dh = 0.0;   /* no CPML above a free surface */
             cpml_coef(di, L, d0, alpha0, g->dt, &g->ai[d][i], &g->bi[d][i]);
             cpml_coef(dh, L, d0, alpha0, g->dt, &g->ah[d][i], &g->bh[d][i]);
         }
@@ -281,6 +293,60 @@ static void state_copy(const grid *g, state *dst, const state *src)
     }
 }
 
+/* ---------------------------------------------------- free surface maps */
+
+/* E_v: ghost half rows of v_z take the even mirror, v_z(z_s-1-j) = v_z(z_s+j). */
+static void fs_mirror_v(const grid *g, double *vz)
+{
+    if (!g->fs) return;
+    int zs = g->o[0];
+    for (int z = 0; z < zs; ++z) {
+        int zm = 2 * zs - 1 - z;
+        if (zm >= g->n[0]) { memset(vz + z * g->s[0], 0, sizeof(double) * g->s[0]); continue; }
+        memcpy(vz + z * g->s[0], vz + zm * g->s[0], sizeof(double) * g->s[0]);
+    }
+}
+
+/* E_p: p(z_s) = 0 and ghost rows the odd mirror, p(z_s-j) = -p(z_s+j). */
+static void fs_mirror_p(const grid *g, double *p)
+{
+    if (!g->fs) return;
+    int zs = g->o[0];
+    memset(p + zs * g->s[0], 0, sizeof(double) * g->s[0]);
+    for (int z = 0; z < zs; ++z) {
+        int zm = 2 * zs - z;
+        for (long c = 0; c < g->s[0]; ++c) p[z * g->s[0] + c] = (zm < g->n[0]) ? -p[zm * g->s[0] + c] : 0.0;
+    }
+}
+
+/* E_v^T: each ghost half row's adjoint added onto its mirror, then cleared. */
+static void fs_fold_v(const grid *g, double *lvz)
+{
+    if (!g->fs) return;
+    int zs = g->o[0];
+    for (int z = 0; z < zs; ++z) {
+        int zm = 2 * zs - 1 - z;
+        if (zm < g->n[0])
+            for (long c = 0; c < g->s[0]; ++c) lvz[zm * g->s[0] + c] += lvz[z * g->s[0] + c];
+        memset(lvz + z * g->s[0], 0, sizeof(double) * g->s[0]);
+    }
+}
+
+/* E_p^T: each ghost row's adjoint subtracted from its mirror, then the ghost
+ * rows and the surface row cleared. */
+static void fs_fold_p(const grid *g, double *lp)
+{
+    if (!g->fs) return;
+    int zs = g->o[0];
+    for (int z = 0; z < zs; ++z) {
+        int zm = 2 * zs - z;
+        if (zm < g->n[0])
+            for (long c = 0; c < g->s[0]; ++c) lp[zm * g->s[0] + c] -= lp[z * g->s[0] + c];
+        memset(lp + z * g->s[0], 0, sizeof(double) * g->s[0]);
+    }
+    memset(lp + zs * g->s[0], 0, sizeof(double) * g->s[0]);
+}
+
 /* One time step of Eq. (1) without the source: v^{n+1/2} from p^n, then
  * p^{n+1} from v^{n+1/2}, each with its CPML memory. Optionally returns the
  * terms the Born sources multiply: G[d] = D+_d p^n + psi_p (half nodes) and
@@ -299,6 +365,7 @@ static void fwd_step(const grid *g, state *st, double **G, double *Q)
             st->v[d][c] -= g->dt * g->bu[d][c] * gg;
         }
     }
+    fs_mirror_v(g, st->v[0]);
     FOR_CELLS(g) {
         long c = CELL(g);
         double qq = 0.0;
@@ -331,6 +398,7 @@ static void born_step(const grid *g, state *ds, double *const *G, const double *
             ds->v[d][c] -= g->dt * (g->bu[d][c] * (dp + ds->psip[d][c]) + dbu[d][c] * G[d][c]);
         }
     }
+    fs_mirror_v(g, ds->v[0]);
     FOR_CELLS(g) {
         long c = CELL(g);
         double qq = 0.0;
@@ -343,6 +411,7 @@ static void born_step(const grid *g, state *ds, double *const *G, const double *
         }
         ds->p[c] -= g->dt * (g->kap[c] * qq + dkap[c] * Q[c]);
     }
+    fs_mirror_p(g, ds->p);
 }
 
 /* Transpose of born_step (sub-steps reversed, each transposed), accumulating
@@ -357,6 +426,8 @@ static void adj_step(const grid *g, state *ls, double *const *G, const double *Q
                      double *gk, double *gr, double *t1, double *t2)
 {
     double dt = g->dt;
+    /* E_p^T (the Born step ends with E_p) */
+    fs_fold_p(g, ls->p);
     /* S4^T */
     FOR_CELLS(g) {
         long c = CELL(g);
@@ -386,6 +457,8 @@ static void adj_step(const grid *g, state *ls, double *const *G, const double *Q
             ls->psiv[d][c] *= g->bi[d][i];
         }
     }
+    /* E_v^T (E_v follows the velocity update S2) */
+    fs_fold_v(g, ls->v[0]);
     /* S2^T then S1^T, per direction */
     for (int q = 0; q < g->nd; ++q) {
         int d = g->dirs[q];
@@ -471,6 +544,7 @@ int orc_model(const orc_cfg *cfg, const double *vp, const double *rho, const dou
         for (int n = 0; n < nt; ++n) {
             fwd_step(&g, &st, NULL, NULL);
             inject(&g, st.p, s, n, src_ptr, src_idx, wav, nt, wav_per_shot);
+            fs_mirror_p(&g, st.p);
             for (int k = rec_ptr[s]; k < rec_ptr[s + 1]; ++k)
                 d[(long)k * nt + n] = st.p[pad_index(&g, rec_idx[k])];
         }
@@ -492,6 +566,7 @@ int orc_snapshot(const orc_cfg *cfg, const double *vp, const double *rho, const 
     for (int n = 0; n < nsnap; ++n) {
         fwd_step(&g, &st, NULL, NULL);
         inject(&g, st.p, 0, n, src_ptr, src_idx, wav, cfg->nt, 0);
+        fs_mirror_p(&g, st.p);
     }
     memcpy(p_out, st.p, sizeof(double) * g.ncell);
     state_free(&st);
@@ -554,6 +629,7 @@ int orc_born(const orc_cfg *cfg, const double *vp, const double *rho, const doub
             for (int n = 0; n < nt; ++n) {
                 fwd_step(&g, &st, G, Q);
                 inject(&g, st.p, s, n, src_ptr, src_idx, wav, nt, wav_per_shot);
+                fs_mirror_p(&g, st.p);
                 born_step(&g, &ds, G, Q, dbu, dkap);
                 for (int k = rec_ptr[s]; k < rec_ptr[s + 1]; ++k)
                     d[(long)k * nt + n] = ds.p[pad_index(&g, rec_idx[k])];
@@ -612,6 +688,7 @@ int orc_adjoint(const orc_cfg *cfg, const double *vp, const double *rho, const d
                 if (n % K == 0) state_copy(&g, &ck[n / K], &st);
                 fwd_step(&g, &st, NULL, NULL);
                 inject(&g, st.p, s, n, src_ptr, src_idx, wav, nt, wav_per_shot);
+                fs_mirror_p(&g, st.p);
             }
             /* reverse pass */
             for (int j = nseg - 1; j >= 0; --j) {
@@ -623,6 +700,7 @@ int orc_adjoint(const orc_cfg *cfg, const double *vp, const double *rho, const d
                         G[g.dirs[q]] = Gs + ((size_t)(n - n0) * 3 + g.dirs[q]) * nc;
                     fwd_step(&g, &st, G, Qs + (size_t)(n - n0) * nc);
                     inject(&g, st.p, s, n, src_ptr, src_idx, wav, nt, wav_per_shot);
+                    fs_mirror_p(&g, st.p);
                 }
                 for (int n = n1 - 1; n >= n0; --n) {
                     double *G[3] = {0, 0, 0};
@@ -693,6 +771,7 @@ int orc_pseudo_hessian(const orc_cfg *cfg, const double *vp, const double *rho,
             for (int n = 0; n < nt; ++n) {
                 fwd_step(&g, &st, G, Q);
                 inject(&g, st.p, s, n, src_ptr, src_idx, wav, nt, wav_per_shot);
+                fs_mirror_p(&g, st.p);
                 FOR_CELLS(&g) {
                     long c = CELL(&g);
                     double hr = 0.0;
