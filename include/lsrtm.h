@@ -84,6 +84,12 @@ typedef struct {
     int wavelet_per_shot;    /* 0: wavelet [nt] shared; 1: wavelet [nshot][nt] */
     int checkpoint_interval; /* steps K between checkpoints in checkpoint mode;
                                 0 = automatic (minimises checkpoint + segment-band memory) */
+    int free_surface;        /* 1: free surface (p = 0) on the first interior row z = 0,
+                                by the method of images: above it the pad holds the odd
+                                mirror of p, the even mirror of v_z and the mirror of the
+                                model, and has no CPML (a reading for the surface
+                                acquisitions of Sec. 4-5); sources may not sit on that row,
+                                receivers there record zero. 0: CPML on every side. */
 } lsrtm_config;
 
 typedef struct {

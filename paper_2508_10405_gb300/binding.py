@@ -49,6 +49,7 @@ class Config(ctypes.Structure):
         ("band_precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
         ("recon_mode", ctypes.c_int), ("plan", ctypes.c_int), ("shots_per_batch", ctypes.c_int),
         ("wavelet_per_shot", ctypes.c_int), ("checkpoint_interval", ctypes.c_int),
+        ("free_surface", ctypes.c_int),
     ]
 
 
@@ -163,7 +164,8 @@ class Lsrtm:
     def __init__(self, *, ndim, nz, nx, ny=1, dz, dx, dy=None, dt, nt, fd_order, npml, f0,
                  vp, rho, wavelet, src_idx, rec_ptr, rec_idx, win_x0=None, win_nx=None, pml_vmax=None,
                  band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_AUTO,
-                 plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, stream=None):
+                 plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, free_surface=False,
+                 stream=None):
         import torch
         self._lib = load_library()
         self._h = ctypes.c_void_p()
@@ -175,7 +177,7 @@ class Lsrtm:
         self.cfg = Config(ndim, nz, ny if ndim == 3 else 1, nx, dz, dy or dx, dx, dt, nt,
                           fd_order, npml, f0, float(pml_vmax), band_precision,
                           int(hbm_budget_bytes), recon_mode, plan, shots_per_batch,
-                          1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval))
+                          1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval), int(bool(free_surface)))
         self._src = np.ascontiguousarray(src_idx, dtype=np.int32)
         self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
         self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)
@@ -212,7 +214,8 @@ class Lsrtm:
                    nt=w.nt, fd_order=w.order, npml=w.npml, f0=w.f0, vp=w.vp, rho=w.rho,
                    wavelet=w.wavelet, src_idx=w.geom.src_idx, rec_ptr=w.geom.rec_ptr,
                    rec_idx=w.geom.rec_idx, win_x0=getattr(w.geom, "win_x0", None),
-                   win_nx=getattr(w.geom, "win_nx", None), **kw)
+                   win_nx=getattr(w.geom, "win_nx", None),
+                   **({"free_surface": getattr(w, "free_surface", False)} | kw))
 
     @property
     def model_shape(self) -> tuple:

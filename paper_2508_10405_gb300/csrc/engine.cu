@@ -927,6 +927,9 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
         return fail(LSRTM_ERR_ARG, "unknown plan");
     if (c->shots_per_batch < 0) return fail(LSRTM_ERR_ARG, "shots_per_batch < 0");
     if (c->checkpoint_interval < 0) return fail(LSRTM_ERR_ARG, "checkpoint_interval < 0");
+    if (c->free_surface != 0 && c->free_surface != 1) return fail(LSRTM_ERR_ARG, "free_surface must be 0 or 1");
+    if (c->free_surface && c->nz < c->fd_order)
+        return fail(LSRTM_ERR_ARG, "a free surface needs nz >= fd_order (its mirror rows)");
     return LSRTM_OK;
 }
 
@@ -1009,6 +1012,8 @@ lsrtm_status build_geometry(lsrtm_handle *h, const lsrtm_geometry *geo)
         if (k < 0 || k >= h->nint) return fail(LSRTM_ERR_GEOMETRY, "source outside the interior grid");
         long long c = pad_cell(k, s);
         if (c < 0) return fail(LSRTM_ERR_GEOMETRY, "source outside its shot's aperture window");
+        if (g.fs && k / ((long long)gm.nx * gm.ny) == 0)
+            return fail(LSRTM_ERR_GEOMETRY, "a source on the free-surface row radiates nothing (p = 0 there)");
         src[s] = (int)c;
     }
     if (g.ndim == 3) {
@@ -1228,6 +1233,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     g.plane = (long long)g.Nz * g.rowz;
     g.dt = (float)cfg->dt;
     g.nt = cfg->nt;
+    g.fs = cfg->free_surface ? 1 : 0;
     double c[4];
     fd_coeffs(g.M, c);
     for (int l = 0; l < kMaxM; ++l) {
@@ -1303,6 +1309,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
             if (!(d == 1 && g.ndim == 2))
                 cpml_profile(N[d], o[d], ni[d], cfg->npml, hh[d], vmax, cfg->f0, cfg->dt, b, b + N[d],
                              b + 2 * N[d], b + 3 * N[d]);
+            if (d == 0 && g.fs)   // no CPML above a free surface (nodes and half nodes above row z0)
+                for (int i = 0; i < o[0]; ++i) b[i] = b[N[d] + i] = b[2 * N[d] + i] = b[3 * N[d] + i] = 0.f;
             h->pml.ai[d] = h->pml_buf + off;
             h->pml.bi[d] = h->pml_buf + off + N[d];
             h->pml.ah[d] = h->pml_buf + off + 2 * N[d];

@@ -66,6 +66,14 @@ template <> __device__ __forceinline__ float zero_<float>() { return 0.f; }
 template <> __device__ __forceinline__ float2 zero_<float2>() { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ float sub_(float a, float b) { return a - b; }
 __device__ __forceinline__ float2 sub_(float2 a, float2 b) { return __ffma2_rn(f2(-1.f), b, a); }
+__device__ __forceinline__ float neg_(float a) { return -a; }
+__device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Free surface (method of images about row z0): a ghost node row r < z0
+// reads its mirror row with the sign flipped (p odd), a ghost half row k < z0
+// its mirror half row (v_z even); other rows read themselves.
+__device__ __forceinline__ int node_src_row(const GridDev &g, int r) { return (g.fs && r < g.z0) ? fs_node_row(g, r) : r; }
+__device__ __forceinline__ int half_src_row(const GridDev &g, int k) { return (g.fs && k < g.z0) ? fs_half_row(g, k) : k; }
 
 // Staggered first difference sum_l c_l (a_l - b_l): the M differences are
 // independent, then one multiply-add chain of depth M (short critical path).
@@ -207,12 +215,15 @@ __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float
     const int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
     const int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
     const int zr = z + W - 1, k = z + M - 1;
-    const bool okr = colok && zr >= 0 && zr < g.Nz;
-    const long long cr = okr ? (long long)zr * pitch + xc : 0;
+    const int zrs = node_src_row(g, zr), ks = half_src_row(g, k);
+    const bool okr = colok && zrs >= 0 && zrs < g.Nz;
+    const long long cr = okr ? (long long)zrs * pitch + xc : 0;
     const bool okk1 = colok && k + 1 >= 0;
     const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
     const bool okk = colok && k >= 0 && k < g.Nz;
     const long long ck = okk ? (long long)k * pitch + xc : 0;
+    const bool okks = okk && ks < g.Nz;
+    const long long cks = okks ? (long long)ks * pitch + xc : 0;
     const bool pz = okk && ((k <= g.z0 - 2) || (k >= g.z0 + g.nz));
     const bool main = z >= zc0 && z < zc1;
     const bool okz = colok && main;
@@ -221,7 +232,7 @@ __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float
     const bool oko = outcol && main;
     constexpr size_t F = (size_t)NTH * 8;   // bytes between field rows of a stage
     cpa(reinterpret_cast<T *>(sl + 0 * F), fin + oP * pT + cr, okr);
-    cpa(reinterpret_cast<T *>(sl + 1 * F), fin + oVZ * pT + ck, okk);
+    cpa(reinterpret_cast<T *>(sl + 1 * F), fin + oVZ * pT + cks, okks);
     cpa_if(reinterpret_cast<T *>(sl + 2 * F), fin + oPPZ * pT + ck, pz);
     cpa(reinterpret_cast<T *>(sl + 3 * F), fin + oVX * pT + cz, okv);
     cpa_if(reinterpret_cast<T *>(sl + 4 * F), fin + oPPX * pT + cz, okv && pmlxh);
@@ -314,8 +325,9 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
         const T *pin = reinterpret_cast<const T *>(in) + oP * pT + xc;
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) {
-            int zr = zstart + j;
-            P[j] = (colok && zr >= 0 && zr < g.Nz) ? pin[(long long)zr * pitch] : zero_<T>();
+            const int zr = zstart + j, zrs = node_src_row(g, zr);
+            const T v = (colok && zrs >= 0 && zrs < g.Nz) ? pin[(long long)zrs * pitch] : zero_<T>();
+            P[j] = zrs != zr ? neg_(v) : v;
         }
     }
     R br_old = zero_<R>();
@@ -348,7 +360,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PDF) * kFwdStageSlotBytes);
             const int k = z + M - 1;   // half row of vz computed in this iteration
             const int sl = u + W - 1;
-            P[sl] = cur.p;
+            P[sl] = (g.fs && z + W - 1 < g.z0) ? neg_(cur.p) : cur.p;   // ghost rows hold -p(mirror)
             // ---- vz at half row k (column-local)
             const float buz = 0.5f * (xof(br_old) + xof(cur.br1));
             const float rsum = yof(br_old) + yof(cur.br1);
@@ -450,6 +462,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
                 } else {
                     if (cz + x == src) pn += wsrc;
                 }
+                if (g.fs && z <= z0) pn = zero_<T>();   // p = 0 on the free surface (ghost rows unused)
                 out[oP * pT + cz] = pn;
                 if (BANDS) {
                     long long b = pband_index(z - z0, ix, M, g.nz, nx);
@@ -532,10 +545,15 @@ __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const floa
     float *s1 = st + 2 * kAdjF2 * NTH + t;
     const float2 *in2 = reinterpret_cast<const float2 *>(in);
     const int zr = z + W - 1, k = z + M - 1;
+    const int zrs = node_src_row(g, zr), ks = half_src_row(g, k);
     const bool okr = colok && zr >= 0 && zr < g.Nz;
     const long long cr = okr ? (long long)zr * pitch + xc : 0;
+    const bool okrs = colok && zrs >= 0 && zrs < g.Nz;
+    const long long crs = okrs ? (long long)zrs * pitch + xc : 0;
     const bool okk = colok && k >= 0 && k < g.Nz;
     const long long ck = okk ? (long long)k * pitch + xc : 0;
+    const bool okks = okk && ks < g.Nz;
+    const long long cks = okks ? (long long)ks * pitch + xc : 0;
     const bool okk1 = colok && k + 1 >= 0;
     const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
     const bool main = z >= zc0 && z < zc1;
@@ -543,8 +561,8 @@ __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const floa
     const long long cz = okz ? (long long)z * pitch + xc : 0;
     const bool okv = vxok && main;
     const int iz = z - z0;
-    cpa(s2 + 0 * NTH, in2 + (A_PL / 2) * p2 + cr, okr);
-    cpa(s2 + 1 * NTH, in2 + (A_VZ / 2) * p2 + ck, okk);
+    cpa(s2 + 0 * NTH, in2 + (A_PL / 2) * p2 + crs, okrs);
+    cpa(s2 + 1 * NTH, in2 + (A_VZ / 2) * p2 + cks, okks);
     cpa(s2 + 2 * NTH, in2 + (A_PL / 2) * p2 + cz, okz);
     cpa(s2 + 3 * NTH, in2 + (A_VX / 2) * p2 + cz, okv);
     cpa(s2 + 4 * NTH, img + cz, outcol && main && inner_col && iz >= 0 && iz < g.nz);
@@ -648,7 +666,13 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
         PIZ[j] = 0.f;
     }
     // (p^n, kdt*lp - ai_z (lpsi_vz - kdt*lp)) at node row r of this column
+    // (pl holds the mirror row's values for a ghost row r < z0; the surface
+    // row carries p = 0 and lambda_p = 0)
     auto pu_node = [&](int r, float2 pl, float kd, float lpvz) -> float2 {
+        if (g.fs && r <= z0) {
+            if (r == z0) return make_float2(0.f, 0.f);
+            return make_float2(-pl.x, -(kd * pl.y));
+        }
         float kl = kd * pl.y;
         if (colok && r >= 0 && r < g.Nz && ((r <= z0 - 1) || (r >= z1))) kl -= a.pml.ai[0][r] * (lpvz - kl);
         return make_float2(pl.x, kl);
@@ -657,10 +681,11 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
         const float2 *in2 = reinterpret_cast<const float2 *>(in);
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) {
-            const int r = zstart + j;
+            const int r = zstart + j, rs = node_src_row(g, r);
             const bool ok = colok && r >= 0 && r < g.Nz;
             const long long cr = ok ? (long long)r * pitch + xc : 0;
-            const float2 pl = ok ? in2[(A_PL / 2) * p2 + cr] : make_float2(0.f, 0.f);
+            const bool oks = colok && rs >= 0 && rs < g.Nz;
+            const float2 pl = oks ? in2[(A_PL / 2) * p2 + (long long)rs * pitch + xc] : make_float2(0.f, 0.f);
             const float kd = ok ? (WIN ? in[W_KDT * plane + cr] : a.kdt[cr]) : 0.f;
             const float lpvz = (ok && ((r <= z0 - 1) || (r >= z1))) ? in[A_LPVZ * plane + cr] : 0.f;
             PU[j] = pu_node(r, pl, kd, lpvz);
@@ -717,7 +742,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 piz = D.x * lv;
                 if (recon && xint) {
                     const int iz = k - z0;
-                    if (iz >= 0 && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
+                    if ((iz >= 0 || g.fs) && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
                     else if (in_xstrip(iz, M, g.nz))
                         vn = band_get(a.bands, 1, rowprev, band_zstrip(iz, ix, M, g.nz, nx));
                 }
@@ -730,8 +755,9 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
 
             // ---- row z: half nodes along x
             const long long cz = (long long)z * pitch;
+            const bool surf = g.fs && z == z0;   // free-surface row: p = 0, lambda_p = 0
             const float pbn = cur.plz.x;
-            const float lp1 = cur.plz.y;
+            const float lp1 = surf ? 0.f : cur.plz.y;
             const float kd = cur.kdz;
             const float kl = kd * lp1;
             sPU[t] = make_float2(pbn, pmlxn ? kl - aix * (cur.lpsvx - kl) : kl);
@@ -787,7 +813,8 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 if (inner) {
                     float2 acc = cur.img;
                     acc.x += E.x * lp1;
-                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[u + M] + PIZ[u + M - 1]);
+                    // (on the free surface the half row above is a ghost: no product of its own)
+                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[u + M] + (surf ? 0.f : PIZ[u + M - 1]));
                     img[cz] = acc;
                 }
                 float pn = 0.f;
@@ -800,7 +827,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                         if (b >= 0) pn = band_get(a.bands, 0, rowprev, b);
                     }
                 }
-                out2[(A_PL / 2) * p2 + cz] = make_float2(pn, lp1 + E.y);
+                out2[(A_PL / 2) * p2 + cz] = (g.fs && z <= z0) ? make_float2(0.f, 0.f) : make_float2(pn, lp1 + E.y);
                 if (pmlxn) outf[A_LPVX * plane + cz] = bix * (cur.lpsvx - kl);
                 if ((z <= z0 - 1) || (z >= z1)) outf[A_LPVZ * plane + cz] = a.pml.bi[0][z] * (cur.lpsvz - kl);
             }

@@ -130,11 +130,13 @@ __global__ void __launch_bounds__(256) k3_v(const Step3D a)
     for (int d = 0; d < 3; ++d) {
         const int i = coord(c, d), N = extent(g, d);
         const long long sd = stride(g, d);
-        float G = diff<M, float>(cdir(g, d), [&](int l) {
-            const float a1 = (i + l < N) ? P[cc + l * sd] : 0.f;
-            const float b1 = (i + 1 - l >= 0) ? P[cc + (1 - l) * sd] : 0.f;
-            return a1 - b1;
-        });
+        // p at node row j along d (free surface: a ghost z row holds -p(mirror))
+        auto pj = [&](int j) -> float {
+            if (j < 0 || j >= N) return 0.f;
+            if (d == 0 && g.fs && j < g.z0) return -P[cc + (long long)(fs_node_row(g, j) - i) * sd];
+            return P[cc + (long long)(j - i) * sd];
+        };
+        float G = diff<M, float>(cdir(g, d), [&](int l) { return pj(i + l) - pj(i + 1 - l); });
         if (pml_half(g, d, i)) {
             float *ps = st + (G3_PP + d) * plane;
             const float v = fmaf(a.pml.bh[d][i], ps[cc], a.pml.ah[d][i] * G);
@@ -179,11 +181,13 @@ __global__ void __launch_bounds__(256) k3_p(const Step3D a)
         const int i = coord(c, d), N = extent(g, d);
         const long long sd = stride(g, d);
         const float *V = st + (G3_V + d) * plane;
-        float q = diff<M, float>(cdir(g, d), [&](int l) {
-            const float a1 = (i + l - 1 < N) ? V[cc + (l - 1) * sd] : 0.f;
-            const float b1 = (i - l >= 0) ? V[cc - l * sd] : 0.f;
-            return a1 - b1;
-        });
+        // v_d at half row j along d (free surface: a ghost z half row holds v_z(mirror))
+        auto vj = [&](int j) -> float {
+            if (j < 0 || j >= N) return 0.f;
+            if (d == 0 && g.fs && j < g.z0) return V[cc + (long long)(fs_half_row(g, j) - i) * sd];
+            return V[cc + (long long)(j - i) * sd];
+        };
+        float q = diff<M, float>(cdir(g, d), [&](int l) { return vj(i + l - 1) - vj(i - l); });
         if (pml_node(g, d, i)) {
             float *pv = st + (G3_PV + d) * plane;
             const float v = fmaf(a.pml.bi[d][i], pv[cc], a.pml.ai[d][i] * q);
@@ -197,6 +201,7 @@ __global__ void __launch_bounds__(256) k3_p(const Step3D a)
     const float kd = a.kdt[cc];
     float pn = fmaf(-kd, Q, p0);
     if (cc == a.src_cell[shot]) pn += a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + a.n];
+    if (g.fs && c.z <= g.z0) pn = 0.f;   // p = 0 on the free surface (ghost rows unused)
     P[cc] = pn;
     const int iz = c.z - g.z0, iy = c.y - g.y0, ix = c.x - g.x0;
     if (BANDS) {

@@ -70,6 +70,13 @@ __device__ __forceinline__ float st1(const float *c, FA fa, FB fb)
     return acc;
 }
 
+// Free surface (method of images about row z0): ghost node rows r < z0 read
+// their mirror row with the sign flipped (p odd), ghost half rows k < z0 their
+// mirror half row (v_z even).
+__device__ __forceinline__ int node_src_row(const GridDev &g, int r) { return (g.fs && r < g.z0) ? fs_node_row(g, r) : r; }
+__device__ __forceinline__ int half_src_row(const GridDev &g, int k) { return (g.fs && k < g.z0) ? fs_half_row(g, k) : k; }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 // ---- shared memory, mbarriers and TMA
 __device__ __forceinline__ unsigned su32(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
 
@@ -184,8 +191,8 @@ __device__ __forceinline__ void born_issue(const Step3F &a, unsigned char *st, u
         return;
     }
     mbar_expect(bar, bytes);
-    tma4(st + S::PA, a.in_core, xc, y0, r, q + F3_P, bar);
-    tma4(st + S::VZ, a.in_core, xc, y0, k, q + F3_VZ, bar);
+    tma4(st + S::PA, a.in_core, xc, y0, node_src_row(g, r), q + F3_P, bar);
+    tma4(st + S::VZ, a.in_core, xc, y0, half_src_row(g, k), q + F3_VZ, bar);
     tma4(st + S::BK, a.m_core, xc, y0, k + 1, 1, bar);
     if (pzs) tma4(st + S::PZ, a.in_core, xc, y0, k, q + F3_PPZ, bar);
     if (main) {
@@ -249,8 +256,9 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_born(const __grid_constan
         const float2 *pin = reinterpret_cast<const float2 *>(a.in) + slot * a.in_pairs * plane + F3_P * plane;
 #pragma unroll
         for (int m = 0; m < W - 1; ++m) {
-            const int zr = zstart + m;
-            P[m] = (colok && zr >= 0 && zr < g.Nz) ? pin[zr * g.rowz + cxy] : make_float2(0.f, 0.f);
+            const int zr = zstart + m, zs = node_src_row(g, zr);
+            const float2 v = (colok && zs >= 0 && zs < g.Nz) ? pin[zs * g.rowz + cxy] : make_float2(0.f, 0.f);
+            P[m] = zs != zr ? neg2(v) : v;
         }
 #pragma unroll
         for (int m = 0; m < W; ++m) VZ[m] = make_float2(0.f, 0.f);
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_born(const __grid_constan
         const int k = z + M - 1;
 
         // ---- vz at half row k (column-local)
-        P[W - 1] = cPA[t];
+        P[W - 1] = (g.fs && z + W - 1 < g.z0) ? neg2(cPA[t]) : cPA[t];   // ghost rows: -p(mirror)
         // (the last half row replicates the last node row's buoyancy)
         const float2 brk1 = k + 1 < g.Nz ? cBK[t] : make_float2(br_old.x, 0.f);
         float2 vzn = make_float2(0.f, 0.f);
@@ -407,6 +415,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_born(const __grid_constan
                 float2 pn = fma2(-kd.x, Q, p0);
                 pn.y = fmaf(-kd.y, Q.x, pn.y);
                 if (c == src) pn.x += wsrc;
+                if (g.fs && z <= g.z0) pn = make_float2(0.f, 0.f);   // p = 0 on the free surface
                 out[F3_P * pl + c] = pn;
             }
         }
@@ -536,9 +545,9 @@ __device__ __forceinline__ void adj_issue(const Adj3F &a, unsigned char *st, uin
         return;
     }
     mbar_expect(bar, bytes);
-    tma4(st + S::PA, a.p_core, 2 * xc, y0, r, qp + A3F_PL / 2, bar);
+    tma4(st + S::PA, a.p_core, 2 * xc, y0, node_src_row(g, r), qp + A3F_PL / 2, bar);
     if (rs) tma4(st + S::LA, a.f_core, xc, y0, r, qf + A3F_LPVZ, bar);
-    tma4(st + S::VZ, a.p_core, 2 * xc, y0, k, qp + A3F_VZ / 2, bar);
+    tma4(st + S::VZ, a.p_core, 2 * xc, y0, half_src_row(g, k), qp + A3F_VZ / 2, bar);
     tma4(st + S::BK, a.m_core, xc, y0, k + 1, 1, bar);
     if (ks) tma4(st + S::PZ, a.f_core, xc, y0, k, qf + A3F_LPPZ, bar);
     if (main) {
@@ -612,7 +621,10 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
     }
 
     // (p^n, u_z) at node row rr of this column
+    // (pq holds the mirror row's values for a ghost row rr < z0; the surface
+    // row carries p = 0 and lambda_p = 0)
     auto pu_node = [&](int rr, float2 pq, float kd, float lpvz) -> float2 {
+        if (g.fs && rr <= g.z0) return rr == g.z0 ? make_float2(0.f, 0.f) : make_float2(-pq.x, -(kd * pq.y));
         float u = kd * pq.y;
         if (colok && rr >= 0 && rr < g.Nz && (rr <= g.z0 - 1 || rr >= g.z0 + g.nz)) u -= a.pml.ai[0][rr] * (lpvz - u);
         return make_float2(pq.x, u);
@@ -630,10 +642,10 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
         const float2 *pin = reinterpret_cast<const float2 *>(in) + (A3F_PL / 2) * (long long)pl;
 #pragma unroll
         for (int m = 0; m < W - 1; ++m) {
-            const int rr = zstart + m;
+            const int rr = zstart + m, rs = node_src_row(g, rr);
             const bool ok = colok && rr >= 0 && rr < g.Nz;
             const int c = ok ? rr * rowz + cxy : 0;
-            const float2 pq = ok ? pin[c] : make_float2(0.f, 0.f);
+            const float2 pq = (colok && rs >= 0 && rs < g.Nz) ? pin[rs * rowz + cxy] : make_float2(0.f, 0.f);
             const float kd = ok ? a.kdt[c] : 0.f;
             const float lv = (ok && (rr <= g.z0 - 1 || rr >= g.z0 + g.nz)) ? in[A3F_LPVZ * (long long)pl + c] : 0.f;
             PU[m] = pu_node(rr, pq, kd, lv);
@@ -691,7 +703,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
                 piz = D.x * lv;
                 if (recon && xin && yin) {
                     const int iz = k - g.z0;
-                    if (iz >= 0 && iz < g.nz) vn = v2.x + dtbu * D.x;
+                    if ((iz >= 0 || g.fs) && iz < g.nz) vn = v2.x + dtbu * D.x;   // ghost half rows: mirrors
                     else {
                         const long long b = fband(g, 0, iz, iyg, ixg);
                         if (b >= 0) vn = band_get(a.bands, 1, rowprev, b);
@@ -719,7 +731,10 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
             // ---- (p, lambda_p) -> (p, dt kappa lambda_p) over the wide tile;
             // the thread's own node first (it keeps p^n and lambda_p)
             const int own_w = (ty + G::YO2) * G::XW2 + tx + G::XO2;
-            const float2 pl1 = wP[own_w];
+            const bool surf = g.fs && z == g.z0;   // free-surface row: p = 0, lambda_p = 0
+            const float lsc = surf ? 0.f : 1.f;
+            float2 pl1 = wP[own_w];
+            pl1.y *= lsc;
             const float kd = wK[own_w];
             const float kl = kd * pl1.y;
             wP[own_w] = make_float2(pl1.x, kl);
@@ -727,7 +742,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
                 const int rr = i / G::XW2, cc = i - rr * G::XW2;
                 if (rr >= G::YO2 && rr < G::YO2 + TY && cc >= G::XO2 && cc < G::XO2 + TX) continue;
                 const float2 v = wP[i];
-                wP[i] = make_float2(v.x, wK[i] * v.y);
+                wP[i] = make_float2(v.x, wK[i] * (v.y * lsc));
             }
             // these generic-proxy writes to the stage must be ordered before the
             // TMA copy that refills it (issued after the next row's barrier):
@@ -862,7 +877,8 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
                 if (inner) {
                     float2 acc = img[c];
                     acc.x += E.x * pl1.y;
-                    acc.y += (oIX[hx] + oIX[hx - 1]) + (oIY[hy] + oIY[hy - TX]) + (PIZ[M] + PIZ[M - 1]);
+                    // (on the free surface the half row above is a ghost: no product of its own)
+                    acc.y += (oIX[hx] + oIX[hx - 1]) + (oIY[hy] + oIY[hy - TX]) + (PIZ[M] + (surf ? 0.f : PIZ[M - 1]));
                     img[c] = acc;
                 }
                 float pn = 0.f;
@@ -876,7 +892,8 @@ __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant
                         if (b >= 0) pn = band_get(a.bands, 0, rowprev, b);
                     }
                 }
-                out2[(A3F_PL / 2) * pl + c] = make_float2(pn, pl1.y + E.y);
+                out2[(A3F_PL / 2) * pl + c] =
+                    (g.fs && z <= g.z0) ? make_float2(0.f, 0.f) : make_float2(pn, pl1.y + E.y);
                 if (x <= g.x0 - 1 || x >= g.x0 + g.nx)
                     outf[A3F_LPVX * pl + c] = a.pml.bi[2][x] * (bLX[ty * G::XW2 + tx + G::XO2] - kl);
                 if (y <= g.y0 - 1 || y >= g.y0 + g.ny)

@@ -30,7 +30,10 @@ __global__ void k_model_prep(GridDev g, const float *vp, const float *rho, float
         long long t = c / g.Nx;
         int y = (int)(t % g.Ny);
         int z = (int)(t / g.Ny);
-        int iz = min(max(z - g.z0, 0), g.nz - 1);
+        // edge replication into the pad; above a free surface the mirror image
+        int iz = z - g.z0;
+        if (g.fs && iz < 0) iz = -iz;
+        iz = min(max(iz, 0), g.nz - 1);
         int iy = min(max(y - g.y0, 0), g.ny - 1);
         int ix = min(max(x - g.x0, 0), g.nx - 1);
         long long k = ((long long)iz * g.ny + iy) * g.nx + ix;
@@ -57,6 +60,9 @@ __global__ void k_pert_prep(GridDev g, const float *dm, const float *kdt, const 
         int z = (int)(t / g.Ny);
         long long c = (long long)z * g.rowz + (long long)y * g.pitch + x;
         int iz = z - g.z0, iy = y - g.y0, ix = x - g.x0;
+        // the perturbation lives on the interior; above a free surface its
+        // mirror image, so ghost velocities are exact mirrors of live ones
+        if (g.fs && iz < 0) iz = -iz;
         float dk = 0.f, dr = 0.f;
         if (iz >= 0 && iz < g.nz && iy >= 0 && iy < g.ny && ix >= 0 && ix < g.nx) {
             long long k = ((long long)iz * g.ny + iy) * g.nx + ix;

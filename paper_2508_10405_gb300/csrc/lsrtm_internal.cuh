@@ -26,7 +26,13 @@ struct GridDev {
     float cz[kMaxM], cy[kMaxM], cx[kMaxM];  // c_l / h
     float dt;
     int nt;
+    int fs;                // free surface on row z0 (method of images; see lsrtm_config)
 };
+
+// Free surface: the padded row a ghost node row r < z0 mirrors (p odd about
+// z0), and the half row a ghost half row k < z0 mirrors (v_z even).
+__host__ __device__ inline int fs_node_row(const GridDev &g, int r) { return 2 * g.z0 - r; }
+__host__ __device__ inline int fs_half_row(const GridDev &g, int k) { return 2 * g.z0 - 1 - k; }
 
 // CPML coefficients, per direction d (0 z, 1 y, 2 x) and array: a/b at
 // integer nodes (ai, bi) and at half nodes (ah, bh).
