@@ -1383,6 +1383,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     // last 6 as the in-place node CPML memories), st[1] (14 planes, pong), the
     // float2 image plane and the pseudo-Hessian plane
     h->sstride1 = d3 ? 2LL * kBornPairs3F * g.plane : h->sstride;
+    if (h->sstride >= (1LL << 31))   // the time-step kernels index within a slot with 32-bit offsets
+        return fail(LSRTM_ERR_ARG, "grid too large: a wavefield slot exceeds 2^31 floats");
     size_t per_slot = d3 ? ((size_t)h->sstride + h->sstride1 + 3 * g.plane) * sizeof(float)
                          : (2 * (size_t)h->sstride + h->vstride + 2 * g.plane + g.plane) * sizeof(float);
     if (h->bands.fmt != BAND_F32) per_slot += 2 * (size_t)h->bands.nb * sizeof(float);   // FP32 band stage

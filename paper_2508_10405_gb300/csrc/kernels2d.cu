@@ -33,6 +33,7 @@ constexpr int PDF = 4;   // depth of the asynchronous row pipeline (forward)
 constexpr int PDA = 3;   // depth of the asynchronous row pipeline (adjoint; 3 CTAs per SM fit)
 constexpr int kFwdMinBlocks = 2;   // resident CTAs per SM the register budget targets
 constexpr int kAdjMinBlocks = 3;
+constexpr int kAdjMinBlocksFS = 2;   // the free-surface variant needs more registers
 // The z-marches are unrolled by 2M / k*GroupDiv rows and shift their register
 // rings after every group: a full 2M-row unroll made the migration loop body
 // large enough to miss in the instruction cache.
@@ -72,8 +73,10 @@ __device__ __forceinline__ float2 neg_(float2 a) { return make_float2(-a.x, -a.y
 // Free surface (method of images about row z0): a ghost node row r < z0
 // reads its mirror row with the sign flipped (p odd), a ghost half row k < z0
 // its mirror half row (v_z even); other rows read themselves.
-__device__ __forceinline__ int node_src_row(const GridDev &g, int r) { return (g.fs && r < g.z0) ? fs_node_row(g, r) : r; }
-__device__ __forceinline__ int half_src_row(const GridDev &g, int k) { return (g.fs && k < g.z0) ? fs_half_row(g, k) : k; }
+template <bool FS>
+__device__ __forceinline__ int node_src_row(const GridDev &g, int r) { return (FS && r < g.z0) ? fs_node_row(g, r) : r; }
+template <bool FS>
+__device__ __forceinline__ int half_src_row(const GridDev &g, int k) { return (FS && k < g.z0) ? fs_half_row(g, k) : k; }
 
 // Staggered first difference sum_l c_l (a_l - b_l): the M differences are
 // independent, then one multiply-add chain of depth M (short critical path).
@@ -194,7 +197,7 @@ struct FwdRow {
     K kd;     // dt kappa (, dt kappa dlnk) at row z
 };
 
-template <int M, bool BORN, bool WIN>
+template <int M, bool BORN, bool WIN, bool FS>
 __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float *in, int xc, int z,
                                           int zc0, int zc1, bool colok, bool vxok, bool outcol,
                                           bool pmlxh)
@@ -211,23 +214,23 @@ __device__ __forceinline__ void fwd_issue(char *st, const Step2D &a, const float
                       : (BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv));
     const K *kk = WIN ? reinterpret_cast<const K *>(in + (BORN ? W_KD2 : W_KDT) * g.plane)
                       : (BORN ? reinterpret_cast<const K *>(a.kd2) : reinterpret_cast<const K *>(a.kdt));
-    const long long pT = g.plane;   // cells per plane: the stride of one (pair) field in units of T
+    const int pT = (int)g.plane;   // cells per plane: the stride of one (pair) field in units of T (in-slot offsets fit 32 bits)
     const int oP = BORN ? B_P / 2 : G_P, oVX = BORN ? B_VX / 2 : G_VX, oVZ = BORN ? B_VZ / 2 : G_VZ;
     const int oPPX = BORN ? B_PPX / 2 : G_PPX, oPPZ = BORN ? B_PPZ / 2 : G_PPZ;
     const int zr = z + W - 1, k = z + M - 1;
-    const int zrs = node_src_row(g, zr), ks = half_src_row(g, k);
+    const int zrs = node_src_row<FS>(g, zr), ks = half_src_row<FS>(g, k);
     const bool okr = colok && zrs >= 0 && zrs < g.Nz;
-    const long long cr = okr ? (long long)zrs * pitch + xc : 0;
+    const int cr = okr ? zrs * pitch + xc : 0;
     const bool okk1 = colok && k + 1 >= 0;
-    const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
+    const int ck1 = okk1 ? min(k + 1, g.Nz - 1) * pitch + xc : 0;
     const bool okk = colok && k >= 0 && k < g.Nz;
-    const long long ck = okk ? (long long)k * pitch + xc : 0;
+    const int ck = okk ? k * pitch + xc : 0;
     const bool okks = okk && ks < g.Nz;
-    const long long cks = okks ? (long long)ks * pitch + xc : 0;
+    const int cks = okks ? ks * pitch + xc : 0;
     const bool pz = okk && ((k <= g.z0 - 2) || (k >= g.z0 + g.nz));
     const bool main = z >= zc0 && z < zc1;
     const bool okz = colok && main;
-    const long long cz = okz ? (long long)z * pitch + xc : 0;
+    const int cz = okz ? z * pitch + xc : 0;
     const bool okv = vxok && main;
     const bool oko = outcol && main;
     constexpr size_t F = (size_t)NTH * 8;   // bytes between field rows of a stage
@@ -261,7 +264,7 @@ __device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
     return r;
 }
 
-template <int M, bool BORN, bool BANDS, bool HESS, bool WIN>
+template <int M, bool BORN, bool BANDS, bool HESS, bool WIN, bool FS>
 __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
 {
     using C = Cols<M>;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
     const int zc1 = min(zc0 + a.tzc, g.Nz);
     const int zstart = zc0 - W;
     const long long plane = g.plane;
-    const long long pT = plane;   // cells per plane: the stride of one (pair) field in units of T
+    const int pT = (int)plane;   // in-slot offsets fit 32 bits (checked by the host)
     const int pitch = g.pitch;
     const int xc = colok ? x : 0;
     const float *in = a.in + slot * a.sstride;
@@ -325,8 +328,8 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
         const T *pin = reinterpret_cast<const T *>(in) + oP * pT + xc;
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) {
-            const int zr = zstart + j, zrs = node_src_row(g, zr);
-            const T v = (colok && zrs >= 0 && zrs < g.Nz) ? pin[(long long)zrs * pitch] : zero_<T>();
+            const int zr = zstart + j, zrs = node_src_row<FS>(g, zr);
+            const T v = (colok && zrs >= 0 && zrs < g.Nz) ? pin[zrs * pitch] : zero_<T>();
             P[j] = zrs != zr ? neg_(v) : v;
         }
     }
@@ -335,13 +338,13 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
         const R *br = WIN ? reinterpret_cast<const R *>(in + (BORN ? W_BR2 : W_BINV) * plane)
                           : (BORN ? reinterpret_cast<const R *>(a.br2) : reinterpret_cast<const R *>(a.binv));
         int k = zstart + M - 1;
-        if (colok && k >= 0 && k < g.Nz) br_old = br[(long long)k * pitch + xc];
+        if (colok && k >= 0 && k < g.Nz) br_old = br[k * pitch + xc];
     }
 
 #pragma unroll
     for (int j = 0; j < PDF - 1; ++j) {
         if (zstart + j < zc1)
-            fwd_issue<M, BORN, WIN>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
+            fwd_issue<M, BORN, WIN, FS>(stages + j * kFwdStageSlotBytes, a, in, xc, zstart + j, zc0, zc1, colok, vxok,
                                outcol, pmlxh);
         cp_commit();
     }
@@ -353,14 +356,14 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             if (z >= zc1) break;
             const int zi = z + PDF - 1;
             if (zi < zc1)
-                fwd_issue<M, BORN, WIN>(stages + ((zi - zstart) % PDF) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
+                fwd_issue<M, BORN, WIN, FS>(stages + ((zi - zstart) % PDF) * kFwdStageSlotBytes, a, in, xc, zi, zc0, zc1,
                                    colok, vxok, outcol, pmlxh);
             cp_commit();
             cp_wait_row<PDF>();
             const FwdRow<BORN> cur = fwd_read<BORN>(stages + ((z - zstart) % PDF) * kFwdStageSlotBytes);
             const int k = z + M - 1;   // half row of vz computed in this iteration
             const int sl = u + W - 1;
-            P[sl] = (g.fs && z + W - 1 < g.z0) ? neg_(cur.p) : cur.p;   // ghost rows hold -p(mirror)
+            P[sl] = (FS && z + W - 1 < g.z0) ? neg_(cur.p) : cur.p;   // ghost rows hold -p(mirror)
             // ---- vz at half row k (column-local)
             const float buz = 0.5f * (xof(br_old) + xof(cur.br1));
             const float rsum = yof(br_old) + yof(cur.br1);
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             T vzn = zero_<T>();
             float hzq = 0.f;
             if (colok && k >= 0 && k < g.Nz) {
-                const long long ck = (long long)k * pitch;
+                const int ck = k * pitch;
                 const bool own = outcol && k >= zc0 && k < zc1;
                 T G = stencil<M, T>(g.cz, [&](int l) { return P[u + M - 1 + l]; },
                                     [&](int l) { return P[u + M - l]; });
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
             if (z < zc0) continue;   // warm-up rows of the z rings
 
             // ---- row z: vx on the output columns and the halo
-            const long long cz = (long long)z * pitch;
+            const int cz = z * pitch;
             const T p0 = P[u];
             sP[t] = p0;
             sB[t] = cur.brz;
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
                 } else {
                     if (cz + x == src) pn += wsrc;
                 }
-                if (g.fs && z <= z0) pn = zero_<T>();   // p = 0 on the free surface (ghost rows unused)
+                if (FS && z <= z0) pn = zero_<T>();   // p = 0 on the free surface (ghost rows unused)
                 out[oP * pT + cz] = pn;
                 if (BANDS) {
                     long long b = pband_index(z - z0, ix, M, g.nz, nx);
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
                         float bx0 = xof(cur.brz);
                         float hr = 0.5f * ((sH[t] + sH[t - 1]) + (HZ[u + M] + HZ[u + M - 1])) / (bx0 * bx0);
                         float kq = kd * xof(Q) / dt;
-                        a.hess[slot * plane + cz + xc] += dt * (hr + kq * kq);
+                        (a.hess + slot * plane)[cz + xc] += dt * (hr + kq * kq);
                     }
                 }
             }
@@ -529,7 +532,7 @@ struct AdjRow {
     float kdr, lpvzr, bz, lppz, kdz, lpsvx, lpsvz, bx, lppx;
 };
 
-template <int M, bool WIN>
+template <int M, bool WIN, bool FS>
 __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const float2 *img, const float *in,
                                           int xc, int z, int zc0, int zc1, bool colok, bool vxok,
                                           bool outcol, bool pmlxh, bool pmlxn, bool inner_col)
@@ -545,15 +548,21 @@ __device__ __forceinline__ void adj_issue(float *st, const Step2D &a, const floa
     float *s1 = st + 2 * kAdjF2 * NTH + t;
     const float2 *in2 = reinterpret_cast<const float2 *>(in);
     const int zr = z + W - 1, k = z + M - 1;
-    const int zrs = node_src_row(g, zr), ks = half_src_row(g, k);
     const bool okr = colok && zr >= 0 && zr < g.Nz;
     const long long cr = okr ? (long long)zr * pitch + xc : 0;
-    const bool okrs = colok && zrs >= 0 && zrs < g.Nz;
-    const long long crs = okrs ? (long long)zrs * pitch + xc : 0;
     const bool okk = colok && k >= 0 && k < g.Nz;
     const long long ck = okk ? (long long)k * pitch + xc : 0;
-    const bool okks = okk && ks < g.Nz;
-    const long long cks = okks ? (long long)ks * pitch + xc : 0;
+    // free surface: the pressure pair of a ghost row and v_z of a ghost half
+    // row come from their mirror rows
+    bool okrs = okr, okks = okk;
+    long long crs = cr, cks = ck;
+    if constexpr (FS) {
+        const int zrs = node_src_row<FS>(g, zr), ks = half_src_row<FS>(g, k);
+        okrs = colok && zrs >= 0 && zrs < g.Nz;
+        crs = okrs ? (long long)zrs * pitch + xc : 0;
+        okks = okk && ks < g.Nz;
+        cks = okks ? (long long)ks * pitch + xc : 0;
+    }
     const bool okk1 = colok && k + 1 >= 0;
     const long long ck1 = okk1 ? (long long)min(k + 1, g.Nz - 1) * pitch + xc : 0;
     const bool main = z >= zc0 && z < zc1;
@@ -602,8 +611,8 @@ __device__ __forceinline__ AdjRow adj_read(const float *st)
     return r;
 }
 
-template <int M, bool WIN>
-__global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
+template <int M, bool WIN, bool FS>
+__global__ void __launch_bounds__(NTH, FS ? kAdjMinBlocksFS : kAdjMinBlocks) k_adj2d(const Step2D a)
 {
     using C = Cols<M>;
     constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
@@ -669,7 +678,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
     // (pl holds the mirror row's values for a ghost row r < z0; the surface
     // row carries p = 0 and lambda_p = 0)
     auto pu_node = [&](int r, float2 pl, float kd, float lpvz) -> float2 {
-        if (g.fs && r <= z0) {
+        if (FS && r <= z0) {
             if (r == z0) return make_float2(0.f, 0.f);
             return make_float2(-pl.x, -(kd * pl.y));
         }
@@ -681,14 +690,14 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
         const float2 *in2 = reinterpret_cast<const float2 *>(in);
 #pragma unroll
         for (int j = 0; j < W - 1; ++j) {
-            const int r = zstart + j, rs = node_src_row(g, r);
+            const int r = zstart + j, rs = node_src_row<FS>(g, r);
             const bool ok = colok && r >= 0 && r < g.Nz;
             const long long cr = ok ? (long long)r * pitch + xc : 0;
             const bool oks = colok && rs >= 0 && rs < g.Nz;
-            const float2 pl = oks ? in2[(A_PL / 2) * p2 + (long long)rs * pitch + xc] : make_float2(0.f, 0.f);
+            const float2 plv = oks ? in2[(A_PL / 2) * p2 + (long long)rs * pitch + xc] : make_float2(0.f, 0.f);
             const float kd = ok ? (WIN ? in[W_KDT * plane + cr] : a.kdt[cr]) : 0.f;
             const float lpvz = (ok && ((r <= z0 - 1) || (r >= z1))) ? in[A_LPVZ * plane + cr] : 0.f;
-            PU[j] = pu_node(r, pl, kd, lpvz);
+            PU[j] = pu_node(r, plv, kd, lpvz);
         }
     }
     float bz_old = 0.f;
@@ -701,7 +710,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
 #pragma unroll
     for (int j = 0; j < PDA - 1; ++j) {
         if (zstart + j < zc1)
-            adj_issue<M, WIN>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
+            adj_issue<M, WIN, FS>(stagef + j * kAdjStageFloats, a, imgs, in, xc, zstart + j, zc0, zc1, colok, vxok,
                          outcol, pmlxh, pmlxn, xint);
         cp_commit();
     }
@@ -713,7 +722,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
             if (z >= zc1) break;
             const int zi = z + PDA - 1;
             if (zi < zc1)
-                adj_issue<M, WIN>(stagef + ((zi - zstart) % PDA) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
+                adj_issue<M, WIN, FS>(stagef + ((zi - zstart) % PDA) * kAdjStageFloats, a, imgs, in, xc, zi, zc0, zc1,
                              colok, vxok, outcol, pmlxh, pmlxn, xint);
             cp_commit();
             cp_wait_row<PDA>();
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                 piz = D.x * lv;
                 if (recon && xint) {
                     const int iz = k - z0;
-                    if ((iz >= 0 || g.fs) && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
+                    if ((iz >= 0 || FS) && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
                     else if (in_xstrip(iz, M, g.nz))
                         vn = band_get(a.bands, 1, rowprev, band_zstrip(iz, ix, M, g.nz, nx));
                 }
@@ -755,7 +764,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
 
             // ---- row z: half nodes along x
             const long long cz = (long long)z * pitch;
-            const bool surf = g.fs && z == z0;   // free-surface row: p = 0, lambda_p = 0
+            const bool surf = FS && z == z0;   // free-surface row: p = 0, lambda_p = 0
             const float pbn = cur.plz.x;
             const float lp1 = surf ? 0.f : cur.plz.y;
             const float kd = cur.kdz;
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(NTH, kAdjMinBlocks) k_adj2d(const Step2D a)
                         if (b >= 0) pn = band_get(a.bands, 0, rowprev, b);
                     }
                 }
-                out2[(A_PL / 2) * p2 + cz] = (g.fs && z <= z0) ? make_float2(0.f, 0.f) : make_float2(pn, lp1 + E.y);
+                out2[(A_PL / 2) * p2 + cz] = (FS && z <= z0) ? make_float2(0.f, 0.f) : make_float2(pn, lp1 + E.y);
                 if (pmlxn) outf[A_LPVX * plane + cz] = bix * (cur.lpsvx - kl);
                 if ((z <= z0 - 1) || (z >= z1)) outf[A_LPVZ * plane + cz] = a.pml.bi[0][z] * (cur.lpsvz - kl);
             }
@@ -879,18 +888,21 @@ __global__ void k_pack_adj(const GridDev g, const float *final_state, int shot0,
 template <int M, bool BORN, bool BANDS, bool HESS, bool WIN>
 cudaError_t launch_fwd_t(const Step2D &a, dim3 grid, cudaStream_t s)
 {
-    k_fwd2d<M, BORN, BANDS, HESS, WIN><<<grid, NTH, kFwdStageBytes, s>>>(a);
+    if (a.g.fs) k_fwd2d<M, BORN, BANDS, HESS, WIN, true><<<grid, NTH, kFwdStageBytes, s>>>(a);
+    else k_fwd2d<M, BORN, BANDS, HESS, WIN, false><<<grid, NTH, kFwdStageBytes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int M, bool BORN, bool BANDS, bool HESS>
 cudaError_t attr_fwd()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdStageBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kFwdStageBytes);
+    cudaError_t e;
+    const int b = (int)kFwdStageBytes;
+    const auto at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, false, false>, at, b)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, true, false>, at, b)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, false, true>, at, b)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fwd2d<M, BORN, BANDS, HESS, true, true>, at, b);
 }
 
 template <int M>
@@ -902,10 +914,12 @@ cudaError_t attr_M()
     if ((e = attr_fwd<M, false, true, false>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, false, true>()) != cudaSuccess) return e;
     if ((e = attr_fwd<M, false, false, false>()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_adj2d<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kAdjStageBytes)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_adj2d<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjStageBytes);
+    const int b = (int)kAdjStageBytes;
+    const auto at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(k_adj2d<M, false, false>, at, b)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_adj2d<M, true, false>, at, b)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_adj2d<M, false, true>, at, b)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj2d<M, true, true>, at, b);
 }
 
 template <int M, bool WIN>
@@ -930,10 +944,11 @@ template <int M>
 cudaError_t launch_adj_M(const Step2D &a, int batch, cudaStream_t s)
 {
     dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
-    if (a.win_nx)
-        k_adj2d<M, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
-    else
-        k_adj2d<M, false><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    const bool w = a.win_nx != nullptr, f = a.g.fs != 0;
+    if (w && f) k_adj2d<M, true, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    else if (w) k_adj2d<M, true, false><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    else if (f) k_adj2d<M, false, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
+    else k_adj2d<M, false, false><<<grid, NTH, kAdjStageBytes, s>>>(a);
     return cudaGetLastError();
 }
 
