@@ -41,8 +41,9 @@ import lsrtm_inputs as li  # noqa: E402
 
 # Algorithmic HBM bytes per cell-update (FP32, one pass per step, model read
 # raw): L = 2 x (3 + 3) state fields read + written + 4 model arrays; L^T = 6
-# state fields read + written + 2 model arrays + 2 image planes read + written.
-BYTES_PER_CELL = {("born", 2): 64.0, ("adjoint", 2): 72.0, ("born", 3): 80.0, ("adjoint", 3): 88.0}
+# state fields read + written + 2 model arrays + 2 image planes read + written;
+# background only = p, velocities read + written + dt kappa and 1/rho.
+from paper_2508_10405_gb300.cglog import BYTES_PER_CELL  # noqa: E402
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -430,8 +431,7 @@ def psf_reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-# Background-only time step: p, vx, vz read and written + dt kappa and 1/rho.
-MODEL_BYTES_PER_CELL = {2: 32.0, 3: 40.0}
+MODEL_BYTES_PER_CELL = {nd: BYTES_PER_CELL[("background", nd)] for nd in (2, 3)}
 
 
 def true_model(w):

@@ -90,6 +90,15 @@ typedef struct {
                                 model, and has no CPML (a reading for the surface
                                 acquisitions of Sec. 4-5); sources may not sit on that row,
                                 receivers there record zero. 0: CPML on every side. */
+    int guard_interval;      /* time steps between the non-finite guard's checks of the
+                                wavefields: every that many steps of every time loop one
+                                kernel scans the pressure planes of all slots of the batch
+                                for NaN/Inf; on a hit it sets a device word, the remaining
+                                time-step kernels of the loop return at once, and the call
+                                (or the next call that synchronises) fails with
+                                LSRTM_ERR_NONFINITE naming the loop and the step. CGNR
+                                also checks its FP64 scalars every iteration and polls the
+                                word one iteration behind. 0 = 64; < 0 = no wavefield checks. */
 } lsrtm_config;
 
 typedef struct {
@@ -155,7 +164,10 @@ lsrtm_status lsrtm_remigrate(lsrtm_handle *h, const float *m, float *out);
  * (computed once). Krylov scalars and inner products are FP64 on the device.
  *   d      : [nrec_total][nt] observed data
  *   dm     : [2][nz][ny][nx] in: starting model, out: solution after niter
- *   misfit : host [niter+1] or NULL: ||d - L dm_k|| / ||d|| per iteration */
+ *   misfit : host [niter+1] or NULL: ||d - L dm_k|| / ||d|| per iteration
+ * Errors: LSRTM_ERR_NONFINITE when the guard (lsrtm_config.guard_interval)
+ * finds NaN/Inf in a wavefield or a Krylov scalar, e.g. from NaN in d: the
+ * solve stops at most one iteration after the hit, dm is not written. */
 lsrtm_status lsrtm_cg_solve(lsrtm_handle *h, const float *d, float *dm, int niter, int precond,
                             int param_mask, double *misfit);
 
@@ -166,7 +178,11 @@ lsrtm_status lsrtm_cg_solve(lsrtm_handle *h, const float *d, float *dm, int nite
  * the normalised misfit after each of them (host [niter]);
  * lsrtm_cg_result copies the current iterate to dm ([2][nz][ny][nx]) and,
  * if misfit0 is not NULL, the misfit of x0. Only one solve per handle is
- * active; lsrtm_cg_begin restarts it. */
+ * active; lsrtm_cg_begin restarts it. lsrtm_cg_iterate returns
+ * LSRTM_ERR_NONFINITE one iteration after the guard trips (the iteration
+ * count then includes that iteration, whose time loops were skipped);
+ * without a misfit buffer a hit in its last iteration is reported by the
+ * next synchronising call (lsrtm_cg_result, lsrtm_synchronize). */
 lsrtm_status lsrtm_cg_begin(lsrtm_handle *h, const float *d, const float *x0, int precond,
                             int param_mask);
 lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit);
@@ -257,9 +273,10 @@ lsrtm_status lsrtm_mute_residual(lsrtm_handle *h, const float *d_obs, const floa
                                  double t_taper, double o_max, double o_taper, float *d_out);
 
 /* Waits for all work queued by the handle and reports a failure that a
- * kernel recorded on the device (a bounded wait for its tile copies that
- * gave up, or a refused misaligned copy) as LSRTM_ERR_CUDA; the record is
- * cleared. Operator calls are asynchronous, so such a failure surfaces here
+ * kernel recorded on the device: a bounded wait for its tile copies that
+ * gave up, or a refused misaligned copy, as LSRTM_ERR_CUDA; a tripped
+ * non-finite guard (lsrtm_config.guard_interval) as LSRTM_ERR_NONFINITE. The
+ * record is cleared. Operator calls are asynchronous, so such a failure surfaces here
  * or at the next synchronous call. The paper has no counterpart: this is
  * host-side error handling. */
 lsrtm_status lsrtm_synchronize(lsrtm_handle *h);

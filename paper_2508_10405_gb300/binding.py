@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
         ("band_precision", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
         ("recon_mode", ctypes.c_int), ("plan", ctypes.c_int), ("shots_per_batch", ctypes.c_int),
         ("wavelet_per_shot", ctypes.c_int), ("checkpoint_interval", ctypes.c_int),
-        ("free_surface", ctypes.c_int),
+        ("free_surface", ctypes.c_int), ("guard_interval", ctypes.c_int),
     ]
 
 
@@ -165,7 +165,7 @@ class Lsrtm:
                  vp, rho, wavelet, src_idx, rec_ptr, rec_idx, win_x0=None, win_nx=None, pml_vmax=None,
                  band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_AUTO,
                  plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, free_surface=False,
-                 stream=None):
+                 guard_interval=0, stream=None):
         import torch
         self._lib = load_library()
         self._h = ctypes.c_void_p()
@@ -177,7 +177,8 @@ class Lsrtm:
         self.cfg = Config(ndim, nz, ny if ndim == 3 else 1, nx, dz, dy or dx, dx, dt, nt,
                           fd_order, npml, f0, float(pml_vmax), band_precision,
                           int(hbm_budget_bytes), recon_mode, plan, shots_per_batch,
-                          1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval), int(bool(free_surface)))
+                          1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval), int(bool(free_surface)),
+                          int(guard_interval))
         self._src = np.ascontiguousarray(src_idx, dtype=np.int32)
         self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
         self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)
@@ -191,6 +192,7 @@ class Lsrtm:
         self.nshot = len(self._src)
         self.nrec_total = int(self._rp[-1])
         self.nt = nt
+        self.ndim = ndim
         self.shape = (nz, nx) if ndim == 2 else (nz, ny, nx)
         self.nint = int(np.prod(self.shape))
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -376,9 +378,18 @@ class Lsrtm:
         _check(self._lib.lsrtm_deblur_wiener(self._h, _ptr(a), _ptr(b), int(spacing), float(eps), _ptr(out)))
         return out
 
-    def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3):
-        """CGNR / PCGNR; returns (dm, misfit history of length niter+1)."""
+    def cg_solve(self, d, niter, x0=None, precond=False, param_mask=3, log=None, m_true=None):
+        """CGNR / PCGNR; returns (dm, misfit history of length niter+1).
+        With `log` (a path, "-" for stderr or a file object; default: the
+        LSRTM_PROFILE environment variable) the solve runs step-wise and
+        writes one JSON line per iteration (cglog): misfit, relative model
+        error against `m_true` if given, seconds, Gcell/s and GB/s."""
         import torch
+        from . import cglog
+        log = log if log is not None else cglog.env_log()
+        if log is not None:
+            return cglog.cg_solve_logged(self, d, niter, x0=x0, precond=precond, param_mask=param_mask,
+                                         log=log, m_true=m_true)
         self._sync_stream()
         d = _f32(d)
         x = torch.zeros((2,) + self.shape, dtype=torch.float32, device=self.device) \

@@ -104,7 +104,12 @@ struct lsrtm_handle {
     long long sstride1 = 0;      // slot stride of st[1] (3D: the fused kernels' pong buffer)
     Step3F f3born[2];            // fused 3D Born step arguments reading st[0] / st[1]
     Adj3F f3adj[2];              // fused 3D adjoint step arguments reading st[0] / st[1]
-    int *kerr = nullptr;         // device error word of the fused kernels
+    int *kerr = nullptr;         // device error words: [0] fused-kernel tile copies, [1] non-finite guard
+    int guard_K = 0;             // time steps between non-finite guard checks (0: off)
+    long long guard_count = 0;   // guard launches queued or captured so far
+    std::map<std::pair<int, int>, long long> graph_guards;   // guard launches per captured graph
+    int *poll_h = nullptr;       // pinned host copies of the error words, two per CG poll slot
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
     float *psiv = nullptr;
     long long vstride = 0;
     float2 *img = nullptr;
@@ -420,6 +425,8 @@ template <class F>
 lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs, long long nlaunch,
                         long long nsteps, F &&body)
 {
+    const long long g0 = h->guard_count;
+    long long guards = 0;   // guard checks (guard_step) of the loop
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (h->timing) {
         ea = take_event(h);
@@ -428,6 +435,7 @@ lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs,
     }
     if (!use_graphs(h)) {
         CHECK(body());
+        guards = h->guard_count - g0;
     } else {
         auto key = std::make_pair(kind, shot0);
         auto it = h->graphs.find(key);
@@ -447,11 +455,14 @@ lsrtm_status run_loop_n(lsrtm_handle *h, int kind, int tkind, int shot0, int bs,
             if (e != cudaSuccess)
                 return fail(LSRTM_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
             h->graphs[key] = exec;
+            h->graph_guards[key] = guards = h->guard_count - g0;
         } else {
             exec = it->second;
+            guards = h->graph_guards[key];
         }
         CU(cudaGraphLaunch(exec, h->work));
     }
+    nlaunch += guards;
     h->launches += nlaunch;
     if (h->timing && ea && eb) {
         CU(cudaEventRecord(eb, h->work));
@@ -468,6 +479,25 @@ int batch_size(const lsrtm_handle *h, int shot0) { return std::min(h->batch, h->
 
 lsrtm_status adj3f_step(lsrtm_handle *h, int i, int n, int s0, const Bands &bands);
 lsrtm_status adj3f_start(lsrtm_handle *h, int fs0, int s0, int bs);
+
+// Non-finite guard after the step of time n of a time loop of kind `kind`;
+// i counts the pass's steps from its start (n forward, nt-1-n in reverse
+// time, also across checkpoint segments). Every guard_K steps it checks the first
+// `planes` planes of each of bs slots of the state just written (the
+// pressure, with its Born or adjoint partner where the slot holds pairs).
+// Once the guard word is set the time-step kernels return at once; the host
+// reads the word when the call synchronises (check_kernel_error).
+lsrtm_status guard_step(lsrtm_handle *h, int kind, int i, int n, const float *st, long long sstride, int planes,
+                        int bs)
+{
+    if (h->guard_K <= 0 || (i + 1) % h->guard_K) return LSRTM_OK;
+    CU(launch_guard_state(st, sstride, planes * h->g.plane, bs, h->kerr + 1, guard_code(kind, n), h->work));
+    h->guard_count++;
+    return LSRTM_OK;
+}
+
+// Slot stride of state buffer j (3D: the fused kernels' ping and pong differ).
+long long slot_stride(const lsrtm_handle *h, int j) { return j ? h->sstride1 : h->sstride; }
 
 lsrtm_status zero_slots(lsrtm_handle *h, int bs)
 {
@@ -508,6 +538,7 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                         CU(launch_fwd3d(a, bs, true, hess, 2, h->work));
                     }
                     if (h->bands.fmt != BAND_F32) CU(launch_band_pack(h->bands, bs, s0, n, h->work));
+                    CHECK(guard_step(h, GK_BACKGROUND, n, n, h->st[0], h->sstride, 1, bs));
                 }
                 return LSRTM_OK;
             }));
@@ -525,6 +556,7 @@ lsrtm_status bg_forward(lsrtm_handle *h, bool hess)
                     a.out = h->st[(n + 1) & 1];
                     CU(launch_fwd2d(a, bs, false, true, hess, h->work));
                     if (h->bands.fmt != BAND_F32) CU(launch_band_pack(h->bands, bs, s0, n, h->work));
+                    CHECK(guard_step(h, GK_BACKGROUND, n, n, a.out, h->sstride, 1, bs));
                 }
                 return LSRTM_OK;
             }));
@@ -571,6 +603,7 @@ lsrtm_status born_core(lsrtm_handle *h)
                     a.trec = h->trv;
                     a.tzc = h->tzc;
                     CU(launch_born3f(a, bs, h->work));
+                    CHECK(guard_step(h, GK_BORN, n, n, a.out, slot_stride(h, 1 - (n & 1)), 2, bs));
                 }
                 return LSRTM_OK;
             }
@@ -581,6 +614,7 @@ lsrtm_status born_core(lsrtm_handle *h)
                 a.in = h->st[n & 1];
                 a.out = h->st[(n + 1) & 1];
                 CU(launch_fwd2d(a, bs, true, false, false, h->work));
+                CHECK(guard_step(h, GK_BORN, n, n, a.out, h->sstride, 2, bs));
             }
             return LSRTM_OK;
         }));
@@ -603,6 +637,7 @@ lsrtm_status model_core(lsrtm_handle *h)
                 for (int n = 0; n < nt; ++n) {
                     a.n = n;
                     CU(launch_fwd3d(a, bs, false, false, 3, h->work));
+                    CHECK(guard_step(h, GK_MODELLING, n, n, h->st[0], h->sstride, 1, bs));
                 }
                 return LSRTM_OK;
             }
@@ -614,6 +649,7 @@ lsrtm_status model_core(lsrtm_handle *h)
                 a.in = h->st[n & 1];
                 a.out = h->st[(n + 1) & 1];
                 CU(launch_fwd2d(a, bs, false, false, false, h->work));
+                CHECK(guard_step(h, GK_MODELLING, n, n, a.out, h->sstride, 1, bs));
             }
             return LSRTM_OK;
         }));
@@ -666,6 +702,7 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
                 if (n % K == 0) CHECK(ck_copy(h, n / K, h->st[0], h->sstride, 10, 0, bs, true));
                 if (n + 1 < nt) {
                     CU(launch_fwd3d(a, bs, false, hess, 3, h->work));
+                    CHECK(guard_step(h, GK_BACKGROUND, n, n, h->st[0], h->sstride, 1, bs));
                     continue;
                 }
                 CU(launch_fwd3d(a, bs, false, hess, 1, h->work));
@@ -690,6 +727,7 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
                     CHECK(ck_copy(h, n / K, h->psiv, h->vstride, 2, 5, bs, true));
                 }
                 CU(launch_fwd2d(a, bs, false, false, hess, h->work));
+                CHECK(guard_step(h, GK_BACKGROUND, n, n, a.out, h->sstride, 1, bs));
             }
             return LSRTM_OK;
         }));
@@ -740,6 +778,7 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
                 a.n = n;
                 CU(launch_fwd3d(a, bs, true, false, 3, h->work));
                 if (pack) CU(launch_band_pack(sb, bs, s0, n, h->work));
+                CHECK(guard_step(h, GK_RECOMPUTE, n, n, a.st, a.sstride, 1, bs));
             }
             return LSRTM_OK;
         }
@@ -756,6 +795,7 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
             a.out = h->rec[(n + 1) & 1];
             CU(launch_fwd2d(a, bs, false, true, false, h->work));
             if (pack) CU(launch_band_pack(sb, bs, s0, n, h->work));
+            CHECK(guard_step(h, GK_RECOMPUTE, n, n, a.out, a.sstride, 1, bs));
         }
         return LSRTM_OK;
     });
@@ -774,7 +814,11 @@ lsrtm_status ck_reverse(lsrtm_handle *h, int s0, int bs, int j)
     const bool d3 = is3d(h);
     return run_loop_n(h, G_SEG + 2 * j + 1, 2, s0, bs, r, r, [&]() -> lsrtm_status {
         if (d3) {
-            for (int n = hi; n >= lo; --n) CHECK(adj3f_step(h, nt - 1 - n, n, s0, sb));
+            for (int n = hi; n >= lo; --n) {
+                CHECK(adj3f_step(h, nt - 1 - n, n, s0, sb));
+                const int o = 1 - ((nt - 1 - n) & 1);
+                CHECK(guard_step(h, GK_MIGRATION, nt - 1 - n, n, h->st[o], slot_stride(h, o), 2, bs));
+            }
             return LSRTM_OK;
         }
         Step2D a = step_args(h, s0);
@@ -785,6 +829,7 @@ lsrtm_status ck_reverse(lsrtm_handle *h, int s0, int bs, int j)
             a.in = h->st[i & 1];
             a.out = h->st[(i + 1) & 1];
             CU(launch_adj2d(a, bs, h->work));
+            CHECK(guard_step(h, GK_MIGRATION, nt - 1 - n, n, a.out, h->sstride, 2, bs));
         }
         return LSRTM_OK;
     });
@@ -858,7 +903,11 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
         if (is3d(h)) {
             CHECK(adj3f_start(h, s0, s0, bs));
             CHECK(run_loop(h, G_ADJ, s0, bs, [&]() -> lsrtm_status {
-                for (int i = 0; i < nt; ++i) CHECK(adj3f_step(h, i, nt - 1 - i, s0, h->bands));
+                for (int i = 0; i < nt; ++i) {
+                    CHECK(adj3f_step(h, i, nt - 1 - i, s0, h->bands));
+                    const int o = 1 - (i & 1);
+                    CHECK(guard_step(h, GK_MIGRATION, i, nt - 1 - i, h->st[o], slot_stride(h, o), 2, bs));
+                }
                 return LSRTM_OK;
             }));
             CU(launch_image_accumulate(h->gm, h->g, h->img, bs, s0, nullptr, nullptr, h->img_acc, h->work));
@@ -876,6 +925,7 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
                     a.in = h->st[i & 1];
                     a.out = h->st[(i + 1) & 1];
                     CU(launch_adj2d(a, bs, h->work));
+                    CHECK(guard_step(h, GK_MIGRATION, i, nt - 1 - i, a.out, h->sstride, 2, bs));
                 }
                 return LSRTM_OK;
             }));
@@ -1186,17 +1236,29 @@ lsrtm_status adj3f_start(lsrtm_handle *h, int fs0, int s0, int bs)
     return LSRTM_OK;
 }
 
-// Reads and clears the fused kernels' error word (synchronises the work stream).
+// Reads and clears the device error words (synchronises the work stream):
+// the fused kernels' tile-copy word and the non-finite guard word.
 lsrtm_status check_kernel_error(lsrtm_handle *h)
 {
     if (!h->kerr) return LSRTM_OK;
-    int e = 0;
-    CU(cudaMemcpyAsync(&e, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->work));
+    int e[2] = {0, 0};
+    CU(cudaMemcpyAsync(e, h->kerr, sizeof(e), cudaMemcpyDeviceToHost, h->work));
     CU(cudaStreamSynchronize(h->work));
-    if (!e) return LSRTM_OK;
-    CU(cudaMemsetAsync(h->kerr, 0, sizeof(int), h->work));
-    return fail(LSRTM_ERR_CUDA, (e & 2) ? "a fused 3D kernel refused a misaligned tile copy"
-                                        : "a fused 3D kernel gave up waiting for its tile copies");
+    if (!e[0] && !e[1]) return LSRTM_OK;
+    CU(cudaMemsetAsync(h->kerr, 0, sizeof(e), h->work));
+    CU(cudaStreamSynchronize(h->work));
+    if (e[0])
+        return fail(LSRTM_ERR_CUDA, (e[0] & 2) ? "a fused 3D kernel refused a misaligned tile copy"
+                                               : "a fused 3D kernel gave up waiting for its tile copies");
+    const int kind = e[1] >> 24, n = (e[1] & 0xFFFFFF) - 1;
+    if (kind == GK_CG)
+        return fail(LSRTM_ERR_NONFINITE, "non-finite CG scalar (<q,q>, gamma or <r,r>) at iteration " +
+                                             std::to_string(n));
+    static const char *names[] = {"?", "background", "Born", "migration", "nonlinear modelling",
+                                  "checkpoint recomputation"};
+    return fail(LSRTM_ERR_NONFINITE, std::string("non-finite wavefield in the ") +
+                                         names[kind >= 1 && kind <= 5 ? kind : 0] + " time loop at step " +
+                                         std::to_string(n) + "; the rest of the loop was skipped");
 }
 
 int geo_nshot(const lsrtm_geometry *geo) { return geo && geo->nshot > 0 ? geo->nshot : 1; }
@@ -1476,6 +1538,10 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     CHECK(dalloc_t(h, &h->img, (size_t)batch * g.plane));
     CHECK(dalloc_t(h, &h->hess, (size_t)batch * g.plane));
     CHECK(dalloc_t(h, &h->kerr, 4));
+    h->guard_K = cfg->guard_interval < 0 ? 0 : (cfg->guard_interval ? cfg->guard_interval : kGuardInterval);
+    h->g.abort = h->kerr + 1;
+    CU(cudaMallocHost(reinterpret_cast<void **>(&h->poll_h), 4 * sizeof(int)));
+    for (cudaEvent_t &e : h->poll_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (d3) CHECK(setup_fused3d(h));
     CU(cudaStreamSynchronize(h->work));
     return LSRTM_OK;
@@ -1697,7 +1763,8 @@ lsrtm_status cg_begin_impl(lsrtm_handle *h, const float *d, const float *x0, int
     CU(launch_scale_copy(h->cg_p, h->cg_z, nm, s));
     CU(launch_dot(h->cg_s, h->cg_z, nm, gamma, h->dotwork, s));
     CU(launch_dot(h->cg_r, h->cg_r, nd, h->scal + 6, h->dotwork, s));
-    h->launches += 10;
+    CU(launch_guard_scalars(h->scal, 7, h->kerr + 1, guard_code(GK_CG, 0), s));
+    h->launches += 11;
     h->cg_active = true;
     return LSRTM_OK;
 }
@@ -1732,7 +1799,22 @@ lsrtm_status cg_iterate_impl(lsrtm_handle *h, int niter)
         CU(cudaMemcpyAsync(gamma, gnew, sizeof(double), cudaMemcpyDeviceToDevice, s));
         h->cg_iter++;
         CU(launch_dot(h->cg_r, h->cg_r, nd, h->mis_dev + h->cg_iter, h->dotwork, s));
-        h->launches += 16;
+        // the iteration's FP64 scalars: <q,q>, gamma, <d,d> and <r,r>
+        CU(launch_guard_scalars(h->scal, 7, h->kerr + 1, guard_code(GK_CG, h->cg_iter), s));
+        CU(launch_guard_scalars(h->mis_dev + h->cg_iter, 1, h->kerr + 1, guard_code(GK_CG, h->cg_iter), s));
+        h->launches += 18;
+        // Poll the error words without draining the queue: copy this
+        // iteration's words to pinned memory, then wait for the copy of the
+        // previous iteration while this one runs. A tripped guard ends the
+        // solve here (the queued iteration's time loops return at once).
+        int *ph = h->poll_h + 2 * (k & 1);
+        CU(cudaMemcpyAsync(ph, h->kerr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecord(h->poll_ev[k & 1], s));
+        if (k > 0) {
+            const int j = (k - 1) & 1;
+            CU(cudaEventSynchronize(h->poll_ev[j]));
+            if (h->poll_h[2 * j] || h->poll_h[2 * j + 1]) return check_kernel_error(h);
+        }
     }
     return LSRTM_OK;
 }
@@ -1776,7 +1858,7 @@ lsrtm_status lsrtm_cg_iterate(lsrtm_handle *h, int niter, double *misfit)
     CHECK(begin_call(h));
     int first = h->cg_iter + 1;
     CHECK(cg_iterate_impl(h, niter));
-    CHECK(end_call(h, false));
+    CHECK(end_call(h, misfit != nullptr));   // reading the misfits synchronises anyway
     if (misfit && niter > 0) CHECK(read_misfits(h, first, niter, misfit));
     return LSRTM_OK;
 }
@@ -2167,6 +2249,7 @@ lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms
     // graphs captured with the previous chunking are stale
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
+    h->graph_guards.clear();
     h->bg_cached = false;
     if (st != LSRTM_OK) return st;
     if (tzc_out) *tzc_out = best_tzc;
@@ -2211,6 +2294,9 @@ void lsrtm_destroy(lsrtm_handle *h)
     }
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     for (void *p : h->allocs) cudaFree(p);
+    if (h->poll_h) cudaFreeHost(h->poll_h);
+    for (cudaEvent_t e : h->poll_ev)
+        if (e) cudaEventDestroy(e);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->work) cudaStreamDestroy(h->work);

@@ -267,6 +267,7 @@ __device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
 template <int M, bool BORN, bool BANDS, bool HESS, bool WIN, bool FS>
 __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
 {
+    if (guard_tripped(a.g)) return;
     using C = Cols<M>;
     using T = typename FwdT<BORN>::T;
     using R = typename FwdT<BORN>::R;
@@ -614,6 +615,7 @@ __device__ __forceinline__ AdjRow adj_read(const float *st)
 template <int M, bool WIN, bool FS>
 __global__ void __launch_bounds__(NTH, FS ? kAdjMinBlocksFS : kAdjMinBlocks) k_adj2d(const Step2D a)
 {
+    if (guard_tripped(a.g)) return;
     using C = Cols<M>;
     constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
     __shared__ float2 sPU[NTH];   // (p^n, kdt*lp - ai_x (lpsi_vx - kdt*lp)), row z

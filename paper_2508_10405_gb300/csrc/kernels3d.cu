@@ -114,6 +114,7 @@ __device__ __forceinline__ bool pml_node(const GridDev &g, int d, int i)
 template <int M, bool BANDS, bool HESS>
 __global__ void __launch_bounds__(256) k3_v(const Step3D a)
 {
+    if (guard_tripped(a.g)) return;
     const GridDev &g = a.g;
     const Cell c = cell_of(g);
     if (!c.ok) return;
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(256) k3_v(const Step3D a)
 template <int M, bool BANDS, bool HESS>
 __global__ void __launch_bounds__(256) k3_p(const Step3D a)
 {
+    if (guard_tripped(a.g)) return;
     const GridDev &g = a.g;
     const Cell c = cell_of(g);
     if (!c.ok) return;

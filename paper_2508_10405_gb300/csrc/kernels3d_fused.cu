@@ -209,6 +209,7 @@ __device__ __forceinline__ void born_issue(const Step3F &a, unsigned char *st, u
 template <int M>
 __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_born(const __grid_constant__ Step3F a)
 {
+    if (guard_tripped(a.g)) return;
     using G = Geo<M>;
     using S = BornSmem<M>;
     constexpr int W = G::W;
@@ -566,6 +567,7 @@ __device__ __forceinline__ void adj_issue(const Adj3F &a, unsigned char *st, uin
 template <int M>
 __global__ void __launch_bounds__(NTH, kMinBlocks) k3f_adj(const __grid_constant__ Adj3F a)
 {
+    if (guard_tripped(a.g)) return;
     using G = Geo<M>;
     using S = AdjSmem<M>;
     constexpr int W = G::W;

@@ -290,6 +290,34 @@ __global__ void k_nonfinite(const float *x, long long n, int *flag)
     if (bad && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// Non-finite guard over the first count4 float4s of each slot (blockIdx.y):
+// a float is NaN or Inf exactly when its eight exponent bits are all ones.
+// A tripped word is left as it is (the first detection names the step).
+__global__ void k_guard_state(const float4 *x, long long stride4, long long count4, int *word, int code)
+{
+    __shared__ int tripped;
+    if (threadIdx.x == 0) tripped = *reinterpret_cast<volatile int *>(word);
+    __syncthreads();
+    if (tripped) return;
+    const float4 *xs = x + blockIdx.y * stride4;
+    unsigned bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = xs[i];
+        const unsigned e = 0x7f800000u;
+        bad |= ((__float_as_uint(v.x) & e) == e) | ((__float_as_uint(v.y) & e) == e) |
+               ((__float_as_uint(v.z) & e) == e) | ((__float_as_uint(v.w) & e) == e);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(word, 0, code);
+}
+
+__global__ void k_guard_scalars(const double *v, int n, int *word, int code)
+{
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bad |= !isfinite(v[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(word, 0, code);
+}
+
 // out[r][n] = mask(r, n) (dobs[r][n] - dsyn[r][n]). The direct-wave mute of
 // receiver r is 0 before sample n0[r] (the first sample after the mute time,
 // decided in FP64 on the host), then the raised-cosine rise
@@ -507,6 +535,24 @@ cudaError_t launch_mute_residual(const float *dobs, const float *dsyn, const int
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s)
 {
     k_nonfinite<<<grid_for(n), NT, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guard_state(const float *base, long long stride, long long count, int nslots, int *word,
+                               int code, cudaStream_t s)
+{
+    if (nslots <= 0 || count <= 0) return cudaSuccess;
+    const long long count4 = count / 4;
+    // about four CTAs per SM over all slots
+    const int gx = (int)std::max(1LL, std::min((count4 + NT - 1) / NT, (long long)std::max(1, 608 / nslots)));
+    k_guard_state<<<dim3(gx, nslots), NT, 0, s>>>(reinterpret_cast<const float4 *>(base), stride / 4, count4, word,
+                                                   code);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guard_scalars(const double *v, int n, int *word, int code, cudaStream_t s)
+{
+    k_guard_scalars<<<1, 32, 0, s>>>(v, n, word, code);
     return cudaGetLastError();
 }
 

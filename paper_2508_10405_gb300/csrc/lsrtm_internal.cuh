@@ -27,7 +27,21 @@ struct GridDev {
     float dt;
     int nt;
     int fs;                // free surface on row z0 (method of images; see lsrtm_config)
+    const int *abort;      // non-finite guard word (or null): when nonzero, the
+                           // time-step kernels return at once, so the rest of a
+                           // tripped time loop costs only its launches
 };
+
+// The guard checks the pressure planes of every slot every guard_interval
+// time steps of a loop (kGuardInterval when the configuration gives 0).
+constexpr int kGuardInterval = 64;
+// Guard codes: (loop kind << 24) | (time step or CG iteration + 1).
+enum GuardKind { GK_BACKGROUND = 1, GK_BORN = 2, GK_MIGRATION = 3, GK_MODELLING = 4, GK_RECOMPUTE = 5,
+                 GK_CG = 6 };
+__host__ __device__ inline int guard_code(int kind, int n) { return (kind << 24) | ((n + 1) & 0xFFFFFF); }
+#ifdef __CUDACC__
+__device__ __forceinline__ bool guard_tripped(const GridDev &g) { return g.abort && *g.abort; }
+#endif
 
 // Free surface: the padded row a ghost node row r < z0 mirrors (p odd about
 // z0), and the half row a ghost half row k < z0 mirrors (v_z even).
@@ -310,6 +324,13 @@ cudaError_t launch_hess_finalize(const GridDev &g, const double *acc, float *out
                                  cudaStream_t s);
 cudaError_t launch_max_abs_reduce(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaStream_t s);
+// Non-finite guard: sets *word to `code` (unless already set) if one of the
+// first `count` floats of any of `nslots` slots (slot stride `stride` floats;
+// base, count and stride multiples of 4 floats) is NaN or Inf.
+cudaError_t launch_guard_state(const float *base, long long stride, long long count, int nslots, int *word,
+                               int code, cudaStream_t s);
+// The same for n FP64 scalars.
+cudaError_t launch_guard_scalars(const double *v, int n, int *word, int code, cudaStream_t s);
 // Muted data residual: out = mute(r, n) fo[r] (dobs - dsyn), dsyn nullable; the
 // mute is 0 for n < n0[r], then (1 - cos(pi v)) / 2 with v = (n - n0[r]) b + a0[r]
 // (1 for v >= 1 or b = 0).
