@@ -99,6 +99,12 @@ typedef struct {
                                 LSRTM_ERR_NONFINITE naming the loop and the step. CGNR
                                 also checks its FP64 scalars every iteration and polls the
                                 word one iteration behind. 0 = 64; < 0 = no wavefield checks. */
+    int checkpoint_precision; /* storage of the checkpointed background states (checkpoint
+                                reconstruction): LSRTM_BAND_FP32 (default; the images then equal
+                                the boundary mode's bit for bit), LSRTM_BAND_BF16 or
+                                LSRTM_BAND_FP16 with one FP32 scale per state plane per shot per
+                                snapshot (values / (max|plane| / 2^15)), which halves the
+                                checkpoint memory; the plain plan always stores FP32. */
 } lsrtm_config;
 
 typedef struct {
@@ -378,16 +384,17 @@ lsrtm_status lsrtm_psf_cg(lsrtm_handle *h, const float *psf_vp, const float *psf
 /* Bytes of device workspace the handle holds. */
 size_t lsrtm_workspace_bytes(const lsrtm_handle *h);
 
-/* Autotuner of the 2D time-step kernels (no counterpart in the paper). A CTA
- * of the 2D kernels owns a fixed number of x-columns and marches down a
- * chunk of tzc padded rows; more chunks give more CTAs per shot but repeat
- * 2M warm-up rows per chunk. The tuner times `steps` Born and migration steps
+/* Autotuner of the Born and migration time-step kernels (no counterpart in
+ * the paper). A CTA of the 2D kernels owns a fixed number of x-columns, one
+ * of the fused 3D kernels a fixed (x, y) tile, and marches down a chunk of
+ * tzc padded rows; more chunks give more CTAs per shot but repeat 2M
+ * warm-up rows per chunk. The tuner times `steps` Born and migration steps
  * (0: 16) on the first batch for every split of the padded depth into 1..12
  * chunks of at least 2M + 8 rows (and the current one), keeps the fastest
  * and rebuilds the receiver tiling; results do not depend on the choice
  * (every cell is computed the same way). Captured graphs and the cached
  * background are dropped. Outputs (each may be NULL):
- *   *tzc      chosen rows per chunk (0 for 3D handles, which have none)
+ *   *tzc      chosen rows per chunk
  *   ms        [2*ncand] pairs (tzc, ms per Born + migration step); room for
  *             at least 2*13 doubles
  *   *ncand    number of candidates timed

@@ -50,6 +50,7 @@ class Config(ctypes.Structure):
         ("recon_mode", ctypes.c_int), ("plan", ctypes.c_int), ("shots_per_batch", ctypes.c_int),
         ("wavelet_per_shot", ctypes.c_int), ("checkpoint_interval", ctypes.c_int),
         ("free_surface", ctypes.c_int), ("guard_interval", ctypes.c_int),
+        ("checkpoint_precision", ctypes.c_int),
     ]
 
 
@@ -165,7 +166,7 @@ class Lsrtm:
                  vp, rho, wavelet, src_idx, rec_ptr, rec_idx, win_x0=None, win_nx=None, pml_vmax=None,
                  band_precision=BAND_FP32, hbm_budget_bytes=0, recon_mode=RECON_AUTO,
                  plan=PLAN_BATCHED, shots_per_batch=0, checkpoint_interval=0, free_surface=False,
-                 guard_interval=0, stream=None):
+                 guard_interval=0, checkpoint_precision=BAND_FP32, stream=None):
         import torch
         self._lib = load_library()
         self._h = ctypes.c_void_p()
@@ -178,7 +179,7 @@ class Lsrtm:
                           fd_order, npml, f0, float(pml_vmax), band_precision,
                           int(hbm_budget_bytes), recon_mode, plan, shots_per_batch,
                           1 if np.ndim(wavelet) == 2 else 0, int(checkpoint_interval), int(bool(free_surface)),
-                          int(guard_interval))
+                          int(guard_interval), int(checkpoint_precision))
         self._src = np.ascontiguousarray(src_idx, dtype=np.int32)
         self._rp = np.ascontiguousarray(rec_ptr, dtype=np.int32)
         self._ri = np.ascontiguousarray(rec_idx, dtype=np.int32)

@@ -104,6 +104,8 @@ struct lsrtm_handle {
     long long sstride1 = 0;      // slot stride of st[1] (3D: the fused kernels' pong buffer)
     Step3F f3born[2];            // fused 3D Born step arguments reading st[0] / st[1]
     Adj3F f3adj[2];              // fused 3D adjoint step arguments reading st[0] / st[1]
+    Maps2D m2d[2];             // 2D TMA row maps reading st[0] / st[1]
+    bool tma2d = false;          // the 2D Born and migration kernels stage rows by TMA (no aperture windows)
     int *kerr = nullptr;         // device error words: [0] fused-kernel tile copies, [1] non-finite guard
     int guard_K = 0;             // time steps between non-finite guard checks (0: off)
     long long guard_count = 0;   // guard launches queued or captured so far
@@ -128,7 +130,9 @@ struct lsrtm_handle {
     int ck_K = 0, ck_nseg = 0, ck_planes = 0;
     float *rec[2] = {nullptr, nullptr};   // background state for the recomputation
     float *rec_psiv = nullptr;
-    float *ck_mem = nullptr;              // [nseg][batch][ck_planes][plane]
+    void *ck_mem = nullptr;               // [nseg][batch][ck_planes][plane], FP32 or 16-bit
+    int ck_fmt = BAND_F32;                // BandFmt of the checkpoints
+    float *ck_amax = nullptr;             // 16-bit checkpoints: [nseg][batch][ck_planes] plane maxima
     Bands segbands{};                     // bands of one segment of one batch
     // staging
     float *dstage = nullptr;     // [nrec_total][nt]
@@ -327,6 +331,7 @@ Step2D step_args(lsrtm_handle *h, int shot0)
     a.tzc = h->tzc;
     a.win_nx = h->win ? h->win_nx_d : nullptr;
     a.pml_xstride = h->win ? h->g.Nx : 0;
+    a.err = h->kerr;
     return a;
 }
 
@@ -496,6 +501,9 @@ lsrtm_status guard_step(lsrtm_handle *h, int kind, int i, int n, const float *st
     return LSRTM_OK;
 }
 
+// TMA row maps of the 2D migration reading state buffer j, or null.
+const Maps2D *maps2_of(const lsrtm_handle *h, int j) { return h->tma2d ? &h->m2d[j] : nullptr; }
+
 // Slot stride of state buffer j (3D: the fused kernels' ping and pong differ).
 long long slot_stride(const lsrtm_handle *h, int j) { return j ? h->sstride1 : h->sstride; }
 
@@ -613,7 +621,7 @@ lsrtm_status born_core(lsrtm_handle *h)
                 a.n = n;
                 a.in = h->st[n & 1];
                 a.out = h->st[(n + 1) & 1];
-                CU(launch_fwd2d(a, bs, true, false, false, h->work));
+                CU(launch_fwd2d(a, bs, true, false, false, h->work, maps2_of(h, n & 1)));
                 CHECK(guard_step(h, GK_BORN, n, n, a.out, h->sstride, 2, bs));
             }
             return LSRTM_OK;
@@ -666,15 +674,31 @@ lsrtm_status model_core(lsrtm_handle *h)
 // same bits), and runs the reverse steps that read those bands.
 // ---------------------------------------------------------------------------
 
-float *ck_slot_base(lsrtm_handle *h, int j) { return h->ck_mem + (size_t)j * h->batch * h->ck_planes * h->g.plane; }
+size_t ck_esize(const lsrtm_handle *h) { return h->ck_fmt == BAND_F32 ? sizeof(float) : 2; }
+
+char *ck_slot_base(lsrtm_handle *h, int j)
+{
+    return static_cast<char *>(h->ck_mem) + (size_t)j * h->batch * h->ck_planes * h->g.plane * ck_esize(h);
+}
 
 // Copies `planes` contiguous planes of each of bs slots (slot stride sstride
-// floats) into, or out of, planes [p0, p0 + planes) of checkpoint j.
+// floats) into, or out of, planes [p0, p0 + planes) of checkpoint j: FP32
+// as they are, 16-bit with one scale per slot and plane (k_ck_pack).
 lsrtm_status ck_copy(lsrtm_handle *h, int j, float *slots, long long sstride, int planes, int p0, int bs,
                      bool save)
 {
+    if (h->ck_fmt != BAND_F32) {
+        float *amax = h->ck_amax + (size_t)j * h->batch * h->ck_planes;
+        if (save)
+            CU(launch_ck_pack(slots, sstride, h->g.plane, planes, p0, bs, h->ck_planes, h->ck_fmt, ck_slot_base(h, j),
+                              amax, h->work));
+        else
+            CU(launch_ck_unpack(slots, sstride, h->g.plane, planes, p0, bs, h->ck_planes, h->ck_fmt,
+                                ck_slot_base(h, j), amax, h->work));
+        return LSRTM_OK;
+    }
     const size_t fb = (size_t)h->g.plane * sizeof(float);
-    float *ck = ck_slot_base(h, j) + (size_t)p0 * h->g.plane;
+    float *ck = reinterpret_cast<float *>(ck_slot_base(h, j)) + (size_t)p0 * h->g.plane;
     const size_t ckpitch = (size_t)h->ck_planes * fb, spitch = (size_t)sstride * sizeof(float);
     if (save)
         CU(cudaMemcpy2DAsync(ck, ckpitch, slots, spitch, planes * fb, bs, cudaMemcpyDeviceToDevice, h->work));
@@ -684,6 +708,13 @@ lsrtm_status ck_copy(lsrtm_handle *h, int j, float *slots, long long sstride, in
 }
 
 enum { G_CKF = 4, G_CKF_HESS = 5, G_SEG = 100 };
+
+// Kernel launches of the 16-bit checkpoint saves of one forward pass
+// (calls: ck_copy calls per snapshot; two kernels each).
+long long ck16_launches(const lsrtm_handle *h, int calls)
+{
+    return h->ck_fmt != BAND_F32 ? 2LL * calls * h->ck_nseg : 0;
+}
 
 // Forward background pass of one batch in the main slots: checkpoints every K
 // steps, the final state (p^{nt-1}, v^{nt-1/2}) of each shot of the batch into
@@ -695,7 +726,7 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
     CHECK(zero_slots(h, bs));
     if (hess) CU(cudaMemsetAsync(h->hess, 0, (size_t)bs * plane * sizeof(float), h->work));
     if (is3d(h)) {
-        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, 2LL * nt, nt, [&]() -> lsrtm_status {
+        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, 2LL * nt + ck16_launches(h, 1), nt, [&]() -> lsrtm_status {
             Step3D a = step3_args(h, s0);
             for (int n = 0; n < nt; ++n) {
                 a.n = n;
@@ -716,7 +747,7 @@ lsrtm_status ck_forward(lsrtm_handle *h, int s0, int bs, bool hess)
                              h->sstride * sizeof(float), 3 * plane * sizeof(float), bs, cudaMemcpyDeviceToDevice,
                              h->work));
     } else {
-        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, nt, nt, [&]() -> lsrtm_status {
+        CHECK(run_loop_n(h, hess ? G_CKF_HESS : G_CKF, 1, s0, bs, nt + ck16_launches(h, 2), nt, [&]() -> lsrtm_status {
             Step2D a = step_args(h, s0);
             for (int n = 0; n < nt; ++n) {
                 a.n = n;
@@ -767,7 +798,9 @@ lsrtm_status ck_recompute(lsrtm_handle *h, int s0, int bs, int j)
     sb.t0 = t0;
     const bool d3 = is3d(h);
     const bool pack = sb.fmt != BAND_F32;
-    return run_loop_n(h, G_SEG + 2 * j, 1, s0, bs, (d3 ? 2 * c : c) + (pack ? c : 0), c, [&]() -> lsrtm_status {
+    const long long unpack = h->ck_fmt != BAND_F32 ? (d3 ? 1 : 2) : 0;   // 16-bit checkpoint restores
+    return run_loop_n(h, G_SEG + 2 * j, 1, s0, bs, (d3 ? 2 * c : c) + (pack ? c : 0) + unpack, c,
+                      [&]() -> lsrtm_status {
         if (d3) {
             CHECK(ck_copy(h, j, h->rec[0], 10 * plane, 10, 0, bs, false));
             Step3D a = step3_args(h, s0);
@@ -828,7 +861,7 @@ lsrtm_status ck_reverse(lsrtm_handle *h, int s0, int bs, int j)
             a.n = n;
             a.in = h->st[i & 1];
             a.out = h->st[(i + 1) & 1];
-            CU(launch_adj2d(a, bs, h->work));
+            CU(launch_adj2d(a, maps2_of(h, i & 1), bs, h->work));
             CHECK(guard_step(h, GK_MIGRATION, nt - 1 - n, n, a.out, h->sstride, 2, bs));
         }
         return LSRTM_OK;
@@ -924,7 +957,7 @@ lsrtm_status adjoint_core(lsrtm_handle *h, float *gout, bool want_hess)
                     a.n = nt - 1 - i;
                     a.in = h->st[i & 1];
                     a.out = h->st[(i + 1) & 1];
-                    CU(launch_adj2d(a, bs, h->work));
+                    CU(launch_adj2d(a, maps2_of(h, i & 1), bs, h->work));
                     CHECK(guard_step(h, GK_MIGRATION, i, nt - 1 - i, a.out, h->sstride, 2, bs));
                 }
                 return LSRTM_OK;
@@ -970,6 +1003,9 @@ lsrtm_status validate_cfg(const lsrtm_config *c)
     if (c->band_precision != LSRTM_BAND_FP32 && c->band_precision != LSRTM_BAND_BF16 &&
         c->band_precision != LSRTM_BAND_FP16)
         return fail(LSRTM_ERR_ARG, "band_precision must be 0 (fp32), 1 (bf16) or 2 (fp16)");
+    if (c->checkpoint_precision != LSRTM_BAND_FP32 && c->checkpoint_precision != LSRTM_BAND_BF16 &&
+        c->checkpoint_precision != LSRTM_BAND_FP16)
+        return fail(LSRTM_ERR_ARG, "checkpoint_precision must be 0 (fp32), 1 (bf16) or 2 (fp16)");
     if (c->recon_mode != LSRTM_RECON_BOUNDARY && c->recon_mode != LSRTM_RECON_CHECKPOINT &&
         c->recon_mode != LSRTM_RECON_AUTO)
         return fail(LSRTM_ERR_ARG, "recon_mode must be 0 (boundary), 1 (checkpoint) or 2 (auto)");
@@ -1484,8 +1520,13 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         // checkpoint: the background planes of a forward state (2D: p vx vz psi_px
         // psi_pz + the two node CPML memories; 3D: p, v, psi_p, psi_v)
         h->ck_planes = d3 ? 10 : 7;
+        h->ck_fmt = cfg->plan == LSRTM_PLAN_PLAIN ? BAND_F32
+                    : (cfg->checkpoint_precision == LSRTM_BAND_BF16 ? BAND_BF16S
+                                                                    : (cfg->checkpoint_precision == LSRTM_BAND_FP16
+                                                                           ? BAND_F16S
+                                                                           : BAND_F32));
         const double seg_step = 2.0 * (double)h->bands.nb * esz;           // band bytes per step
-        const double ck_one = (double)h->ck_planes * fbytes;               // bytes per checkpoint
+        const double ck_one = (double)h->ck_planes * g.plane * ck_esize(h) + h->ck_planes * sizeof(float);
         int K = cfg->checkpoint_interval > 0
                     ? cfg->checkpoint_interval
                     : (int)std::lround(std::sqrt((double)g.nt * ck_one / seg_step));
@@ -1494,7 +1535,7 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         h->ck_nseg = (g.nt + K - 1) / K;
         // recomputation state: 2D 5 + 5 ping-pong planes and 2 CPML planes; 3D 10 in place
         size_t rec_slot = (d3 ? 10 : 12) * fbytes;
-        size_t ck_slot = (size_t)h->ck_nseg * h->ck_planes * fbytes + (size_t)K * (size_t)seg_step +
+        size_t ck_slot = (size_t)h->ck_nseg * (size_t)ck_one + (size_t)K * (size_t)seg_step +
                          rec_slot + h->fs_planes * fbytes +
                          (h->bands.fmt != BAND_F32 ? 2 * (size_t)K * sizeof(float) : 0);
         per_slot += ck_slot;
@@ -1518,7 +1559,8 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
         h->bands = h->segbands;
         h->bands.shot0 = 0;
         h->bands.t0 = 0;
-        CHECK(dalloc_t(h, &h->ck_mem, (size_t)h->ck_nseg * batch * h->ck_planes * g.plane));
+        CHECK(dalloc(h, &h->ck_mem, (size_t)h->ck_nseg * batch * h->ck_planes * g.plane * ck_esize(h)));
+        if (h->ck_fmt != BAND_F32) CHECK(dalloc_t(h, &h->ck_amax, (size_t)h->ck_nseg * batch * h->ck_planes));
         CHECK(dalloc_t(h, &h->final_state, (size_t)batch * h->fs_planes * g.plane));
         if (d3) {
             CHECK(dalloc_t(h, &h->rec[0], (size_t)batch * 10 * g.plane));
@@ -1543,6 +1585,14 @@ lsrtm_status create_impl(const lsrtm_config *cfg, const float *vp, const float *
     CU(cudaMallocHost(reinterpret_cast<void **>(&h->poll_h), 4 * sizeof(int)));
     for (cudaEvent_t &e : h->poll_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (d3) CHECK(setup_fused3d(h));
+    else if (!h->win) {
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = maps2d(&h->m2d[b], h->g, h->st[b], h->sstride, h->kdt, h->binv, h->kd2, h->br2, h->img,
+                                   batch);
+            if (e != cudaSuccess) return fail(LSRTM_ERR_CUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
+        }
+        h->tma2d = true;
+    }
     CU(cudaStreamSynchronize(h->work));
     return LSRTM_OK;
 }
@@ -1763,6 +1813,9 @@ lsrtm_status cg_begin_impl(lsrtm_handle *h, const float *d, const float *x0, int
     CU(launch_scale_copy(h->cg_p, h->cg_z, nm, s));
     CU(launch_dot(h->cg_s, h->cg_z, nm, gamma, h->dotwork, s));
     CU(launch_dot(h->cg_r, h->cg_r, nd, h->scal + 6, h->dotwork, s));
+    // gamma_new and <q,q> of an earlier solve are not this solve's: clear them
+    // before the guard reads the scalars
+    CU(cudaMemsetAsync(h->scal + 1, 0, 2 * sizeof(double), s));
     CU(launch_guard_scalars(h->scal, 7, h->kerr + 1, guard_code(GK_CG, 0), s));
     h->launches += 11;
     h->cg_active = true;
@@ -2182,12 +2235,8 @@ lsrtm_status lsrtm_psf_cg(lsrtm_handle *h, const float *psf_vp, const float *psf
 lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms_out, int *ncand_out)
 {
     if (!h) return fail(LSRTM_ERR_ARG, "null handle");
-    if (h->g.ndim != 2) {   // the 3D kernels have no z-chunk to choose
-        if (tzc_out) *tzc_out = 0;
-        if (ncand_out) *ncand_out = 0;
-        return LSRTM_OK;
-    }
     CHECK(begin_call(h));
+    const bool d3 = is3d(h);
     const GridDev &g = h->g;
     // candidates: the padded depth split into 1..12 chunks of at least 2M + 8 rows
     std::vector<int> cand;
@@ -2218,12 +2267,22 @@ lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms
         for (int rep = 0; rep < 2 && st == LSRTM_OK; ++rep) {   // first pass warms up
             cudaEventRecord(e0, h->work);
             for (int i = 0; i < steps; ++i) {
+                if (d3) {
+                    Step3F &b = h->f3born[i & 1];
+                    b.n = i;
+                    b.shot0 = 0;
+                    b.trec = h->trv;
+                    b.tzc = c;
+                    launch_born3f(b, bs, h->work);
+                    adj3f_step(h, i, steps - i, 0, h->bands);
+                    continue;
+                }
                 a.n = i;
                 a.in = h->st[i & 1];
                 a.out = h->st[(i + 1) & 1];
-                launch_fwd2d(a, bs, true, false, false, h->work);
+                launch_fwd2d(a, bs, true, false, false, h->work, maps2_of(h, i & 1));
                 a.n = steps - i;
-                launch_adj2d(a, bs, h->work);
+                launch_adj2d(a, maps2_of(h, i & 1), bs, h->work);
             }
             cudaEventRecord(e1, h->work);
             cudaError_t e = cudaEventSynchronize(e1);
@@ -2235,6 +2294,7 @@ lsrtm_status lsrtm_autotune(lsrtm_handle *h, int steps, int *tzc_out, double *ms
         }
         h->launches += 4LL * steps;
         times.push_back(ms);
+        if (d3 && st == LSRTM_OK) st = check_kernel_error(h);   // a fused kernel's wait that gave up
         if (st != LSRTM_OK) break;
         if (ms < best) {
             best = ms;

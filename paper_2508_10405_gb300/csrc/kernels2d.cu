@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "lsrtm_internal.cuh"
+#include "tma.cuh"
 
 namespace lsrtm {
 namespace {
@@ -514,6 +515,278 @@ __global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
 }
 
 // ---------------------------------------------------------------------------
+// Born step with TMA row staging (shots without aperture windows): k_fwd2d's
+// Born arithmetic in the same order, with the rows ahead staged as in
+// k_adj2t (one thread issues each field row of a stage as one tile copy on
+// the stage's mbarrier; zero fill outside the grid; unused fields not copied;
+// a stage is refilled only after a barrier that follows every read of it).
+// ---------------------------------------------------------------------------
+struct Fwd2T {
+    Step2D a;
+    Maps2D m;
+};
+
+constexpr unsigned kFwdStageBytesT = (unsigned)kFwdStageSlotBytes;
+static_assert(kFwdStageBytesT % 128 == 0, "stage rows stay 128-byte aligned");
+constexpr unsigned kFwdBarOff = PDF * kFwdStageBytesT;
+constexpr unsigned kFwdSmemT = kFwdBarOff + 64 + 128;   // stages, barriers, alignment slack
+
+// Issues the copies of row z (the stage layout of fwd_issue) on barrier b;
+// tph: the CTA has half-node CPML columns.
+template <int M, bool FS>
+__device__ __forceinline__ void fwd_issue_tma(const Fwd2T &p, char *st, uint64_t *b, int slot, int xs, int z,
+                                              int zc0, int zc1, bool tph)
+{
+    const GridDev &g = p.a.g;
+    const Maps2D &m = p.m;
+    constexpr int W = 2 * M;
+    constexpr unsigned F = NTH * 8;   // bytes of one field row
+    const int zr = z + W - 1, k = z + M - 1;
+    const int qp = slot * m.pps;
+    const bool ink = k >= 0 && k < g.Nz;
+    int rp = zr, rvz = ink ? k : -1;
+    if constexpr (FS) {
+        const int zrs = node_src_row<FS>(g, zr), ks = half_src_row<FS>(g, k);
+        rp = (zrs >= 0 && zrs < g.Nz) ? zrs : -1;
+        rvz = (ink && ks < g.Nz) ? ks : -1;
+    }
+    const int rb1 = k + 1 >= 0 ? min(k + 1, g.Nz - 1) : -1;
+    const bool pz = ink && ((k <= g.z0 - 2) || (k >= g.z0 + g.nz));
+    const bool main = z >= zc0 && z < zc1;
+    const bool px = main && tph;
+    const unsigned bytes = (3 + (pz ? 1 : 0) + (main ? 3 : 0) + (px ? 1 : 0)) * F;
+    tma::fence_proxy_async();
+    tma::mbar_expect(b, bytes);
+    tma::load3(st + 0 * F, m.pr, xs, rp, qp + B_P / 2, b);
+    tma::load3(st + 1 * F, m.pr, xs, rvz, qp + B_VZ / 2, b);
+    if (pz) tma::load3(st + 2 * F, m.pr, xs, k, qp + B_PPZ / 2, b);
+    tma::load3(st + 5 * F, m.mb, xs, rb1, 1, b);
+    if (main) {
+        tma::load3(st + 3 * F, m.pr, xs, z, qp + B_VX / 2, b);
+        tma::load3(st + 6 * F, m.mb, xs, z, 1, b);
+        tma::load3(st + 7 * F, m.mb, xs, z, 0, b);
+    }
+    if (px) tma::load3(st + 4 * F, m.pr, xs, z, qp + B_PPX / 2, b);
+}
+
+template <int M, bool FS>
+__global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2t(const __grid_constant__ Fwd2T p)
+{
+    const Step2D &a = p.a;
+    if (guard_tripped(a.g)) return;
+    using C = Cols<M>;
+    using T = float2;
+    using R = float2;
+    constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
+    static_assert(TXO % 2 == 0 && HXP % 2 == 0, "CTA column starts must be 16-byte aligned for 8-byte elements");
+    __shared__ T sP[NTH];
+    __shared__ R sB[NTH];
+    __shared__ T sV[NTH];
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sm = smraw + ((128u - (tma::su32(smraw) & 127u)) & 127u);
+    char *stages = reinterpret_cast<char *>(sm);   // [PDF][kFwdSlots][NTH] x 8 bytes
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kFwdBarOff);
+
+    const GridDev &g = a.g;
+    const int t = threadIdx.x;
+    const int slot = blockIdx.z, shot = a.shot0 + slot;
+    const int Nx = g.Nx, nx = g.nx;
+    const int xs = (int)blockIdx.x * TXO - HXP;
+    const int x = xs + t;
+    const bool colok = x >= 0 && x < Nx;
+    const bool outcol = colok && t >= HXP && t < HXP + TXO;
+    const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
+    const int zc0 = (int)blockIdx.y * a.tzc;
+    const int zc1 = min(zc0 + a.tzc, g.Nz);
+    const int zstart = zc0 - W;
+    const long long plane = g.plane;
+    const int pT = (int)plane;   // in-slot offsets fit 32 bits (checked by the host)
+    const int pitch = g.pitch;
+    const int xc = colok ? x : 0;
+    const float *in = a.in + slot * a.sstride;
+    T *out = reinterpret_cast<T *>(a.out + slot * a.sstride) + xc;
+    T *psiv = reinterpret_cast<T *>(a.psiv + slot * a.vstride) + xc;
+    const float dt = g.dt;
+    const int x0 = g.x0, x1 = g.x0 + nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
+    const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
+    const bool tph = (xs <= x0 - 2) || (xs + NTH - 1 >= x1);   // CTA has half-node CPML columns
+    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
+    const int src = a.src_cell[shot];
+    const float wsrc = a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + a.n];
+    constexpr int oP = B_P / 2, oVX = B_VX / 2, oVZ = B_VZ / 2, oPPX = B_PPX / 2, oPPZ = B_PPZ / 2;
+    constexpr int oPVX = B_PVX / 2, oPVZ = B_PVZ / 2;
+    constexpr int PR = NTH - 1;   // the thread that issues the copies
+
+    if (t == 0) {
+        for (int i = 0; i < PDF; ++i) tma::mbar_init(bar + i);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    if (t == PR) {
+        for (int j = 0; j < PDF - 1 && zstart + j < zc1; ++j)
+            fwd_issue_tma<M, FS>(p, stages + j * kFwdStageBytesT, bar + j, slot, xs, zstart + j, zc0, zc1, tph);
+    }
+
+    constexpr int U = W / kFwdGroupDiv > 0 ? W / kFwdGroupDiv : 1, RL = W + U - 1;
+    T P[RL], VZ[RL];
+#pragma unroll
+    for (int j = 0; j < RL; ++j) {
+        P[j] = zero_<T>();
+        VZ[j] = zero_<T>();
+    }
+    {
+        const T *pin = reinterpret_cast<const T *>(in) + oP * pT + xc;
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            const int zr = zstart + j, zrs = node_src_row<FS>(g, zr);
+            const T v = (colok && zrs >= 0 && zrs < g.Nz) ? pin[zrs * pitch] : zero_<T>();
+            P[j] = zrs != zr ? neg_(v) : v;
+        }
+    }
+    R br_old = zero_<R>();
+    {
+        int k = zstart + M - 1;
+        if (colok && k >= 0 && k < g.Nz) br_old = a.br2[k * pitch + xc];
+    }
+
+    bool bad = false;      // this thread's wait gave up
+    int fail_row = zc1;    // first row whose stage was not consumed
+    for (int zb = zstart; zb < zc1; zb += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int z = zb + u;
+            if (z >= zc1) break;
+            const int j = z - zstart;
+            // refill the stage of row z - 1 with row z + PDF - 1: every thread
+            // passed a barrier after reading it (the previous row's)
+            const int zi = z + PDF - 1;
+            if (t == PR && zi < zc1)
+                fwd_issue_tma<M, FS>(p, stages + ((j + PDF - 1) % PDF) * kFwdStageBytesT, bar + (j + PDF - 1) % PDF,
+                                     slot, xs, zi, zc0, zc1, tph);
+            bad |= !tma::mbar_wait(bar + j % PDF, (unsigned)(j / PDF) & 1u);
+            const FwdRow<true> cur = fwd_read<true>(stages + (j % PDF) * kFwdStageBytesT);
+            const int k = z + M - 1;   // half row of vz computed in this iteration
+            const int sl = u + W - 1;
+            P[sl] = (FS && z + W - 1 < g.z0) ? neg_(cur.p) : cur.p;   // ghost rows hold -p(mirror)
+            // ---- vz at half row k (column-local)
+            const float buz = 0.5f * (xof(br_old) + xof(cur.br1));
+            const float rsum = yof(br_old) + yof(cur.br1);
+            br_old = cur.br1;
+            T vzn = zero_<T>();
+            if (colok && k >= 0 && k < g.Nz) {
+                const int ck = k * pitch;
+                const bool own = outcol && k >= zc0 && k < zc1;
+                T G = stencil<M, T>(g.cz, [&](int l) { return P[u + M - 1 + l]; },
+                                    [&](int l) { return P[u + M - l]; });
+                if ((k <= z0 - 2) || (k >= z1)) {
+                    T ps = fma_(a.pml.bh[0][k], cur.psz, mul_(a.pml.ah[0][k], G));
+                    if (own) out[oPPZ * pT + ck] = ps;
+                    G = add_(G, ps);
+                }
+                const float dtbu = dt * buz;
+                vzn = fma_(-dtbu, G, cur.vz);
+                vzn.y = fmaf(0.5f * dt * rsum, G.x, vzn.y);
+                if (own) out[oVZ * pT + ck] = vzn;
+            }
+            VZ[sl] = vzn;
+            if (z < zc0) {
+                // warm-up row: the barrier that lets its stage be refilled
+                if (__syncthreads_or(bad)) {
+                    fail_row = z;
+                    break;
+                }
+                continue;
+            }
+
+            // ---- row z: vx on the output columns and the halo
+            const int cz = z * pitch;
+            const T p0 = P[u];
+            sP[t] = p0;
+            sB[t] = cur.brz;
+            if (__syncthreads_or(bad)) {
+                fail_row = z;
+                break;
+            }
+            T vxn = zero_<T>();
+            if (vxok) {
+                T G = stencil<M, T>(g.cx, [&](int l) { return sP[t + l]; }, [&](int l) { return sP[t + 1 - l]; });
+                const bool last = x + 1 >= Nx;
+                const R bn = last ? cur.brz : sB[t + 1];
+                const float bux = 0.5f * (xof(cur.brz) + xof(bn));
+                if (pmlxh) {
+                    T ps = fma_(bhx, cur.psx, mul_(ahx, G));
+                    if (outcol) out[oPPX * pT + cz] = ps;
+                    G = add_(G, ps);
+                }
+                const float dtbu = dt * bux;
+                vxn = fma_(-dtbu, G, cur.vx);
+                float rs = yof(cur.brz) + (last ? 0.f : yof(bn));
+                vxn.y = fmaf(0.5f * dt * rs, G.x, vxn.y);
+                if (outcol) out[oVX * pT + cz] = vxn;
+            }
+            sV[t] = vxn;
+            __syncthreads();
+
+            // ---- row z: pressure on the output columns
+            if (outcol) {
+                T qx = stencil<M, T>(g.cx, [&](int l) { return sV[t + l - 1]; }, [&](int l) { return sV[t - l]; });
+                T qz = stencil<M, T>(g.cz, [&](int l) { return VZ[u + M + l - 1]; },
+                                     [&](int l) { return VZ[u + M - l]; });
+                if (pmlxn) {
+                    T ps = fma_(bix, psiv[oPVX * pT + cz], mul_(aix, qx));
+                    psiv[oPVX * pT + cz] = ps;
+                    qx = add_(qx, ps);
+                }
+                if ((z <= z0 - 1) || (z >= z1)) {
+                    T ps = fma_(a.pml.bi[0][z], psiv[oPVZ * pT + cz], mul_(a.pml.ai[0][z], qz));
+                    psiv[oPVZ * pT + cz] = ps;
+                    qz = add_(qz, ps);
+                }
+                const T Q = add_(qx, qz);
+                const float kd = xof(cur.kd);
+                T pn = fma_(-kd, Q, p0);
+                pn.y = fmaf(-cur.kd.y, Q.x, pn.y);
+                if (cz + x == src) pn.x += wsrc;
+                if (FS && z <= z0) pn = zero_<T>();   // p = 0 on the free surface (ghost rows unused)
+                out[oP * pT + cz] = pn;
+            }
+        }
+        if (fail_row < zc1) break;
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            P[j] = P[j + U];
+            VZ[j] = VZ[j + U];
+        }
+    }
+
+    if (fail_row < zc1) {
+        // a wait gave up: record it, let the copies in flight land (rows up to
+        // fail_row + PDF - 1 were issued), return
+        if (t == PR) {
+            atomicOr(a.err, 1);
+            for (int zz = fail_row; zz <= min(fail_row + PDF - 1, zc1 - 1); ++zz) {
+                const int jj = zz - zstart;
+                (void)tma::mbar_wait(bar + jj % PDF, (unsigned)(jj / PDF) & 1u);
+            }
+        }
+        return;
+    }
+
+    // record dp^{n+1} (or the background p^{n+1} in nonlinear modelling) at
+    // the receivers of this CTA
+    __syncthreads();
+    int tile = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+    int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
+    const float2 *po = reinterpret_cast<const float2 *>(a.out + slot * a.sstride + B_P * plane);
+    for (int i = b + t; i < e; i += NTH) {
+        int2 rc = a.trec.rec[i];
+        a.dstage[(long long)rc.y * g.nt + a.n] = a.rec_bg ? po[rc.x].x : po[rc.x].y;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Reverse step n (n = nt-1 .. 0) of L^T. Input state: (background p^n,
 // lambda_p) with the residual of step n already added, (v^{n+1/2}, lambda_v)
 // and the lambda CPML memories. The step applies the transposed Born
@@ -871,6 +1144,367 @@ __global__ void __launch_bounds__(NTH, FS ? kAdjMinBlocksFS : kAdjMinBlocks) k_a
 
 // Start state of a reverse pass: (p, 0), (vx, 0), (vz, 0) from the saved
 // background final state [p][vx][vz] of each shot of the batch.
+// ---------------------------------------------------------------------------
+// Migration step with TMA row staging (shots without aperture windows). The
+// same arithmetic as k_adj2d, in the same order, so the results are the same
+// bits; only the loads of the rows ahead differ. One thread (the last) issues
+// every field row of a stage as one tensor-map tile copy (a kThreads2D-wide
+// row of one field) on the stage's mbarrier; the tensor maps read zeros
+// outside the padded grid, which is what the per-thread copies' zero fill
+// gives at the grid edges. Rows the per-thread copies zero-fill inside the
+// grid (a row whose source row is out of range) are read from row -1.
+// Fields a row does not use (the CPML memories outside the strips, the
+// row-z fields of the warm-up rows) are not copied; no consumer reads them.
+// A stage is refilled only after a CTA barrier that follows every read of
+// it: the previous row's barriers (a warm-up row adds one for this).
+// ---------------------------------------------------------------------------
+struct Adj2T {
+    Step2D a;
+    Maps2D m;
+};
+
+constexpr unsigned kAdjStageBytesT = (unsigned)(kAdjStageFloats * sizeof(float));
+static_assert(kAdjStageBytesT % 128 == 0, "stage rows stay 128-byte aligned");
+constexpr unsigned kAdjBarOff = PDA * kAdjStageBytesT;
+constexpr unsigned kAdjSmemT = kAdjBarOff + 64 + 128;   // stages, barriers, alignment slack
+
+// Issues the copies of row z (the stage layout of adj_issue) on barrier b.
+// xs: first column of the CTA (a multiple of 4, so every copy starts on a
+// 16-byte boundary); tpn / tph: the CTA has node / half-node CPML columns.
+template <int M, bool FS>
+__device__ __forceinline__ void adj_issue_tma(const Adj2T &p, float *st, uint64_t *b, int slot, int xs, int z,
+                                              int zc0, int zc1, bool tpn, bool tph)
+{
+    const GridDev &g = p.a.g;
+    const Maps2D &m = p.m;
+    constexpr int W = 2 * M;
+    constexpr unsigned R2 = NTH * 8, R1 = NTH * 4;   // bytes of one float2 / float field row
+    const int z0 = g.z0, z1 = g.z0 + g.nz;
+    const int zr = z + W - 1, k = z + M - 1;
+    const int qp = slot * m.pps, qf = slot * m.fps;
+    char *s2 = reinterpret_cast<char *>(st);
+    char *s1 = s2 + kAdjF2 * R2;
+    const bool inr = zr >= 0 && zr < g.Nz, ink = k >= 0 && k < g.Nz;
+    int rpl = zr, rvz = ink ? k : -1;
+    if constexpr (FS) {
+        const int zrs = node_src_row<FS>(g, zr), ks = half_src_row<FS>(g, k);
+        rpl = (zrs >= 0 && zrs < g.Nz) ? zrs : -1;
+        rvz = (ink && ks < g.Nz) ? ks : -1;
+    }
+    const int rbz = k + 1 >= 0 ? min(k + 1, g.Nz - 1) : -1;
+    const bool lpa = inr && ((zr <= z0 - 1) || (zr >= z1));
+    const bool lpz = ink && ((k <= z0 - 2) || (k >= z1));
+    const bool main = z >= zc0 && z < zc1;
+    const int iz = z - z0;
+    const bool im = main && iz >= 0 && iz < g.nz;
+    const bool lvx = main && tpn, lvz = main && ((z <= z0 - 1) || (z >= z1)), lpx = main && tph;
+    unsigned bytes = 2 * R2 + 2 * R1 + (lpa ? R1 : 0) + (lpz ? R1 : 0);
+    if (main) bytes += 2 * R2 + 2 * R1;
+    if (im) bytes += R2;
+    if (lvx) bytes += R1;
+    if (lvz) bytes += R1;
+    if (lpx) bytes += R1;
+    tma::fence_proxy_async();
+    tma::mbar_expect(b, bytes);
+    tma::load3(s2 + 0 * R2, m.pr, xs, rpl, qp + A_PL / 2, b);
+    tma::load3(s2 + 1 * R2, m.pr, xs, rvz, qp + A_VZ / 2, b);
+    tma::load3(s1 + 0 * R1, m.md, xs, zr, 0, b);
+    if (lpa) tma::load3(s1 + 1 * R1, m.fl, xs, zr, qf + A_LPVZ, b);
+    tma::load3(s1 + 2 * R1, m.md, xs, rbz, 1, b);
+    if (lpz) tma::load3(s1 + 3 * R1, m.fl, xs, k, qf + A_LPPZ, b);
+    if (main) {
+        tma::load3(s2 + 2 * R2, m.pr, xs, z, qp + A_PL / 2, b);
+        tma::load3(s2 + 3 * R2, m.pr, xs, z, qp + A_VX / 2, b);
+        tma::load3(s1 + 4 * R1, m.md, xs, z, 0, b);
+        tma::load3(s1 + 7 * R1, m.md, xs, z, 1, b);
+    }
+    if (im) tma::load3(s2 + 4 * R2, m.im, xs, z, slot, b);
+    if (lvx) tma::load3(s1 + 5 * R1, m.fl, xs, z, qf + A_LPVX, b);
+    if (lvz) tma::load3(s1 + 6 * R1, m.fl, xs, z, qf + A_LPVZ, b);
+    if (lpx) tma::load3(s1 + 8 * R1, m.fl, xs, z, qf + A_LPPX, b);
+}
+
+template <int M, bool FS>
+__global__ void __launch_bounds__(NTH, FS ? kAdjMinBlocksFS : kAdjMinBlocks) k_adj2t(const __grid_constant__ Adj2T p)
+{
+    const Step2D &a = p.a;
+    if (guard_tripped(a.g)) return;
+    using C = Cols<M>;
+    constexpr int W = C::W, HXP = C::HXP, TXO = C::TXO;
+    static_assert(TXO % 4 == 0 && HXP % 4 == 0, "CTA column starts must be 16-byte aligned for 4-byte elements");
+    __shared__ float2 sPU[NTH];   // (p^n, kdt*lp - ai_x (lpsi_vx - kdt*lp)), row z
+    __shared__ float sB[NTH];     // 1/rho, row z
+    __shared__ float2 sVW[NTH];   // (vx^{n+1/2}, dt*bu_x*lvx - ah_x*lpsi_px), row z
+    __shared__ float sVN[NTH];    // vx^{n-1/2}, row z
+    __shared__ float sPi[NTH];    // Gx * lvx, row z
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sm = smraw + ((128u - (tma::su32(smraw) & 127u)) & 127u);
+    float *stagef = reinterpret_cast<float *>(sm);   // [PDA][kAdjStageFloats]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kAdjBarOff);
+
+    const GridDev &g = a.g;
+    const int t = threadIdx.x;
+    const int slot = blockIdx.z, shot = a.shot0 + slot;
+    const int Nx = g.Nx, nx = g.nx;
+    const int xs = (int)blockIdx.x * TXO - HXP;
+    const int x = xs + t;
+    const bool colok = x >= 0 && x < Nx;
+    const bool outcol = colok && t >= HXP && t < HXP + TXO;
+    const bool vxok = colok && t >= M - 1 && t <= NTH - 1 - M;
+    const int zc0 = (int)blockIdx.y * a.tzc;
+    const int zc1 = min(zc0 + a.tzc, g.Nz);
+    const int zstart = zc0 - W;
+    const long long plane = g.plane;
+    const long long p2 = plane;   // stride of one pair field in float2 units
+    const int pitch = g.pitch;
+    const int xc = colok ? x : 0;
+    const float *in = a.in + slot * a.sstride;
+    float *outf = a.out + slot * a.sstride + xc;
+    float2 *out2 = reinterpret_cast<float2 *>(a.out + slot * a.sstride) + xc;
+    const float dt = g.dt;
+    const int n = a.n;
+    const bool recon = n > 0;
+    const int x0 = g.x0, x1 = g.x0 + nx, z0 = g.z0, z1 = g.z0 + g.nz;
+    const int ix = x - x0;
+    const bool xint = ix >= 0 && ix < nx;
+    const bool pmlxh = colok && ((x <= x0 - 2) || (x >= x1));
+    const bool pmlxn = colok && ((x <= x0 - 1) || (x >= x1));
+    const bool tph = (xs <= x0 - 2) || (xs + NTH - 1 >= x1);   // CTA has half-node / node CPML columns
+    const bool tpn = (xs <= x0 - 1) || (xs + NTH - 1 >= x1);
+    const float ahx = pmlxh ? a.pml.ah[2][x] : 0.f, bhx = pmlxh ? a.pml.bh[2][x] : 0.f;
+    const float aix = pmlxn ? a.pml.ai[2][x] : 0.f, bix = pmlxn ? a.pml.bi[2][x] : 0.f;
+    const long long rowprev = band_row(a.bands, shot, n - 1);
+    const int src = a.src_cell[shot];
+    const float wsrc = recon ? a.src_scale * a.wav[(a.wav_per_shot ? (long long)shot * g.nt : 0) + n - 1] : 0.f;
+    float2 *img = a.img + slot * plane + xc;
+    constexpr int PR = NTH - 1;   // the thread that issues the copies
+
+    if (t == 0) {
+        for (int i = 0; i < PDA; ++i) tma::mbar_init(bar + i);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    if (t == PR) {
+        for (int j = 0; j < PDA - 1 && zstart + j < zc1; ++j)
+            adj_issue_tma<M, FS>(p, stagef + j * kAdjStageFloats, bar + j, slot, xs, zstart + j, zc0, zc1, tpn, tph);
+    }
+
+    constexpr int U = W / kAdjGroupDiv > 0 ? W / kAdjGroupDiv : 1, RL = W + U - 1;
+    float2 PU[RL], VW[RL];
+    float VN[RL], PIZ[RL];
+#pragma unroll
+    for (int j = 0; j < RL; ++j) {
+        PU[j] = make_float2(0.f, 0.f);
+        VW[j] = make_float2(0.f, 0.f);
+        VN[j] = 0.f;
+        PIZ[j] = 0.f;
+    }
+    auto pu_node = [&](int r, float2 pl, float kd, float lpvz) -> float2 {
+        if (FS && r <= z0) {
+            if (r == z0) return make_float2(0.f, 0.f);
+            return make_float2(-pl.x, -(kd * pl.y));
+        }
+        float kl = kd * pl.y;
+        if (colok && r >= 0 && r < g.Nz && ((r <= z0 - 1) || (r >= z1))) kl -= a.pml.ai[0][r] * (lpvz - kl);
+        return make_float2(pl.x, kl);
+    };
+    {
+        const float2 *in2 = reinterpret_cast<const float2 *>(in);
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            const int r = zstart + j, rs = node_src_row<FS>(g, r);
+            const bool ok = colok && r >= 0 && r < g.Nz;
+            const long long cr = ok ? (long long)r * pitch + xc : 0;
+            const bool oks = colok && rs >= 0 && rs < g.Nz;
+            const float2 plv = oks ? in2[(A_PL / 2) * p2 + (long long)rs * pitch + xc] : make_float2(0.f, 0.f);
+            const float kd = ok ? a.kdt[cr] : 0.f;
+            const float lpvz = (ok && ((r <= z0 - 1) || (r >= z1))) ? in[A_LPVZ * plane + cr] : 0.f;
+            PU[j] = pu_node(r, plv, kd, lpvz);
+        }
+    }
+    float bz_old = 0.f;
+    {
+        int k = zstart + M - 1;
+        if (colok && k >= 0 && k < g.Nz) bz_old = a.binv[(long long)k * pitch + xc];
+    }
+
+    bool bad = false;      // this thread's wait gave up
+    int fail_row = zc1;    // first row whose stage was not consumed
+    for (int zb = zstart; zb < zc1; zb += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int z = zb + u;
+            if (z >= zc1) break;
+            const int j = z - zstart;
+            // refill the stage of row z - 1 with row z + PDA - 1: every thread
+            // passed a barrier after reading it (the previous row's)
+            const int zi = z + PDA - 1;
+            if (t == PR && zi < zc1)
+                adj_issue_tma<M, FS>(p, stagef + ((j + PDA - 1) % PDA) * kAdjStageFloats, bar + (j + PDA - 1) % PDA,
+                                     slot, xs, zi, zc0, zc1, tpn, tph);
+            bad |= !tma::mbar_wait(bar + j % PDA, (unsigned)(j / PDA) & 1u);
+            const AdjRow cur = adj_read(stagef + (j % PDA) * kAdjStageFloats);
+            const int k = z + M - 1;
+            const int sl = u + W - 1;
+            PU[sl] = pu_node(z + W - 1, cur.pl, cur.kdr, cur.lpvzr);
+            const float buz = 0.5f * (bz_old + cur.bz);
+            bz_old = cur.bz;
+            // ---- half row k along z: lambda_vz, lambda_psi_pz, background vz^{n-1/2}
+            float wz = 0.f, vn = 0.f, piz = 0.f;
+            if (colok && k >= 0 && k < g.Nz) {
+                const long long ck = (long long)k * pitch;
+                const bool own = outcol && k >= zc0 && k < zc1;
+                const float2 D = stencil<M, float2>(g.cz, [&](int l) { return PU[u + M - 1 + l]; },
+                                                    [&](int l) { return PU[u + M - l]; });
+                const float lv = cur.v2z.y + D.y;
+                const float dtbu = dt * buz;
+                wz = dtbu * lv;
+                if ((k <= z0 - 2) || (k >= z1)) {
+                    float l1 = cur.lppz - dtbu * lv;
+                    wz -= a.pml.ah[0][k] * l1;
+                    if (own) outf[A_LPPZ * plane + ck] = a.pml.bh[0][k] * l1;
+                }
+                piz = D.x * lv;
+                if (recon && xint) {
+                    const int iz = k - z0;
+                    if ((iz >= 0 || FS) && iz < g.nz) vn = cur.v2z.x + dtbu * D.x;
+                    else if (in_xstrip(iz, M, g.nz))
+                        vn = band_get(a.bands, 1, rowprev, band_zstrip(iz, ix, M, g.nz, nx));
+                }
+                if (own) out2[(A_VZ / 2) * p2 + ck] = make_float2(vn, lv);
+            }
+            VW[sl] = make_float2(cur.v2z.x, wz);
+            VN[sl] = vn;
+            PIZ[sl] = piz;
+            if (z < zc0) {
+                // warm-up row: the barrier that lets its stage be refilled
+                if (__syncthreads_or(bad)) {
+                    fail_row = z;
+                    break;
+                }
+                continue;
+            }
+
+            // ---- row z: half nodes along x
+            const long long cz = (long long)z * pitch;
+            const bool surf = FS && z == z0;   // free-surface row: p = 0, lambda_p = 0
+            const float pbn = cur.plz.x;
+            const float lp1 = surf ? 0.f : cur.plz.y;
+            const float kd = cur.kdz;
+            const float kl = kd * lp1;
+            sPU[t] = make_float2(pbn, pmlxn ? kl - aix * (cur.lpsvx - kl) : kl);
+            sB[t] = cur.bx;
+            if (__syncthreads_or(bad)) {
+                fail_row = z;
+                break;
+            }
+            float2 vw = make_float2(cur.v2x.x, 0.f);
+            float vxn = 0.f, pix = 0.f;
+            if (vxok) {
+                const float2 D = stencil<M, float2>(g.cx, [&](int l) { return sPU[t + l]; },
+                                                    [&](int l) { return sPU[t + 1 - l]; });
+                const float bux = 0.5f * (cur.bx + (x + 1 >= Nx ? cur.bx : sB[t + 1]));
+                const float dtbu = dt * bux;
+                const float lv = cur.v2x.y + D.y;
+                float wx = dtbu * lv;
+                if (pmlxh) {
+                    float l1 = cur.lppx - dtbu * lv;
+                    wx -= ahx * l1;
+                    if (outcol) outf[A_LPPX * plane + cz] = bhx * l1;
+                }
+                vw.y = wx;
+                pix = D.x * lv;
+                if (recon) {
+                    const int iz = z - z0;
+                    if (iz >= 0 && iz < g.nz) {
+                        if (xint) vxn = cur.v2x.x + dtbu * D.x;
+                        else if (in_xstrip(ix, M, nx))
+                            vxn = band_get(a.bands, 1, rowprev, band_xstrip(iz, ix, M, g.nz, nx));
+                    }
+                }
+                if (outcol) out2[(A_VX / 2) * p2 + cz] = make_float2(vxn, lv);
+            }
+            sVW[t] = vw;
+            sVN[t] = vxn;
+            sPi[t] = pix;
+            __syncthreads();
+
+            // ---- row z: nodes on the output columns
+            if (outcol) {
+                const float2 Ex = stencil<M, float2>(g.cx, [&](int l) { return sVW[t + l - 1]; },
+                                                     [&](int l) { return sVW[t - l]; });
+                const float2 Ez = stencil<M, float2>(g.cz, [&](int l) { return VW[u + M + l - 1]; },
+                                                     [&](int l) { return VW[u + M - l]; });
+                const float2 E = add_(Ex, Ez);
+                float qn = 0.f;
+                if (recon)
+                    qn = stencil<M, float>(g.cx, [&](int l) { return sVN[t + l - 1]; }, [&](int l) { return sVN[t - l]; }) +
+                         stencil<M, float>(g.cz, [&](int l) { return VN[u + M + l - 1]; },
+                                           [&](int l) { return VN[u + M - l]; });
+                const int iz = z - z0;
+                const bool inner = xint && iz >= 0 && iz < g.nz;
+                if (inner) {
+                    float2 acc = cur.img;
+                    acc.x += E.x * lp1;
+                    // (on the free surface the half row above is a ghost: no product of its own)
+                    acc.y += (sPi[t] + sPi[t - 1]) + (PIZ[u + M] + (surf ? 0.f : PIZ[u + M - 1]));
+                    img[cz] = acc;
+                }
+                float pn = 0.f;
+                if (recon) {
+                    if (inner) {
+                        pn = pbn + kd * qn;
+                        if (cz + x == src) pn -= wsrc;
+                    } else {
+                        long long b = pband_index(iz, ix, M, g.nz, nx);
+                        if (b >= 0) pn = band_get(a.bands, 0, rowprev, b);
+                    }
+                }
+                out2[(A_PL / 2) * p2 + cz] = (FS && z <= z0) ? make_float2(0.f, 0.f) : make_float2(pn, lp1 + E.y);
+                if (pmlxn) outf[A_LPVX * plane + cz] = bix * (cur.lpsvx - kl);
+                if ((z <= z0 - 1) || (z >= z1)) outf[A_LPVZ * plane + cz] = a.pml.bi[0][z] * (cur.lpsvz - kl);
+            }
+        }
+        if (fail_row < zc1) break;
+#pragma unroll
+        for (int j = 0; j < W - 1; ++j) {
+            PU[j] = PU[j + U];
+            VW[j] = VW[j + U];
+            VN[j] = VN[j + U];
+            PIZ[j] = PIZ[j + U];
+        }
+    }
+
+    if (fail_row < zc1) {
+        // a wait gave up: record it, let the copies in flight land (rows up to
+        // fail_row + PDA - 1 were issued), return
+        if (t == PR) {
+            atomicOr(a.err, 1);
+            for (int zz = fail_row; zz <= min(fail_row + PDA - 1, zc1 - 1); ++zz) {
+                const int jj = zz - zstart;
+                (void)tma::mbar_wait(bar + jj % PDA, (unsigned)(jj / PDA) & 1u);
+            }
+        }
+        return;
+    }
+
+    if (recon) {
+        // pre-add the residual of step n-1 at the receivers of this CTA
+        __syncthreads();
+        int tile = shot * a.trec.ntiles + blockIdx.y * gridDim.x + blockIdx.x;
+        int b = a.trec.ptr[tile], e = a.trec.ptr[tile + 1];
+        float2 *plo = reinterpret_cast<float2 *>(a.out + slot * a.sstride + A_PL * plane);
+        for (int i = b + t; i < e; i += NTH) {
+            int2 rc = a.trec.rec[i];
+            if (i > b && a.trec.rec[i - 1].x == rc.x) continue;  // run handled by its first entry
+            float add = 0.f;
+            for (int q = i; q < e && a.trec.rec[q].x == rc.x; ++q)
+                add += a.dstage[(long long)a.trec.rec[q].y * g.nt + (n - 1)];
+            plo[rc.x].y += add;
+        }
+    }
+}
+
 __global__ void k_pack_adj(const GridDev g, const float *final_state, int shot0, int batch, float *st,
                            long long sstride)
 {
@@ -921,7 +1555,11 @@ cudaError_t attr_M()
     if ((e = cudaFuncSetAttribute(k_adj2d<M, false, false>, at, b)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_adj2d<M, true, false>, at, b)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_adj2d<M, false, true>, at, b)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_adj2d<M, true, true>, at, b);
+    if ((e = cudaFuncSetAttribute(k_adj2d<M, true, true>, at, b)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd2t<M, false>, at, (int)kFwdSmemT)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd2t<M, true>, at, (int)kFwdSmemT)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_adj2t<M, false>, at, (int)kAdjSmemT)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj2t<M, true>, at, (int)kAdjSmemT);
 }
 
 template <int M, bool WIN>
@@ -935,18 +1573,37 @@ cudaError_t launch_fwd_MW(const Step2D &a, dim3 grid, bool born, bool bands, boo
 }
 
 template <int M>
-cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool hess, cudaStream_t s)
+cudaError_t launch_fwd_M(const Step2D &a, int batch, bool born, bool bands, bool hess, cudaStream_t s,
+                         const Maps2D *maps)
 {
     dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
+    if (born && maps && !a.win_nx) {
+        if (!a.err) return cudaErrorInvalidValue;
+        Fwd2T p;
+        p.a = a;
+        p.m = *maps;
+        if (a.g.fs) k_fwd2t<M, true><<<grid, NTH, kFwdSmemT, s>>>(p);
+        else k_fwd2t<M, false><<<grid, NTH, kFwdSmemT, s>>>(p);
+        return cudaGetLastError();
+    }
     if (a.win_nx) return launch_fwd_MW<M, true>(a, grid, born, bands, hess, s);
     return launch_fwd_MW<M, false>(a, grid, born, bands, hess, s);
 }
 
 template <int M>
-cudaError_t launch_adj_M(const Step2D &a, int batch, cudaStream_t s)
+cudaError_t launch_adj_M(const Step2D &a, const Maps2D *maps, int batch, cudaStream_t s)
 {
     dim3 grid((a.g.Nx + Cols<M>::TXO - 1) / Cols<M>::TXO, (a.g.Nz + a.tzc - 1) / a.tzc, batch);
     const bool w = a.win_nx != nullptr, f = a.g.fs != 0;
+    if (maps && !w) {
+        if (!a.err) return cudaErrorInvalidValue;
+        Adj2T p;
+        p.a = a;
+        p.m = *maps;
+        if (f) k_adj2t<M, true><<<grid, NTH, kAdjSmemT, s>>>(p);
+        else k_adj2t<M, false><<<grid, NTH, kAdjSmemT, s>>>(p);
+        return cudaGetLastError();
+    }
     if (w && f) k_adj2d<M, true, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
     else if (w) k_adj2d<M, true, false><<<grid, NTH, kAdjStageBytes, s>>>(a);
     else if (f) k_adj2d<M, false, true><<<grid, NTH, kAdjStageBytes, s>>>(a);
@@ -1026,16 +1683,39 @@ cudaError_t ensure_kernels_configured()
     return cudaSuccess;
 }
 
-cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess, cudaStream_t s)
+cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess, cudaStream_t s,
+                         const Maps2D *maps)
 {
-    if (a.g.M == 2) return launch_fwd_M<2>(a, batch, born, save_bands, hess, s);
-    return launch_fwd_M<4>(a, batch, born, save_bands, hess, s);
+    if (a.g.M == 2) return launch_fwd_M<2>(a, batch, born, save_bands, hess, s, maps);
+    return launch_fwd_M<4>(a, batch, born, save_bands, hess, s, maps);
 }
 
-cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s)
+cudaError_t launch_adj2d(const Step2D &a, const Maps2D *maps, int batch, cudaStream_t s)
 {
-    if (a.g.M == 2) return launch_adj_M<2>(a, batch, s);
-    return launch_adj_M<4>(a, batch, s);
+    if (a.g.M == 2) return launch_adj_M<2>(a, maps, batch, s);
+    return launch_adj_M<4>(a, maps, batch, s);
+}
+
+cudaError_t maps2d(Maps2D *m, const GridDev &g, const float *st, long long sstride, const float *kdt,
+                   const float *binv, const float2 *kd2, const float2 *br2, const float2 *img, int batch)
+{
+    // the two model arrays of each kind are one map: their planes must be adjacent
+    if (binv != kdt + g.plane || br2 != kd2 + g.plane || sstride % (2 * g.plane)) return cudaErrorInvalidValue;
+    m->pps = (int)(sstride / (2 * g.plane));
+    m->fps = (int)(sstride / g.plane);
+    const cuuint32_t box[3] = {(cuuint32_t)NTH, 1, 1};
+    const cuuint64_t s8[2] = {(cuuint64_t)g.pitch * 8, (cuuint64_t)g.plane * 8};
+    const cuuint64_t s4[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
+    const cuuint64_t dpr[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Nz, (cuuint64_t)batch * m->pps};
+    const cuuint64_t dfl[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Nz, (cuuint64_t)batch * m->fps};
+    const cuuint64_t dmd[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Nz, 2};
+    const cuuint64_t dim[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Nz, (cuuint64_t)batch};
+    cudaError_t e;
+    if ((e = encode_tmap(&m->pr, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, st, dpr, s8, box)) != cudaSuccess) return e;
+    if ((e = encode_tmap(&m->fl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, st, dfl, s4, box)) != cudaSuccess) return e;
+    if ((e = encode_tmap(&m->md, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, kdt, dmd, s4, box)) != cudaSuccess) return e;
+    if ((e = encode_tmap(&m->mb, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, kd2, dmd, s8, box)) != cudaSuccess) return e;
+    return encode_tmap(&m->im, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, img, dim, s8, box);
 }
 
 cudaError_t launch_window_model(const GridDev &gm, const GridDev &g, const int *win_x0, const int *win_nx,

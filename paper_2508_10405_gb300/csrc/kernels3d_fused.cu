@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "lsrtm_internal.cuh"
+#include "tma.cuh"
 
 namespace lsrtm {
 namespace {
@@ -36,7 +37,6 @@ namespace {
 constexpr int TX = kTile3X, TY = kTile3Y, NTH = TX * TY;
 constexpr int PD = 2;                       // stage ring depth
 constexpr int kMinBlocks = 2;               // resident CTAs per SM the register budget targets
-constexpr unsigned kWaitLimit = 1u << 22;   // mbarrier polls before giving up
 
 // ---- packed arithmetic
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -77,44 +77,17 @@ __device__ __forceinline__ int node_src_row(const GridDev &g, int r) { return (g
 __device__ __forceinline__ int half_src_row(const GridDev &g, int k) { return (g.fs && k < g.z0) ? fs_half_row(g, k) : k; }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-// ---- shared memory, mbarriers and TMA
-__device__ __forceinline__ unsigned su32(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(uint64_t *b, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *b, unsigned phase)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase `phase` of barrier b; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned phase)
-{
-    for (unsigned i = 0; i < kWaitLimit; ++i)
-        if (mbar_test(b, phase)) return true;
-    return false;
-}
+// ---- shared memory, mbarriers and TMA (tma.cuh)
+using tma::al128;
+using tma::kWaitLimit;
+using tma::mbar_expect;
+using tma::mbar_init;
+using tma::mbar_wait;
+using tma::su32;
 __device__ __forceinline__ void tma4(void *dst, const CUtensorMap &m, int x, int y, int z, int q, uint64_t *b)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];\n" ::"r"(su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(&m)), "r"(x), "r"(y), "r"(z), "r"(q), "r"(su32(b))
-        : "memory");
+    tma::load4(dst, m, x, y, z, q, b);
 }
-
-constexpr unsigned al128(unsigned b) { return (b + 127u) / 128u * 128u; }
 
 // Tile geometry for half-width M. Box shapes (x extent in elements, rows):
 //   core  TX x TY                      the thread block's own columns
@@ -960,6 +933,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 }  // namespace
+
+cudaError_t encode_tmap(CUtensorMap *m, CUtensorMapDataType type, int rank, const void *base, const cuuint64_t *dims,
+                        const cuuint64_t *strides, const cuuint32_t *box)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, type, (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 // Tensor map over `nq` planes of `esz`-byte elements (4: float, 8: float2
 // pair) starting at base: dims (x in floats, y, z, plane), box (bx elements,

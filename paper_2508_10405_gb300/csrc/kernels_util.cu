@@ -311,6 +311,68 @@ __global__ void k_guard_state(const float4 *x, long long stride4, long long coun
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(word, 0, code);
 }
 
+// 16-bit checkpoint planes. Plane q of slot s of a snapshot is stored as
+// v / c with c = m / 2^15, m = max|plane| (c = 1 for a zero plane): m is
+// taken first (k_ck_absmax, a float's bits order like the float for
+// magnitudes), then k_ck_pack writes the scaled values and k_ck_unpack
+// multiplies back. amax: [slot][ck_planes] of the snapshot.
+__device__ __forceinline__ float ck_scale(float m) { return m > 0.f ? m * (1.f / 32768.f) : 1.f; }
+
+__global__ void k_ck_absmax(const float *src, long long sstride, long long plane, float *amax, int ck_planes,
+                            int p0)
+{
+    const float *x = src + blockIdx.z * sstride + blockIdx.y * plane;
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wm[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0)
+            atomicMax(reinterpret_cast<int *>(amax + blockIdx.z * ck_planes + p0 + blockIdx.y), __float_as_int(m));
+    }
+}
+
+template <class H>
+__device__ __forceinline__ H to16(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+
+template <class H>
+__global__ void k_ck_pack(const float *src, long long sstride, long long plane, const float *amax, int ck_planes,
+                          int p0, H *dst)
+{
+    const float *x = src + blockIdx.z * sstride + blockIdx.y * plane;
+    const int q = p0 + blockIdx.y;
+    H *o = dst + ((long long)blockIdx.z * ck_planes + q) * plane;
+    const float inv = 1.f / ck_scale(amax[blockIdx.z * ck_planes + q]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x)
+        o[i] = to16<H>(x[i] * inv);
+}
+
+template <class H>
+__global__ void k_ck_unpack(float *dst, long long sstride, long long plane, const float *amax, int ck_planes, int p0,
+                            const H *src)
+{
+    float *x = dst + blockIdx.z * sstride + blockIdx.y * plane;
+    const int q = p0 + blockIdx.y;
+    const H *i16 = src + ((long long)blockIdx.z * ck_planes + q) * plane;
+    const float c = ck_scale(amax[blockIdx.z * ck_planes + q]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = c * from16(i16[i]);
+}
+
 __global__ void k_guard_scalars(const double *v, int n, int *word, int code)
 {
     bool bad = false;
@@ -547,6 +609,37 @@ cudaError_t launch_guard_state(const float *base, long long stride, long long co
     const int gx = (int)std::max(1LL, std::min((count4 + NT - 1) / NT, (long long)std::max(1, 608 / nslots)));
     k_guard_state<<<dim3(gx, nslots), NT, 0, s>>>(reinterpret_cast<const float4 *>(base), stride / 4, count4, word,
                                                    code);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ck_pack(const float *src, long long sstride, long long plane, int planes, int p0, int bs,
+                           int ck_planes, int fmt, void *dst, float *amax, cudaStream_t s)
+{
+    if (bs <= 0 || planes <= 0) return cudaSuccess;
+    const int gx = (int)std::max(1LL, std::min((plane + NT - 1) / NT, (long long)std::max(1, 608 / (planes * bs))));
+    const dim3 grid(gx, planes, bs);
+    // the maxima of these planes start from zero
+    cudaError_t e = cudaMemset2DAsync(amax + p0, ck_planes * sizeof(float), 0, planes * sizeof(float), bs, s);
+    if (e != cudaSuccess) return e;
+    k_ck_absmax<<<grid, NT, 0, s>>>(src, sstride, plane, amax, ck_planes, p0);
+    if (fmt == BAND_BF16S)
+        k_ck_pack<<<grid, NT, 0, s>>>(src, sstride, plane, amax, ck_planes, p0, static_cast<__nv_bfloat16 *>(dst));
+    else
+        k_ck_pack<<<grid, NT, 0, s>>>(src, sstride, plane, amax, ck_planes, p0, static_cast<__half *>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ck_unpack(float *dst, long long sstride, long long plane, int planes, int p0, int bs,
+                             int ck_planes, int fmt, const void *src, const float *amax, cudaStream_t s)
+{
+    if (bs <= 0 || planes <= 0) return cudaSuccess;
+    const int gx = (int)std::max(1LL, std::min((plane + NT - 1) / NT, (long long)std::max(1, 608 / (planes * bs))));
+    const dim3 grid(gx, planes, bs);
+    if (fmt == BAND_BF16S)
+        k_ck_unpack<<<grid, NT, 0, s>>>(dst, sstride, plane, amax, ck_planes, p0,
+                                        static_cast<const __nv_bfloat16 *>(src));
+    else
+        k_ck_unpack<<<grid, NT, 0, s>>>(dst, sstride, plane, amax, ck_planes, p0, static_cast<const __half *>(src));
     return cudaGetLastError();
 }
 

@@ -146,6 +146,7 @@ struct Step2D {
     // slot) and its x CPML profiles at pml.*[2] + shot * pml_xstride.
     const int *win_nx;
     int pml_xstride;
+    int *err;             // error word of the TMA-staged kernels (1 = a wait gave up, 2 = misaligned copy refused)
 };
 
 // Planes of a 2D slot when shots have aperture windows: the 10 state planes,
@@ -256,9 +257,29 @@ constexpr int kThreads2D = 256;
 int march2d_txo(int M);
 
 // Launchers (kernels2d.cu). Return the cudaError of the launch.
+struct Maps2D;
+// maps (Born modelling only): TMA row staging, as for launch_adj2d.
 cudaError_t launch_fwd2d(const Step2D &a, int batch, bool born, bool save_bands, bool hess,
-                         cudaStream_t s);
-cudaError_t launch_adj2d(const Step2D &a, int batch, cudaStream_t s);
+                         cudaStream_t s, const Maps2D *maps = nullptr);
+// TMA row maps of the 2D Born and migration kernels reading one state buffer
+// (boxes one kThreads2D-wide row of one field): pr over the float2 pair planes
+// of every slot (8-byte elements; coordinates x, z, slot * pps + pair), fl
+// over its float planes (x, z, slot * fps + plane), md over dt kappa and
+// 1/rho (x, z, 0 | 1), mb over the Born model pairs (dt kappa, dt kappa
+// dlnk), (1/rho, rr) (x, z, 0 | 1), im over the image accumulators (x, z,
+// slot). Outside the padded grid the copies read zeros.
+struct Maps2D {
+    CUtensorMap pr, fl, md, mb, im;
+    int pps, fps;
+};
+cudaError_t maps2d(Maps2D *m, const GridDev &g, const float *st, long long sstride, const float *kdt,
+                   const float *binv, const float2 *kd2, const float2 *br2, const float2 *img, int batch);
+// maps: TMA row staging (shots without aperture windows), or null for the
+// per-thread asynchronous copies.
+cudaError_t launch_adj2d(const Step2D &a, const Maps2D *maps, int batch, cudaStream_t s);
+// cuTensorMapEncodeTiled (element strides 1, no swizzle, zero fill).
+cudaError_t encode_tmap(CUtensorMap *m, CUtensorMapDataType type, int rank, const void *base, const cuuint64_t *dims,
+                        const cuuint64_t *strides, const cuuint32_t *box);
 cudaError_t configure_2d_kernels();
 cudaError_t configure_3d_kernels();
 // Sets the launch attributes (dynamic shared memory limits) of every kernel
@@ -329,6 +350,15 @@ cudaError_t launch_nonfinite_count(const float *x, long long n, int *flag, cudaS
 // base, count and stride multiples of 4 floats) is NaN or Inf.
 cudaError_t launch_guard_state(const float *base, long long stride, long long count, int nslots, int *word,
                                int code, cudaStream_t s);
+// 16-bit checkpoint planes (fmt BAND_BF16S or BAND_F16S): planes [p0, p0 +
+// planes) of bs slots (slot stride sstride floats, plane floats each) to and
+// from a snapshot stored [slot][ck_planes][plane] in 16 bits with one scale
+// per slot and plane derived from amax ([slot][ck_planes], the planes'
+// largest magnitudes, written by the pack).
+cudaError_t launch_ck_pack(const float *src, long long sstride, long long plane, int planes, int p0, int bs,
+                           int ck_planes, int fmt, void *dst, float *amax, cudaStream_t s);
+cudaError_t launch_ck_unpack(float *dst, long long sstride, long long plane, int planes, int p0, int bs,
+                             int ck_planes, int fmt, const void *src, const float *amax, cudaStream_t s);
 // The same for n FP64 scalars.
 cudaError_t launch_guard_scalars(const double *v, int n, int *word, int code, cudaStream_t s);
 // Muted data residual: out = mute(r, n) fo[r] (dobs - dsyn), dsyn nullable; the

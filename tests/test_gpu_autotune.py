@@ -1,4 +1,4 @@
-"""The 2D z-chunk autotuner: it picks one of the timed candidates, and the
+"""The z-chunk autotuner (2D and fused 3D kernels): it picks one of the timed candidates, and the
 operators give bit-identical results before and after (the chunking changes
 which CTA computes a cell, not how)."""
 import dataclasses
@@ -46,8 +46,7 @@ def test_autotune_windowed_and_checkpointed():
            recon_mode=RECON_CHECKPOINT, checkpoint_interval=10)
 
 
-def test_autotune_3d_is_a_no_op():
-    w = li.small_case(ndim=3, nz=12, ny=10, nx=14, nt=20, order=4, npml=5, nshot=1, seed=304)
-    h = handle(w)
-    assert h.autotune()["tzc"] == 0
-    h.close()
+def test_autotune_3d_results_unchanged():
+    """The fused 3D kernels' z-chunk: several candidates, identical bits."""
+    _check(li.small_case(ndim=3, nz=40, ny=14, nx=20, nt=40, order=4, npml=5, nshot=2, seed=304))
+    _check(li.small_case(ndim=3, nz=44, ny=12, nx=18, nt=36, order=8, npml=6, nshot=2, seed=305))

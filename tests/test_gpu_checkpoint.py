@@ -169,3 +169,44 @@ def test_checkpoint_with_16bit_bands_equals_boundary(fmt):
         gc = handle(w, recon_mode=RECON_CHECKPOINT, band_precision=bp, checkpoint_interval=9).adjoint(d)
         print(f"{name} {fmt}: checkpoint vs boundary {rel(cpu(gc), cpu(gb)):.3e}, bitwise {torch.equal(gc, gb)}")
         assert rel(cpu(gc), cpu(gb)) < 1e-6
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp16"])
+def test_16bit_checkpoints(case, fmt):
+    """Checkpoint states stored in 16 bits with one FP32 scale per plane, shot
+    and snapshot: the image against the FP32-checkpoint image and the oracle,
+    and the checkpoint store at half its FP32 size."""
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, RECON_CHECKPOINT
+    name, w, dres = case
+    cp = BAND_BF16 if fmt == "bf16" else BAND_FP16
+    d = torch.tensor(dres, dtype=torch.float32, device="cuda")
+    h32 = handle(w, recon_mode=RECON_CHECKPOINT, checkpoint_interval=16)
+    h16 = handle(w, recon_mode=RECON_CHECKPOINT, checkpoint_interval=16, checkpoint_precision=cp)
+    g32, g16 = cpu(h32.adjoint(d)), cpu(h16.adjoint(d))
+    e32, eo = rel(g16, g32), rel(g16, oracle.adjoint(w, dres))
+    print(f"{name} {fmt} checkpoints: vs FP32 checkpoints {e32:.3e}, vs oracle {eo:.3e}; "
+          f"workspace {h16.workspace_bytes() / 1e6:.2f} vs {h32.workspace_bytes() / 1e6:.2f} MB")
+    assert e32 < (2e-3 if fmt == "bf16" else 2e-4)
+    assert eo < (2e-3 if fmt == "bf16" else 2e-4)
+    assert h16.workspace_bytes() < h32.workspace_bytes()
+    assert torch.equal(h16.adjoint(d), torch.tensor(g16, dtype=torch.float32, device="cuda"))
+    h32.close()
+    h16.close()
+
+
+def test_16bit_checkpoints_autograd_workload():
+    """The autograd workload (200 x 200, 16 shots, nt = 1500) in checkpoint
+    mode: 16-bit checkpoint images within 1e-3 of the FP32-checkpoint image."""
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, RECON_CHECKPOINT
+    w = li.preset(3)
+    rng = np.random.default_rng(12)
+    d = torch.tensor(rng.standard_normal((w.geom.nrec_total, w.nt)), dtype=torch.float32, device="cuda")
+    h32 = handle(w, recon_mode=RECON_CHECKPOINT)
+    g32 = cpu(h32.adjoint(d))
+    h32.close()
+    for cp, name in ((BAND_BF16, "bf16"), (BAND_FP16, "fp16")):
+        h16 = handle(w, recon_mode=RECON_CHECKPOINT, checkpoint_precision=cp)
+        e = rel(cpu(h16.adjoint(d)), g32)
+        print(f"autograd workload, {name} checkpoints (K = {h16.reconstruction()['interval']}): {e:.3e}")
+        assert e < 1e-3
+        h16.close()
