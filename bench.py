@@ -161,9 +161,20 @@ class ClockSampler:
         return out
 
 
+def step_kernels(w):
+    """Names of the Born and migration step kernels the workload runs: the
+    TMA-staged 2D kernels (no aperture windows), the per-thread-copy ones
+    (windows), or the fused 3D ones."""
+    if w.ndim == 3:
+        return {"born": "k3f_born", "adjoint": "k3f_adj"}
+    if getattr(w.geom, "win_nx", None) is not None:
+        return {"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"}
+    return {"born": "k_fwd2t", "adjoint": "k_adj2t"}
+
+
 def kernel_src_sha(ndim=2):
     h = hashlib.sha256()
-    for f in ("kernels2d.cu" if ndim == 2 else "kernels3d_fused.cu", "lsrtm_internal.cuh"):
+    for f in ("kernels2d.cu" if ndim == 2 else "kernels3d_fused.cu", "lsrtm_internal.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_2508_10405_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -868,12 +879,10 @@ def main():
     bpc = BYTES_PER_CELL[(dom, w.ndim)]
     achieved = bpc * cells_per_launch / avg_launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = ncu_traffic(({"born": "k_fwd2d_born", "adjoint": "k_adj2d"} if w.ndim == 2
-                           else {"born": "k3f_born", "adjoint": "k3f_adj"})[dom], cells_per_launch, w.ndim)
+    kname = step_kernels(w)[dom]
+    traffic = ncu_traffic(kname, cells_per_launch, w.ndim)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": ({"born": "k_fwd2d<BORN>", "adjoint": "k_adj2d"} if w.ndim == 2
-                           else {"born": "k3f_born", "adjoint": "k3f_adj"})[dom],
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_cell": bpc, "cells_per_launch": cells_per_launch,

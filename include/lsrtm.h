@@ -50,8 +50,9 @@ typedef enum {
 } lsrtm_status;
 
 /* Storage precision of the saved boundary bands (App. A). The 16-bit formats
- * keep one FP32 scale per band per step: values are stored as v / s with
- * s = max|band| / 2^15, so FP16 keeps its 11-bit mantissa down to 2^-24 of
+ * keep one FP32 scale per band per step: values are stored as v / s with s
+ * the power of two that puts max|band| / s in [2^14, 2^15) (s >= 2^-126), so
+ * the scaling is exact, FP16 keeps its 11-bit mantissa down to about 2^-23 of
  * each band's maximum and BF16 its 8-bit mantissa over the FP32 range. The
  * plain plan always stores FP32. */
 enum { LSRTM_BAND_FP32 = 0, LSRTM_BAND_BF16 = 1, LSRTM_BAND_FP16 = 2 };
@@ -103,7 +104,7 @@ typedef struct {
                                 reconstruction): LSRTM_BAND_FP32 (default; the images then equal
                                 the boundary mode's bit for bit), LSRTM_BAND_BF16 or
                                 LSRTM_BAND_FP16 with one FP32 scale per state plane per shot per
-                                snapshot (values / (max|plane| / 2^15)), which halves the
+                                snapshot (the bands' power-of-two scaling), which halves the
                                 checkpoint memory; the plain plan always stores FP32. */
 } lsrtm_config;
 

@@ -123,10 +123,11 @@ __global__ void k_image_acc(GridDev gm, GridDev g, const float2 *img, int batch,
     }
 }
 
-// One CTA per (field, slot): scale = max |band| / 2^15 of the step's FP32
-// stage, then the scaled values in the 16-bit format.
+// One CTA per (field, slot): scale = pow2_scale(max |band|) of the step's
+// FP32 stage, then the scaled values in the 16-bit format.
 __global__ void k_band_pack(Bands b, int shot0, int n)
 {
+    using lsrtm::pow2_scale;
     __shared__ float red[32];
     const int field = blockIdx.x, slot = blockIdx.y;
     const float *src = b.stage + ((long long)slot * 2 + field) * b.nb;
@@ -141,8 +142,8 @@ __global__ void k_band_pack(Bands b, int shot0, int n)
         if (threadIdx.x == 0) red[0] = m;
     }
     __syncthreads();
-    const float sc = red[0] > 0.f ? red[0] * (1.0f / 32768.0f) : 1.0f;
-    const float inv = 1.0f / sc;
+    const float sc = pow2_scale(red[0]);
+    const float inv = 1.0f / sc;   // exact: a power of two
     const long long row = band_row(b, shot0 + slot, n);
     if (threadIdx.x == 0) b.scale[row * 2 + field] = sc;
     void *dst = field ? b.v : b.p;
@@ -312,11 +313,11 @@ __global__ void k_guard_state(const float4 *x, long long stride4, long long coun
 }
 
 // 16-bit checkpoint planes. Plane q of slot s of a snapshot is stored as
-// v / c with c = m / 2^15, m = max|plane| (c = 1 for a zero plane): m is
-// taken first (k_ck_absmax, a float's bits order like the float for
-// magnitudes), then k_ck_pack writes the scaled values and k_ck_unpack
-// multiplies back. amax: [slot][ck_planes] of the snapshot.
-__device__ __forceinline__ float ck_scale(float m) { return m > 0.f ? m * (1.f / 32768.f) : 1.f; }
+// v / c with c = pow2_scale(m), m = max|plane|: m is taken first
+// (k_ck_absmax; the bits of non-negative floats order like the floats),
+// then k_ck_pack writes the scaled values and k_ck_unpack multiplies back.
+// amax: [slot][ck_planes] of the snapshot.
+__device__ __forceinline__ float ck_scale(float m) { return pow2_scale(m); }
 
 __global__ void k_ck_absmax(const float *src, long long sstride, long long plane, float *amax, int ck_planes,
                             int p0)

@@ -64,9 +64,9 @@ struct Pml {
 // Storage: FP32, or 16-bit values with one FP32 scale per band per step
 // (BF16 or FP16). With a 16-bit format the time-step kernels write the step's
 // bands in FP32 into a per-slot stage; k_band_pack then takes the largest
-// magnitude of each band, stores scale = max / 2^15 and the values divided by
-// it (so FP16 keeps its full mantissa over 2^15 .. 2^-24 of the band's
-// maximum), and the reverse pass multiplies back.
+// magnitude of each band, stores scale = pow2_scale(max) and the values
+// divided by it (so FP16 keeps its full mantissa down to about 2^-23 of the
+// band's maximum), and the reverse pass multiplies back.
 enum BandFmt { BAND_F32 = 0, BAND_BF16S = 1, BAND_F16S = 2 };
 
 struct Bands {
@@ -88,6 +88,18 @@ __host__ __device__ inline long long band_row(const Bands &b, int shot, int n)
 __host__ __device__ inline long long band_base(const Bands &b, int shot, int n) { return band_row(b, shot, n) * b.nb; }
 
 #ifdef __CUDACC__
+// Scale of a 16-bit block (a band of one step, a checkpoint plane) whose
+// largest magnitude is m: the power of two 2^e with m / 2^e in [2^14, 2^15),
+// so the scaled values fit FP16 and BF16 alike and the division and the
+// multiplication back are exact; e >= -126 keeps the scale and its inverse
+// normal (a block of subnormal magnitudes is then stored below 2^14). A zero
+// block gets 1.
+__device__ __forceinline__ float pow2_scale(float m)
+{
+    if (!(m > 0.f)) return 1.f;
+    return ldexpf(1.f, max(ilogbf(m) - 14, -126));
+}
+
 // Saves value v at slot idx of field (0: p band, 1: normal-v band) of the band
 // starting at base = band_base(shot, n) of batch slot `slot`.
 __device__ __forceinline__ void band_put(const Bands &b, int field, int slot, long long base, long long idx, float v)
@@ -321,7 +333,7 @@ cudaError_t launch_psfh_patches(const float *psf_vp, const float *psf_ip, int nz
 cudaError_t launch_psfh_apply(const PsfHessDev &a, bool transpose, const float *in, float *out, cudaStream_t s);
 
 // Utility kernels (kernels_util.cu).
-// 16-bit band formats: per slot and field, scale = max|stage| / 2^15 and the
+// 16-bit band formats: per slot and field, scale = pow2_scale(max|stage|) and the
 // scaled values into the band store at row band_row(shot0 + slot, n).
 cudaError_t launch_band_pack(const Bands &b, int batch, int shot0, int n, cudaStream_t s);
 cudaError_t launch_model_prep(const GridDev &g, const float *vp, const float *rho, float *kdt,
