@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", type=int, default=2, help="preset number (default 2)")
     ap.add_argument("--shots-per-batch", type=int, default=0)
-    ap.add_argument("--bands", choices=["fp32", "bf16", "fp16"], default="bf16",
+    ap.add_argument("--bands", choices=["fp32", "bf16", "fp16"], default="fp16",
                     help="boundary-band precision of the batched (timed) plan")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -788,6 +788,15 @@ def plain_compare(w, nshots, s_batched, bands, torch, image_shots):
             res[k] = {"bands_vs_fp32": float(torch.linalg.norm(x16.double() - x32) / nrm),
                       "fp32_under_1e-6_data_perturbation": float(torch.linalg.norm(xp.double() - x32) / nrm),
                       "misfit_fp32": float(m32[-1]), f"misfit_{bands}": float(m16[-1])}
+        # the stand-in checked here too: the plain plan's own 5-iteration image
+        hpl = Lsrtm.from_workload(sub, plan=PLAN_PLAIN, band_precision=BAND_FP32)
+        hpl.autotune()
+        xpl, _ = hpl.cg_solve(dd, 5)
+        x32, _ = h32.cg_solve(dd, 5)
+        hpl.close()
+        res["plain_vs_batched_fp32_5_iterations"] = {
+            "rel_l2": float(torch.linalg.norm(xpl.double() - x32.double()) / torch.linalg.norm(x32.double())),
+            "bitwise": bool(torch.equal(xpl, x32))}
         h32.close()
         h16.close()
         out["final_image_rel_l2"] = res[ni]["bands_vs_fp32"]

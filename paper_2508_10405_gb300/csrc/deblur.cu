@@ -14,10 +14,16 @@
 //
 // k_deblur_solve: one CTA per (node, parameter plane). The window's patch of
 // m'' (window + h on each side, zero outside the image) sits in shared memory
-// as float; each thread accumulates entries of the upper triangle of A^T A in
-// FP64 (products of two floats are exact in FP64); the matrix, factorised in
-// place by a right-looking Cholesky, and the right-hand side stay in shared
-// memory (121 x 121 doubles = 117 KB for flen = 11).
+// as float. Entry (u, v) of A^T A is the sum of P(q) P(q + d) over the window
+// shifted to tap u's origin, d = origin(v) - origin(u): the products depend on
+// the lag d only, so per lag one warp forms, for every patch row, the
+// running sums of the row's lagged products over the window width at every
+// origin column (one pass along the row), then slides those along z over the
+// window height at every origin row. That is 15x fewer FP64 operations than
+// summing each entry over the window (products of two floats are exact in
+// FP64; sums in FP64). The matrix, factorised in place by a right-looking
+// Cholesky, and the right-hand side stay in shared memory (121 x 121 doubles
+// = 117 KB for flen = 11).
 // k_deblur_apply: one thread per pixel and plane; FP32 taps, at most four
 // covering nodes.
 // The paper's own Fourier form of the filter (per-block Wiener ratio) follows
@@ -37,7 +43,7 @@ constexpr int kSolveThreads = 256;
 
 __global__ void __launch_bounds__(kSolveThreads) k_deblur_solve(const float *mref, const float *mrem, int nz,
                                                                  int nx, int s, int flen, double eps,
-                                                                 float *filt, int *flag)
+                                                                 float *filt, int *flag, int nrs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = flen * flen, h = flen / 2;
@@ -51,7 +57,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_deblur_solve(const float *mre
     double *G = reinterpret_cast<double *>(smem);   // [n][n]
     double *rhs = G + n * n;                        // [n]
     double *red = rhs + n;                          // [2]: trace, pivot status
-    float *P = reinterpret_cast<float *>(red + 2);  // [PZ][PX]
+    double *RS = red + 2;                           // [nrs warps][PZ][2h + 1] row sums of one lag
+    float *P = reinterpret_cast<float *>(RS + (size_t)nrs * PZ * (2 * h + 1));   // [PZ][PX]
     const long long plane = (long long)nz * nx;
     const float *m2 = mrem + param * plane;
     const float *m1 = mref + param * plane;
@@ -68,20 +75,44 @@ __global__ void __launch_bounds__(kSolveThreads) k_deblur_solve(const float *mre
     }
     __syncthreads();
 
-    // A[p, u] = m''(p - (a, b)) = P[pz + h - a][px + h - b], u = (a + h) flen + (b + h)
-    for (int e = t; e < n * n; e += blockDim.x) {
-        const int u = e / n, v = e - u * n;
-        if (v < u) continue;
-        const int ozu = 2 * h - u / flen, oxu = 2 * h - u % flen;
-        const int ozv = 2 * h - v / flen, oxv = 2 * h - v % flen;
-        double acc = 0.0;
-        for (int pz = 0; pz < WZ; ++pz) {
-            const float *ru = P + (pz + ozu) * PX + oxu;
-            const float *rv = P + (pz + ozv) * PX + oxv;
-            for (int px = 0; px < WX; ++px) acc = fma((double)ru[px], (double)rv[px], acc);
+    // A[p, u] = m''(p - (a, b)) = P[pz + oz_u][px + ox_u], u = (a + h) flen + (b + h),
+    // origin (oz_u, ox_u) = (2h - u / flen, 2h - u % flen) in [0, 2h]^2
+    {
+        const int warp = t >> 5, lane = t & 31, W2 = 2 * h + 1;
+        double *rs = RS + (size_t)warp * PZ * W2;
+        const int nlag = 2 * h * (4 * h + 1) + (2 * h + 1);   // dz > 0, or dz = 0 and dx >= 0
+        for (int li = warp; li < nlag && warp < nrs; li += nrs) {
+            const int dz = li < 2 * h + 1 ? 0 : 1 + (li - (2 * h + 1)) / (4 * h + 1);
+            const int dx = li < 2 * h + 1 ? li : (li - (2 * h + 1)) % (4 * h + 1) - 2 * h;
+            const int oz0 = max(0, -dz), oz1 = min(2 * h, 2 * h - dz);   // origins of u with u + d a tap
+            const int ox0 = max(0, -dx), ox1 = min(2 * h, 2 * h - dx);
+            // rs[r][ox] = sum_{c = ox}^{ox + WX - 1} P[r][c] P[r + dz][c + dx]
+            for (int r = oz0 + lane; r < oz1 + WZ; r += 32) {
+                const float *a = P + r * PX, *b = P + (r + dz) * PX + dx;
+                double acc = 0.0;
+                for (int c = ox0; c < ox0 + WX; ++c) acc = fma((double)a[c], (double)b[c], acc);
+                rs[r * W2 + ox0] = acc;
+                for (int ox = ox0 + 1; ox <= ox1; ++ox) {
+                    acc = fma((double)a[ox + WX - 1], (double)b[ox + WX - 1], acc);
+                    acc = fma(-(double)a[ox - 1], (double)b[ox - 1], acc);
+                    rs[r * W2 + ox] = acc;
+                }
+            }
+            __syncwarp();
+            // S(oz, ox) = sum_{r = oz}^{oz + WZ - 1} rs[r][ox] -> G[u][v] and G[v][u]
+            for (int ox = ox0 + lane; ox <= ox1; ox += 32) {
+                double acc = 0.0;
+                for (int r = oz0; r < oz0 + WZ; ++r) acc += rs[r * W2 + ox];
+                for (int oz = oz0; oz <= oz1; ++oz) {
+                    if (oz > oz0) acc += rs[(oz + WZ - 1) * W2 + ox] - rs[(oz - 1) * W2 + ox];
+                    const int u = (2 * h - oz) * flen + (2 * h - ox);
+                    const int v = (2 * h - oz - dz) * flen + (2 * h - ox - dx);
+                    G[u * n + v] = acc;
+                    G[v * n + u] = acc;
+                }
+            }
+            __syncwarp();
         }
-        G[u * n + v] = acc;
-        G[v * n + u] = acc;
     }
     for (int u = t; u < n; u += blockDim.x) {
         const int ozu = 2 * h - u / flen, oxu = 2 * h - u % flen;
@@ -369,11 +400,22 @@ cudaError_t launch_wiener(const float *mref, const float *mrem, int nz, int nx, 
     return cudaGetLastError();
 }
 
-size_t deblur_solve_smem(int nz, int nx, int s, int flen)
+// Shared memory of k_deblur_solve with nrs warps forming lag sums.
+size_t deblur_solve_smem(int nz, int nx, int s, int flen, int nrs)
 {
     const int n = flen * flen, h = flen / 2;
     const int wz = std::min(nz, 2 * s + 1), wx = std::min(nx, 2 * s + 1);
-    return ((size_t)n * n + n + 2) * sizeof(double) + (size_t)(wz + 2 * h) * (wx + 2 * h) * sizeof(float);
+    return ((size_t)n * n + n + 2 + (size_t)nrs * (wz + 2 * h) * (2 * h + 1)) * sizeof(double) +
+           (size_t)(wz + 2 * h) * (wx + 2 * h) * sizeof(float);
+}
+
+// Warps of k_deblur_solve that form lag sums: as many as fit (at most all),
+// 0 if not even one does.
+int deblur_solve_warps(int nz, int nx, int s, int flen)
+{
+    int nrs = kSolveThreads / 32;
+    while (nrs > 0 && deblur_solve_smem(nz, nx, s, flen, nrs) > kDeblurSmemLimit) --nrs;
+    return nrs;
 }
 
 int deblur_nodes(int n, int s) { return n > s / 2 ? (n - 1 - s / 2) / s + 1 : 0; }
@@ -382,10 +424,12 @@ cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, 
                           float *filt, float *out, int *flag, cudaStream_t st)
 {
     const int nkz = deblur_nodes(nz, s), nkx = deblur_nodes(nx, s);
-    const size_t sm = deblur_solve_smem(nz, nx, s, flen);
+    const int nrs = deblur_solve_warps(nz, nx, s, flen);
+    if (nrs < 1) return cudaErrorInvalidValue;
+    const size_t sm = deblur_solve_smem(nz, nx, s, flen, nrs);
     cudaError_t e = cudaFuncSetAttribute(k_deblur_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_deblur_solve<<<dim3(nkx, nkz, 2), kSolveThreads, sm, st>>>(mref, mrem, nz, nx, s, flen, eps, filt, flag);
+    k_deblur_solve<<<dim3(nkx, nkz, 2), kSolveThreads, sm, st>>>(mref, mrem, nz, nx, s, flen, eps, filt, flag, nrs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const long long plane = (long long)nz * nx;
     k_deblur_apply<<<dim3((unsigned)((plane + 255) / 256), 2), 256, 0, st>>>(mref, filt, nz, nx, s, flen, nkz, nkx,

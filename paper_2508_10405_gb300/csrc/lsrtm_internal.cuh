@@ -314,7 +314,10 @@ cudaError_t launch_pack_adjoint(const GridDev &g, const float *final_state, int 
 // the [2][nz][nx] images, then the valence-weighted filtered image.
 // filt: [2][nkz][nkx][flen*flen]; flag |= 1 where a factorisation failed.
 int deblur_nodes(int n, int s);
-size_t deblur_solve_smem(int nz, int nx, int s, int flen);
+constexpr size_t kDeblurSmemLimit = 227 * 1024;   // dynamic shared memory of one CTA
+// Warps of the filter solve that form lag sums (as many as fit; 0: the
+// filter length does not fit shared memory).
+int deblur_solve_warps(int nz, int nx, int s, int flen);
 cudaError_t launch_deblur(const float *mref, const float *mrem, int nz, int nx, int s, int flen, double eps,
                           float *filt, float *out, int *flag, cudaStream_t st);
 
