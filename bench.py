@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--shots", type=int, default=None,
                     help="override the shot count (smaller cases for profiling)")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: split the survey's shots over the ranks and run the shot-parallel "
+                         "CGNR (image all-reduce after every L^T) instead of one survey per rank")
     ap.add_argument("--plan", choices=["batched", "plain"], default="batched",
                     help="execution plan of the timed handle")
     ap.add_argument("--no-autotune", action="store_true",
@@ -807,6 +810,86 @@ def plain_compare(w, nshots, s_batched, bands, torch, image_shots):
     return out
 
 
+def shard_bench(args, rank, world, local):
+    """Strong scaling of one survey (Sec. 3: shots mapped to processors, the
+    image reduced): rank r owns shots r, r + N, ... and the step is one
+    iteration of the shot-parallel CGNR (distributed.ShotParallelCG: the
+    rank's L and L^T, an all-reduce of the two-parameter image after every
+    L^T and of the FP64 data-space inner products). value = the whole
+    survey's cell-updates per iteration / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    import dataclasses
+    from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, BAND_FP32, Lsrtm
+    from paper_2508_10405_gb300.distributed import ShotParallelCG, shard
+    bands = {"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[args.bands]
+    w = workload(args)
+    K, W = args.steps, args.warmup
+    mine = shard(w.geom.nshot, rank, world)
+    wl = dataclasses.replace(w, geom=w.geom.subset(mine))
+    cells_per_step = 2.0 * float(shot_cells(w).sum()) * w.nt   # the whole survey's L + L^T
+    h = Lsrtm.from_workload(wl, band_precision=bands, shots_per_batch=args.shots_per_batch)
+    tune = None if args.no_autotune else h.autotune()
+    dm_true = torch.tensor(w.dm, dtype=torch.float32, device="cuda")
+    d_local = h.born(dm_true)
+    cg = ShotParallelCG(h, heartbeat_timeout=600.0)
+    ev = {W: torch.cuda.Event(enable_timing=True), W + K: torch.cuda.Event(enable_timing=True)}
+    clocks = ClockSampler(local)
+
+    def mark(k):
+        if k == W:
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            clocks.start()
+            h.timing(True)
+            h.timings(reset=True)
+        if k in ev:
+            ev[k].record()
+
+    if W == 0:
+        mark(0)
+    x, mis = cg.solve(d_local, W + K, on_iteration=mark)
+    torch.cuda.synchronize()
+    tm = h.timings(reset=True)
+    h.timing(False)
+    clk = clocks.stop()
+    t = torch.tensor([ev[W].elapsed_time(ev[W + K]) / 1e3], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    kinds = {"born": (tm["born_ms"], tm["born_launches"], tm["born_cells"]),
+             "adjoint": (tm["adjoint_ms"], tm["adjoint_launches"], tm["adjoint_cells"])}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, nl, cells = kinds[dom]
+    bpc = BYTES_PER_CELL[(dom, w.ndim)]
+    achieved = bpc * (cells / max(nl, 1)) / (ms / 1e3 / max(nl, 1)) / 1e9 if ms else None
+    peak, peak_kind = peaks()
+    kname = step_kernels(w)[dom]
+    if rank == 0:
+        line = {
+            "metric": "Born+migration Gcell-updates/s", "value": cells_per_step * K / t_max / 1e9,
+            "unit": "Gcell-updates/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "nt": w.nt, "order": w.order,
+                       "shots": w.geom.nshot, "shots_per_rank": len(mine), "bands": args.bands,
+                       "autotune": tune, "s_per_lsrtm_iter": t_max / K,
+                       "step": "one shot-parallel CGNR iteration (rank-local L + L^T, image and FP64 "
+                               "inner-product all-reduces)",
+                       "parallelism": f"shots sharded over {world} rank(s), image all-reduce per L^T"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": ncu_traffic(kname, cells / max(nl, 1), w.ndim), "kernel": kname,
+                         "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"},
+            "clocks": clk, "misfit": mis[-1], "e2e": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -827,6 +910,9 @@ def main():
         return
     if world > 1:
         dist.init_process_group("nccl")
+    if args.shard:
+        shard_bench(args, rank, world, local)
+        return
 
     from paper_2508_10405_gb300 import BAND_BF16, BAND_FP16, BAND_FP32, PLAN_BATCHED, PLAN_PLAIN, Lsrtm
     bands = {"fp32": BAND_FP32, "bf16": BAND_BF16, "fp16": BAND_FP16}[args.bands]

@@ -238,50 +238,87 @@ __global__ void k_deblur_apply(const float *mref, const float *filt, int nz, int
 // valence of the space-domain filters.
 //
 // k_wiener_block: one CTA per (node, plane); the block, its spectra and a
-// transform buffer sit in shared memory as complex FP32; each 2D DFT is two
-// passes of direct N-term sums (rows, then columns) with a twiddle table;
-// the block result goes to blk[plane][node][N*N].
+// transform buffer sit in shared memory as complex FP32; each 2D DFT runs
+// along the rows, then the columns, each as one Cooley-Tukey split N = N1 N2
+// (dft2) with a twiddle table; the block result goes to
+// blk[plane][node][N*N].
 // k_wiener_blend: one thread per pixel, the (up to) four covering blocks.
 // ---------------------------------------------------------------------------
 constexpr int kWienerThreads = 256, kWienerMaxS = 32;
 
-// dst = DFT2(src) (sign -1) or the unscaled inverse (sign +1), via tmp.
+// One Cooley-Tukey split of a length-N DFT, N = N1 N2 (N1 the divisor of N
+// nearest sqrt N; 5 x 8 for N = 40): with n = N2 n1 + n2 and k = k1 + N1 k2,
+//   X[k] = sum_n2 w^(N1 n2 k2) [ w^(n2 k1) sum_n1 x[N2 n1 + n2] w^(N2 n1 k1) ],
+// w = exp(-+2 pi i / N): N1 + N2 terms per output instead of N. Pass A (the
+// inner sums and the twiddle) writes tmp[row][n2 N1 + k1]; pass B the outputs.
+// Applied to every row (stride 1 along a row, rows `rs` apart) or every
+// column (stride N, columns 1 apart) of an N x N block.
+__device__ int dft_split(int N)
+{
+    int best = 1;
+    for (int d = 2; d <= N; ++d)
+        if (N % d == 0 && fabsf((float)d * d - (float)N) < fabsf((float)best * best - (float)N)) best = d;
+    return best;
+}
+
+__device__ void dft_pass_a(const float2 *src, float2 *tmp, const float2 *tw, int N, int N1, bool inverse, bool cols)
+{
+    const int N2 = N / N1, NN = N * N;
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+        const int line = idx / N, e = idx - line * N;   // e = n2 N1 + k1
+        const int n2 = e / N1, k1 = e - n2 * N1;
+        const int st = cols ? N : 1, base = cols ? line : line * N;
+        float re = 0.f, im = 0.f;
+        int j = 0;
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const float2 w = tw[j];
+            const float wi = inverse ? w.y : -w.y;
+            const float2 v = src[base + (N2 * n1 + n2) * st];
+            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
+            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
+            j += N2 * k1;
+            while (j >= N) j -= N;
+        }
+        int jt = n2 * k1;
+        while (jt >= N) jt -= N;
+        const float2 w = tw[jt];
+        const float wi = inverse ? w.y : -w.y;
+        tmp[idx] = make_float2(re * w.x - im * wi, re * wi + im * w.x);
+    }
+    __syncthreads();
+}
+
+__device__ void dft_pass_b(const float2 *tmp, float2 *dst, const float2 *tw, int N, int N1, bool inverse, bool cols)
+{
+    const int N2 = N / N1, NN = N * N;
+    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {
+        const int line = idx / N, k = idx - line * N;   // k = k1 + N1 k2
+        const int k2 = k / N1, k1 = k - k2 * N1;
+        float re = 0.f, im = 0.f;
+        int j = 0;
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const float2 w = tw[j];
+            const float wi = inverse ? w.y : -w.y;
+            const float2 v = tmp[line * N + n2 * N1 + k1];
+            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
+            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
+            j += N1 * k2;
+            while (j >= N) j -= N;
+        }
+        dst[cols ? k * N + line : line * N + k] = make_float2(re, im);
+    }
+    __syncthreads();
+}
+
+// dst = DFT2(src) (sign -1) or the unscaled inverse (sign +1), rows then
+// columns, via tmp (src is kept; dst and tmp are overwritten).
 __device__ void dft2(const float2 *src, float2 *tmp, float2 *dst, const float2 *tw, int N, bool inverse)
 {
-    const int NN = N * N;
-    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {   // along x: tmp[r][k] = sum_n src[r][n] w^(k n)
-        const int r = idx / N, k = idx - r * N;
-        const float2 *row = src + r * N;
-        float re = 0.f, im = 0.f;
-        int j = 0;
-        for (int n = 0; n < N; ++n) {
-            const float2 w = tw[j];
-            const float wi = inverse ? w.y : -w.y;
-            const float2 v = row[n];
-            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
-            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
-            j += k;
-            if (j >= N) j -= N;
-        }
-        tmp[idx] = make_float2(re, im);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NN; idx += blockDim.x) {   // along z: dst[k][c] = sum_n tmp[n][c] w^(k n)
-        const int k = idx / N, c = idx - k * N;
-        float re = 0.f, im = 0.f;
-        int j = 0;
-        for (int n = 0; n < N; ++n) {
-            const float2 w = tw[j];
-            const float wi = inverse ? w.y : -w.y;
-            const float2 v = tmp[n * N + c];
-            re = fmaf(v.x, w.x, fmaf(-v.y, wi, re));
-            im = fmaf(v.x, wi, fmaf(v.y, w.x, im));
-            j += k;
-            if (j >= N) j -= N;
-        }
-        dst[idx] = make_float2(re, im);
-    }
-    __syncthreads();
+    const int N1 = dft_split(N);
+    dft_pass_a(src, tmp, tw, N, N1, inverse, false);
+    dft_pass_b(tmp, dst, tw, N, N1, inverse, false);
+    dft_pass_a(dst, tmp, tw, N, N1, inverse, true);
+    dft_pass_b(tmp, dst, tw, N, N1, inverse, true);
 }
 
 __device__ void load_block(const float *g, int nz, int nx, int zc, int xc, int N, float2 *dst)
