@@ -588,11 +588,15 @@ def model_bench(args, rank, world, local):
 
 def wiener_flops(nz, nx, s):
     """Algorithmic FP32 flops of the Wiener blocks: per block and plane three
-    2D DFTs of N = 2s points per axis as direct sums (2 passes of N^3 complex
-    multiply-adds, 8 flops each)."""
+    2D DFTs of N = 2s points per axis, each axis one Cooley-Tukey split
+    N = N1 N2 (N1 the divisor nearest sqrt N): per output N1 + N2 complex
+    multiply-adds and one twiddle product (8 and 6 flops), over N^2 outputs
+    and 2 axes."""
     nk = len(range(s // 2, nz, s)) * len(range(s // 2, nx, s))
     N = 2 * s
-    return 2.0 * nk * 3 * 2 * N ** 3 * 8
+    n1 = min((d for d in range(1, N + 1) if N % d == 0), key=lambda d: abs(d * d - N))
+    per_out = (n1 + N // n1) * 8 + 6
+    return 2.0 * nk * 3 * 2 * N ** 2 * per_out
 
 
 def deblur_bench(args, rank, world, local):
