@@ -34,6 +34,7 @@ constexpr int PDF = 4;   // depth of the asynchronous row pipeline (forward)
 constexpr int PDA = 3;   // depth of the asynchronous row pipeline (adjoint; 3 CTAs per SM fit)
 constexpr int kFwdMinBlocks = 2;   // resident CTAs per SM the register budget targets
 constexpr int kFwdTMinBlocks = 3;  // the TMA-staged Born kernel: three CTAs per SM (measured +25%)
+constexpr int kFwdPlainMinBlocks = 3;   // the background step without bands or pseudo-Hessian (modelling)
 constexpr int kAdjMinBlocks = 3;
 constexpr int kAdjMinBlocksFS = 2;   // the free-surface variant needs more registers
 // The z-marches are unrolled by 2M / k*GroupDiv rows and shift their register
@@ -267,7 +268,7 @@ __device__ __forceinline__ FwdRow<BORN> fwd_read(const char *st)
 }
 
 template <int M, bool BORN, bool BANDS, bool HESS, bool WIN, bool FS>
-__global__ void __launch_bounds__(NTH, kFwdMinBlocks) k_fwd2d(const Step2D a)
+__global__ void __launch_bounds__(NTH, (BORN || BANDS || HESS) ? kFwdMinBlocks : kFwdPlainMinBlocks) k_fwd2d(const Step2D a)
 {
     if (guard_tripped(a.g)) return;
     using C = Cols<M>;
